@@ -1,0 +1,232 @@
+"""Plain FP64 CPU oracle for microlensing critical curves and caustics.
+
+TEST INFRASTRUCTURE ONLY.  The slow, obviously-correct reference that the CUDA path is
+checked against (Weisenbach 2025, Secs. 3-5 and Appendices A and C).  Only the test
+suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
+it.  It shares no code with the CUDA library and never imports the product package.
+
+The arithmetic lives in ``cc_oracle.c`` (C99, FP64, ``-ffp-contract=off``); this module
+compiles it with gcc and wraps it with ctypes.  Parity status of each function is in the
+C file's comments; everything here is pinned by tests in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cc_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_DP = ctypes.POINTER(ctypes.c_double)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_U8P = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/_liboracle.so`` (OpenMP if gcc supports it)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    base = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math"]
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    r = subprocess.run(base + ["-fopenmp", "-o", tmp, _SRC, "-lm"], capture_output=True, text=True)
+    if r.returncode != 0:
+        r = subprocess.run(base + ["-o", tmp, _SRC, "-lm"], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stderr)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        i64, dbl, i32 = ctypes.c_int64, ctypes.c_double, ctypes.c_int32
+        lib.orc_F.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, dbl, _DP, _DP]
+        lib.orc_F.restype = dbl
+        lib.orc_dF.argtypes = [_DP, _DP, _DP, i64, _DP, _DP]
+        lib.orc_dF.restype = dbl
+        lib.orc_inv_mu.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, _DP]
+        lib.orc_inv_mu.restype = dbl
+        lib.orc_solve_row.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, dbl, _DP, _DP, ctypes.c_int, dbl, _I32P]
+        lib.orc_solve_row.restype = i64
+        lib.orc_phi.argtypes = [i64, i64]
+        lib.orc_phi.restype = dbl
+        lib.orc_critical_curves.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, i64, dbl, ctypes.c_int,
+                                            ctypes.c_int, _DP, _I32P]
+        lib.orc_critical_curves.restype = i64
+        lib.orc_map_caustics.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, _DP, i64, _DP]
+        lib.orc_map_caustics.restype = None
+        lib.orc_min_separation.argtypes = [_DP, i64]
+        lib.orc_min_separation.restype = dbl
+        lib.orc_orient2d.argtypes = [dbl] * 6
+        lib.orc_orient2d.restype = ctypes.c_int
+        lib.orc_pixel_center.argtypes = [dbl, dbl, i32, i32]
+        lib.orc_pixel_center.restype = dbl
+        lib.orc_winding_at.argtypes = [_DP, i64, i64, dbl, dbl]
+        lib.orc_winding_at.restype = i64
+        lib.orc_crossing_map.argtypes = [_DP, i64, i64, dbl, dbl, dbl, dbl, i32, i32, _I32P]
+        lib.orc_crossing_map.restype = None
+        lib.orc_feature_mask.argtypes = [_I32P, i32, i32, _U8P]
+        lib.orc_feature_mask.restype = None
+        lib.orc_distance_map_brute.argtypes = [_I32P, i32, i32, dbl, _DP]
+        lib.orc_distance_map_brute.restype = None
+        lib.orc_distance_map_separable.argtypes = [_I32P, i32, i32, dbl, _DP]
+        lib.orc_distance_map_separable.restype = None
+        lib.orc_num_threads.argtypes = []
+        lib.orc_num_threads.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _stars(x, y, m):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    if not (x.shape == y.shape == m.shape and x.ndim == 1):
+        raise ValueError("x, y, m must be 1-D arrays of equal length")
+    return x, y, m
+
+
+def num_threads() -> int:
+    """OpenMP threads the oracle uses (1 when built without OpenMP)."""
+    return int(_load().orc_num_threads())
+
+
+def phi(j: int, msteps: int) -> float:
+    """phi_j = 2 pi j / m, computed exactly as the oracle does (Sec. 4.3)."""
+    return float(_load().orc_phi(int(j), int(msteps)))
+
+
+def F(x, y, m, kappa_s, gamma, phi_, z):
+    """F(z, phi) of the parametric critical-curve equation (Sec. 3.1, Appendix A)."""
+    x, y, m = _stars(x, y, m)
+    zz = np.array([complex(z).real, complex(z).imag])
+    out = np.zeros(2)
+    _load().orc_F(_d(x), _d(y), _d(m), len(x), kappa_s, gamma, phi_, _d(zz), _d(out))
+    return complex(out[0], out[1])
+
+
+def dF(x, y, m, z):
+    """dF/dz = -2 sum m_i/(z - z_i)^3."""
+    x, y, m = _stars(x, y, m)
+    zz = np.array([complex(z).real, complex(z).imag])
+    out = np.zeros(2)
+    _load().orc_dF(_d(x), _d(y), _d(m), len(x), _d(zz), _d(out))
+    return complex(out[0], out[1])
+
+
+def inv_mu(x, y, m, kappa_s, gamma, z):
+    """1/mu = det J at z (Sec. 2.1, Appendix C)."""
+    x, y, m = _stars(x, y, m)
+    zz = np.array([complex(z).real, complex(z).imag])
+    return float(_load().orc_inv_mu(_d(x), _d(y), _d(m), len(x), kappa_s, gamma, _d(zz)))
+
+
+def solve_row(x, y, m, kappa_s, gamma, phi_, z0=None, max_iter=500, tol=1e-9, return_iters=False):
+    """Roots of F(., phi) for one row: Jacobi Aberth (from z0, or from the z_i +- 1 guesses
+    when z0 is None) followed by a Newton polish.  Returns (z[2N] complex128, unfrozen)."""
+    x, y, m = _stars(x, y, m)
+    n = len(x)
+    out = np.zeros(2 * n, dtype=np.complex128)
+    zin = None
+    if z0 is not None:
+        zin = np.ascontiguousarray(z0, dtype=np.complex128)
+        if zin.shape != (2 * n,):
+            raise ValueError("z0 must have 2N entries")
+    iters = np.zeros(2 * n, dtype=np.int32)
+    left = _load().orc_solve_row(_d(x), _d(y), _d(m), n, kappa_s, gamma, phi_,
+                                 None if zin is None else zin.view(np.float64).ctypes.data_as(_DP),
+                                 out.view(np.float64).ctypes.data_as(_DP), int(max_iter), tol,
+                                 iters.ctypes.data_as(_I32P))
+    if return_iters:
+        return out, int(left), iters
+    return out, int(left)
+
+
+def critical_curves(x, y, m, kappa_s, gamma, msteps, tol=1e-9, max_iter_cold=500, max_iter_warm=200):
+    """Chain matrix of Sec. 4.3: (m+1) x 2N complex128 roots, row j at phi_j = 2 pi j/m.
+    Returns (z, iters, unfrozen_total)."""
+    if msteps < 2 or msteps % 2:
+        raise ValueError("m must be even and >= 2")
+    x, y, m = _stars(x, y, m)
+    n = len(x)
+    z = np.zeros((msteps + 1, 2 * n), dtype=np.complex128)
+    it = np.zeros((msteps + 1, 2 * n), dtype=np.int32)
+    bad = _load().orc_critical_curves(_d(x), _d(y), _d(m), n, kappa_s, gamma, int(msteps), tol,
+                                      int(max_iter_cold), int(max_iter_warm),
+                                      z.view(np.float64).ctypes.data_as(_DP), it.ctypes.data_as(_I32P))
+    return z, it, int(bad)
+
+
+def map_caustics(x, y, m, kappa_s, gamma, z):
+    """Lens map w(z) of every critical point (Sec. 3.1); same shape as z."""
+    x, y, m = _stars(x, y, m)
+    zz = np.ascontiguousarray(z, dtype=np.complex128)
+    w = np.zeros_like(zz)
+    _load().orc_map_caustics(_d(x), _d(y), _d(m), len(x), kappa_s, gamma,
+                             zz.view(np.float64).ctypes.data_as(_DP), zz.size,
+                             w.view(np.float64).ctypes.data_as(_DP))
+    return w
+
+
+def min_separation(zrow):
+    zz = np.ascontiguousarray(zrow, dtype=np.complex128)
+    return float(_load().orc_min_separation(zz.view(np.float64).ctypes.data_as(_DP), zz.size))
+
+
+def orient2d(ax, ay, bx, by, cx, cy) -> int:
+    """Exact sign of (a-c) x (b-c): +1 if c is left of a->b, -1 right, 0 collinear."""
+    return int(_load().orc_orient2d(float(ax), float(ay), float(bx), float(by), float(cx), float(cy)))
+
+
+def pixel_center(lo, hi, cnt, i) -> float:
+    return float(_load().orc_pixel_center(float(lo), float(hi), int(cnt), int(i)))
+
+
+def winding_at(w, px, py) -> int:
+    """Sunday winding number of the caustic polygons (columns of w) around (px, py)."""
+    ww = np.ascontiguousarray(w, dtype=np.complex128)
+    rows, nr = ww.shape
+    return int(_load().orc_winding_at(ww.view(np.float64).ctypes.data_as(_DP), rows, nr, px, py))
+
+
+def crossing_map(w, x0, x1, y0, y1, W, H):
+    """N_cc = -winding number at every pixel centre (Sec. 5.1); int32 [H, W]."""
+    ww = np.ascontiguousarray(w, dtype=np.complex128)
+    rows, nr = ww.shape
+    out = np.zeros((H, W), dtype=np.int32)
+    _load().orc_crossing_map(ww.view(np.float64).ctypes.data_as(_DP), rows, nr, x0, x1, y0, y1,
+                             int(W), int(H), out.ctypes.data_as(_I32P))
+    return out
+
+
+def feature_mask(ncc):
+    a = np.ascontiguousarray(ncc, dtype=np.int32)
+    H, W = a.shape
+    out = np.zeros((H, W), dtype=np.uint8)
+    _load().orc_feature_mask(a.ctypes.data_as(_I32P), W, H, out.ctypes.data_as(_U8P))
+    return out
+
+
+def distance_map(ncc, pixel, method="separable"):
+    """Distance from each pixel to the nearest caustic pixel (Sec. 5.2), FP64 [H, W]."""
+    a = np.ascontiguousarray(ncc, dtype=np.int32)
+    H, W = a.shape
+    out = np.zeros((H, W), dtype=np.float64)
+    fn = _load().orc_distance_map_brute if method == "brute" else _load().orc_distance_map_separable
+    fn(a.ctypes.data_as(_I32P), W, H, float(pixel), out.ctypes.data_as(_DP))
+    return out

@@ -1,0 +1,564 @@
+/*
+ * Plain FP64 CPU oracle for microlensing critical curves, caustics, caustic-crossing
+ * maps and distance-to-caustic maps (Weisenbach 2025, "A GPU Code for Finding
+ * Microlensing Critical Curves and Caustics").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct reference that
+ * the CUDA path is checked against.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may build, load or call it.  It shares no code,
+ * header, table or helper with the CUDA library.
+ *
+ * Conventions
+ *   - theta_* = 1 (Einstein radius of a unit mass); stars (x_i, y_i, m_i).
+ *   - Lens model: circular field with the compensating sheet extended to infinity
+ *     (Appendix A), so alpha_s(z) = -kappa_* z everywhere and
+ *       w(z)    = (1 - kappa_s) z + gamma conj(z) - sum_i m_i / conj(z - z_i)   (Sec. 3.1)
+ *       F(z,phi)= gamma + sum_i m_i / (z - z_i)^2 - (1 - kappa_s) e^{-i phi}     (Eq. parametric cc)
+ *     where kappa_s is the smooth convergence (kappa - kappa_*).
+ *   - Complex arrays are interleaved (re, im) doubles == C99 double complex.
+ *   - Built with -ffp-contract=off and without fast-math: every operation is an IEEE
+ *     round-to-nearest FP64 operation in the order written.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* pi to double precision (same value as the POSIX M_PI). */
+#define ORC_PI 3.14159265358979323846
+
+/* ------------------------------------------------------------------------------------
+ * Lens model (Sec. 3.1 and Appendix A)
+ * ------------------------------------------------------------------------------------ */
+
+/* F(z, phi) of the parametric critical-curve equation (Sec. 3.1) with the infinite
+ * compensating sheet (Appendix A): dalpha_s/dz = -kappa_*, dalpha_s/dconj(z) = 0, so
+ * 1 - kappa - dalpha_s/dz = 1 - kappa_s. */
+static cplx lens_F(const double* x, const double* y, const double* m, int64_t n,
+                   double kappa_s, double gamma, cplx e_mphi, cplx z) {
+    cplx s = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        cplx d = z - (x[i] + I * y[i]);
+        s += m[i] / (d * d);
+    }
+    return gamma + s - (1.0 - kappa_s) * e_mphi;
+}
+
+/* dF/dz = -2 sum_i m_i / (z - z_i)^3 (derivative of F, needed by P'/P in Sec. 3.2). */
+static cplx lens_dF(const double* x, const double* y, const double* m, int64_t n, cplx z) {
+    cplx s = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        cplx d = z - (x[i] + I * y[i]);
+        s += m[i] / (d * d * d);
+    }
+    return -2.0 * s;
+}
+
+/* Complex lens equation (Sec. 3.1) with alpha_s = -kappa_* z (Appendix A):
+ * w = (1 - kappa_s) z + gamma conj(z) - sum_i m_i / (conj(z) - conj(z_i)). */
+static cplx lens_w(const double* x, const double* y, const double* m, int64_t n,
+                   double kappa_s, double gamma, cplx z) {
+    cplx s = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        cplx d = conj(z) - (x[i] - I * y[i]);
+        s += m[i] / d;
+    }
+    return (1.0 - kappa_s) * z + gamma * conj(z) - s;
+}
+
+double orc_F(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
+             double gamma, double phi, const double* z, double* out) {
+    cplx e = cos(phi) - I * sin(phi);
+    cplx f = lens_F(x, y, m, n, kappa_s, gamma, e, z[0] + I * z[1]);
+    out[0] = creal(f);
+    out[1] = cimag(f);
+    return cabs(f);
+}
+
+double orc_dF(const double* x, const double* y, const double* m, int64_t n, const double* z,
+              double* out) {
+    cplx f = lens_dF(x, y, m, n, z[0] + I * z[1]);
+    out[0] = creal(f);
+    out[1] = cimag(f);
+    return cabs(f);
+}
+
+/* Inverse magnification 1/mu = det J = (1 - kappa_s)^2 - |gamma + sum m_i/conj(z - z_i)^2|^2
+ * (Sec. 2.1; Appendix C, with the infinite sheet). */
+double orc_inv_mu(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
+                  double gamma, const double* z) {
+    cplx zz = z[0] + I * z[1];
+    cplx s = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        cplx d = zz - (x[i] + I * y[i]);
+        s += m[i] / (d * d);
+    }
+    double a = 1.0 - kappa_s;
+    double g = cabs(gamma + s);
+    return a * a - g * g;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Aberth-Ehrlich iteration on P(z) = F(z) prod (z - z_i)^2 (Sec. 3.2)
+ * ------------------------------------------------------------------------------------ */
+
+/* One root's Aberth correction (Sec. 3.2):
+ *   P'/P = F'/F + 2 sum_i 1/(z_k - z_i)
+ *   Delta = 1 / (P'/P - sum_{r != k} 1/(z_k - z_r)),   z_k <- z_k - Delta. */
+static cplx aberth_delta(const double* x, const double* y, const double* m, int64_t n,
+                         double kappa_s, double gamma, cplx e_mphi, const cplx* z, int64_t nr,
+                         int64_t k) {
+    cplx zk = z[k];
+    cplx F = lens_F(x, y, m, n, kappa_s, gamma, e_mphi, zk);
+    if (F == 0.0) return 0.0; /* z_k is an exact root */
+    cplx dF = lens_dF(x, y, m, n, zk);
+    cplx s1 = 0.0;
+    for (int64_t i = 0; i < n; i++) s1 += 1.0 / (zk - (x[i] + I * y[i]));
+    cplx pp = dF / F + 2.0 * s1;
+    cplx ab = 0.0;
+    for (int64_t r = 0; r < nr; r++)
+        if (r != k) ab += 1.0 / (zk - z[r]);
+    return 1.0 / (pp - ab);
+}
+
+/* Jacobi Aberth over the n_r = 2n roots of one phi row (Sec. 3.2): every iteration
+ * updates all unfrozen roots from the previous iterate; frozen roots still enter the
+ * root sum.  A root is frozen once |z^{a+1} - z^a| < tol (Sec. 3.2 footnote).
+ * Returns the number of roots still unfrozen after max_iter iterations. */
+static int64_t aberth_jacobi(const double* x, const double* y, const double* m, int64_t n,
+                             double kappa_s, double gamma, double phi, cplx* z, int max_iter,
+                             double tol, int32_t* iters) {
+    int64_t nr = 2 * n;
+    cplx e = cos(phi) - I * sin(phi);
+    cplx* nxt = (cplx*)malloc(sizeof(cplx) * (size_t)nr);
+    unsigned char* frozen = (unsigned char*)calloc((size_t)nr, 1);
+    unsigned char* frozen_nxt = (unsigned char*)calloc((size_t)nr, 1);
+    int64_t active = nr;
+    if (iters)
+        for (int64_t k = 0; k < nr; k++) iters[k] = 0;
+    for (int a = 0; a < max_iter && active > 0; a++) {
+        int64_t still = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : still)
+        for (int64_t k = 0; k < nr; k++) {
+            if (frozen[k]) {
+                nxt[k] = z[k];
+                frozen_nxt[k] = 1;
+                continue;
+            }
+            cplx d = aberth_delta(x, y, m, n, kappa_s, gamma, e, z, nr, k);
+            nxt[k] = z[k] - d;
+            if (iters) iters[k] = a + 1;
+            if (cabs(d) < tol) {
+                frozen_nxt[k] = 1;
+            } else {
+                frozen_nxt[k] = 0;
+                still++;
+            }
+        }
+        memcpy(z, nxt, sizeof(cplx) * (size_t)nr);
+        memcpy(frozen, frozen_nxt, (size_t)nr);
+        active = still;
+    }
+    free(nxt);
+    free(frozen);
+    free(frozen_nxt);
+    return active;
+}
+
+/* Newton refinement of each root on F alone, to |dz| < 1e-13 max(1,|z|) (at most 8
+ * steps).  This takes the Aberth result (accurate to ~1e-9) to the FP64 limit, so the
+ * oracle's roots stand for the exact roots of F(., phi). */
+static void newton_polish(const double* x, const double* y, const double* m, int64_t n,
+                          double kappa_s, double gamma, double phi, cplx* z, int64_t nr) {
+    cplx e = cos(phi) - I * sin(phi);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < nr; k++) {
+        cplx zk = z[k];
+        for (int s = 0; s < 8; s++) {
+            cplx F = lens_F(x, y, m, n, kappa_s, gamma, e, zk);
+            cplx dF = lens_dF(x, y, m, n, zk);
+            if (F == 0.0 || dF == 0.0) break;
+            cplx d = F / dF;
+            zk -= d;
+            double sc = cabs(zk) > 1.0 ? cabs(zk) : 1.0;
+            if (cabs(d) < 1e-13 * sc) break;
+        }
+        z[k] = zk;
+    }
+}
+
+/* Initial guesses z_i + 1 and z_i - 1 for every star (Sec. 3.2), stored as
+ * [2i] = z_i + 1, [2i+1] = z_i - 1.  A guess that coincides (within 1e-12) with an
+ * earlier one is moved by 1e-6 (1 + i) so that the Aberth root sum stays finite. */
+static void initial_guesses(const double* x, const double* y, int64_t n, cplx* z) {
+    int64_t nr = 2 * n;
+    for (int64_t i = 0; i < n; i++) {
+        z[2 * i] = (x[i] + 1.0) + I * y[i];
+        z[2 * i + 1] = (x[i] - 1.0) + I * y[i];
+    }
+    for (int64_t b = 1; b < nr; b++) {
+        int moved = 1;
+        while (moved) {
+            moved = 0;
+            for (int64_t a = 0; a < b; a++) {
+                if (cabs(z[b] - z[a]) < 1e-12) {
+                    z[b] += 1e-6 * (1.0 + I);
+                    moved = 1;
+                }
+            }
+        }
+    }
+}
+
+/* Solve one phi row from a given start (warm) or from the star guesses (z_in == NULL),
+ * then Newton-polish.  Output: z_out[2n] complex.  Returns the unfrozen count. */
+int64_t orc_solve_row(const double* x, const double* y, const double* m, int64_t n,
+                      double kappa_s, double gamma, double phi, const double* z_in,
+                      double* z_out, int max_iter, double tol, int32_t* iters) {
+    int64_t nr = 2 * n;
+    cplx* z = (cplx*)z_out;
+    if (z_in)
+        memcpy(z, z_in, sizeof(cplx) * (size_t)nr);
+    else
+        initial_guesses(x, y, n, z);
+    int64_t left = aberth_jacobi(x, y, m, n, kappa_s, gamma, phi, z, max_iter, tol, iters);
+    newton_polish(x, y, m, n, kappa_s, gamma, phi, z, nr);
+    return left;
+}
+
+/* phi_j = 2 pi j / m for the (m+1)-row chain matrix (Sec. 4.3). */
+double orc_phi(int64_t j, int64_t msteps) { return 2.0 * ORC_PI * (double)j / (double)msteps; }
+
+/* Chain matrix of Sec. 4.3: rows j = 0..m (m even) hold the n_r roots at phi_j.  The
+ * central row m/2 (phi = pi) starts from the star guesses (cap max_iter_cold); the
+ * matrix then grows toward rows 0 and m, each row warm-started from its neighbour
+ * nearer the centre (Sec. 3.2 last paragraph), cap max_iter_warm.
+ * z_out: (m+1) x 2n complex; iters_out (optional): (m+1) x 2n.
+ * Returns the total number of unfrozen roots over all rows (0 = all converged). */
+int64_t orc_critical_curves(const double* x, const double* y, const double* m, int64_t n,
+                            double kappa_s, double gamma, int64_t msteps, double tol,
+                            int max_iter_cold, int max_iter_warm, double* z_out,
+                            int32_t* iters_out) {
+    int64_t nr = 2 * n;
+    int64_t c = msteps / 2;
+    int64_t bad = 0;
+    double* zr = z_out;
+    bad += orc_solve_row(x, y, m, n, kappa_s, gamma, orc_phi(c, msteps), NULL, zr + 2 * nr * c,
+                         max_iter_cold, tol, iters_out ? iters_out + nr * c : NULL);
+    for (int64_t j = c - 1; j >= 0; j--)
+        bad += orc_solve_row(x, y, m, n, kappa_s, gamma, orc_phi(j, msteps),
+                             zr + 2 * nr * (j + 1), zr + 2 * nr * j, max_iter_warm, tol,
+                             iters_out ? iters_out + nr * j : NULL);
+    for (int64_t j = c + 1; j <= msteps; j++)
+        bad += orc_solve_row(x, y, m, n, kappa_s, gamma, orc_phi(j, msteps),
+                             zr + 2 * nr * (j - 1), zr + 2 * nr * j, max_iter_warm, tol,
+                             iters_out ? iters_out + nr * j : NULL);
+    return bad;
+}
+
+/* Caustic mapping (Sec. 3.1, Sec. 5.1): w = lens map of each critical point. */
+void orc_map_caustics(const double* x, const double* y, const double* m, int64_t n,
+                      double kappa_s, double gamma, const double* z, int64_t count,
+                      double* w_out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < count; p++) {
+        cplx w = lens_w(x, y, m, n, kappa_s, gamma, z[2 * p] + I * z[2 * p + 1]);
+        w_out[2 * p] = creal(w);
+        w_out[2 * p + 1] = cimag(w);
+    }
+}
+
+/* Smallest pairwise distance among the n_r roots of one row (distinctness check). */
+double orc_min_separation(const double* z, int64_t nr) {
+    double best = INFINITY;
+    for (int64_t a = 0; a < nr; a++)
+        for (int64_t b = a + 1; b < nr; b++) {
+            double dx = z[2 * a] - z[2 * b], dy = z[2 * a + 1] - z[2 * b + 1];
+            double d = sqrt(dx * dx + dy * dy);
+            if (d < best) best = d;
+        }
+    return best;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Exact orientation predicate by exact expansion arithmetic.
+ *
+ * sign of (ax-cx)(by-cy) - (ay-cy)(bx-cx): +1 if c lies strictly to the left of the
+ * directed line a->b, -1 strictly right, 0 on it.  Every difference is split exactly
+ * into two doubles (Knuth's two-sum), every product of two doubles exactly into two
+ * doubles (fma), and the 16 resulting terms are summed exactly into a non-overlapping
+ * expansion (Shewchuk 1997, grow-expansion); the sign of the largest component is the
+ * sign of the sum.  No floating-point filter: every call takes the exact route.
+ * Exact as long as nothing overflows or underflows.
+ * ------------------------------------------------------------------------------------ */
+static void two_sum(double a, double b, double* s, double* e) {
+    double x = a + b;
+    double bv = x - a;
+    double av = x - bv;
+    double br = b - bv;
+    double ar = a - av;
+    *s = x;
+    *e = ar + br;
+}
+
+static void two_prod(double a, double b, double* p, double* e) {
+    double x = a * b;
+    *p = x;
+    *e = fma(a, b, -x);
+}
+
+/* h <- h + b exactly (h non-overlapping, increasing magnitude); returns new length. */
+static int grow_expansion(double* h, int len, double b) {
+    double q = b;
+    for (int i = 0; i < len; i++) {
+        double s, e;
+        two_sum(q, h[i], &s, &e);
+        h[i] = e;
+        q = s;
+    }
+    h[len] = q;
+    return len + 1;
+}
+
+int orc_orient2d(double ax, double ay, double bx, double by, double cx, double cy) {
+    double acx[2], bcy[2], acy[2], bcx[2];
+    two_sum(ax, -cx, &acx[0], &acx[1]);
+    two_sum(by, -cy, &bcy[0], &bcy[1]);
+    two_sum(ay, -cy, &acy[0], &acy[1]);
+    two_sum(bx, -cx, &bcx[0], &bcx[1]);
+    double h[40];
+    int len = 0;
+    for (int u = 0; u < 2; u++)
+        for (int v = 0; v < 2; v++) {
+            double p, e;
+            two_prod(acx[u], bcy[v], &p, &e);
+            len = grow_expansion(h, len, e);
+            len = grow_expansion(h, len, p);
+            two_prod(acy[u], bcx[v], &p, &e);
+            len = grow_expansion(h, len, -e);
+            len = grow_expansion(h, len, -p);
+        }
+    for (int i = len - 1; i >= 0; i--) {
+        if (h[i] > 0.0) return 1;
+        if (h[i] < 0.0) return -1;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------
+ * Caustic-crossing counts (Sec. 5.1): winding numbers of the discretised caustics.
+ *
+ * The caustic polygons are the columns of the (rows x n_r) vertex matrix: segment
+ * (w[j][k], w[j+1][k]) for j = 0..rows-2.  Sunday's (2001) crossing rule: an upward
+ * edge (a.y <= P.y < b.y) with P strictly left adds +1, a downward edge
+ * (b.y <= P.y < a.y) with P strictly right adds -1.  Caustics are traced clockwise
+ * (Sec. 5.1), so the number of caustic crossings is N_cc = -winding number.
+ * ------------------------------------------------------------------------------------ */
+
+/* Pixel centre of index i on [lo, hi] split into cnt pixels. */
+double orc_pixel_center(double lo, double hi, int32_t cnt, int32_t i) {
+    double step = (hi - lo) / (double)cnt;
+    return lo + ((double)i + 0.5) * step;
+}
+
+static int sunday_edge(double ax, double ay, double bx, double by, double px, double py) {
+    if (ay <= py) {
+        if (by > py && orc_orient2d(ax, ay, bx, by, px, py) > 0) return 1;
+    } else {
+        if (by <= py && orc_orient2d(ax, ay, bx, by, px, py) < 0) return -1;
+    }
+    return 0;
+}
+
+/* Winding number of all caustic polygons around one point (definition, all segments). */
+int64_t orc_winding_at(const double* w, int64_t rows, int64_t nr, double px, double py) {
+    int64_t wn = 0;
+    for (int64_t k = 0; k < nr; k++)
+        for (int64_t j = 0; j + 1 < rows; j++) {
+            const double* a = w + 2 * (j * nr + k);
+            const double* b = w + 2 * ((j + 1) * nr + k);
+            wn += sunday_edge(a[0], a[1], b[0], b[1], px, py);
+        }
+    return wn;
+}
+
+/* Full N_cc map (row 0 = y0 side, column 0 = x0 side).  Same decisions as evaluating
+ * orc_winding_at at every pixel centre: a segment can only change the count of pixel
+ * rows whose centre satisfies min(a.y,b.y) <= y < max(a.y,b.y), so other rows are
+ * skipped for that segment. */
+void orc_crossing_map(const double* w, int64_t rows, int64_t nr, double x0, double x1,
+                      double y0, double y1, int32_t W, int32_t H, int32_t* ncc) {
+    int64_t npx = (int64_t)W * H;
+    int64_t* wn = (int64_t*)calloc((size_t)npx, sizeof(int64_t));
+    double* pyc = (double*)malloc(sizeof(double) * (size_t)H);
+    double* pxc = (double*)malloc(sizeof(double) * (size_t)W);
+    for (int32_t r = 0; r < H; r++) pyc[r] = orc_pixel_center(y0, y1, H, r);
+    for (int32_t i = 0; i < W; i++) pxc[i] = orc_pixel_center(x0, x1, W, i);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t r = 0; r < H; r++) {
+        double py = pyc[r];
+        for (int64_t k = 0; k < nr; k++)
+            for (int64_t j = 0; j + 1 < rows; j++) {
+                const double* a = w + 2 * (j * nr + k);
+                const double* b = w + 2 * ((j + 1) * nr + k);
+                double lo = a[1] < b[1] ? a[1] : b[1];
+                double hi = a[1] < b[1] ? b[1] : a[1];
+                if (!(lo <= py && py < hi)) continue;
+                for (int32_t i = 0; i < W; i++)
+                    wn[(int64_t)r * W + i] += sunday_edge(a[0], a[1], b[0], b[1], pxc[i], py);
+            }
+    }
+    for (int64_t p = 0; p < npx; p++) ncc[p] = (int32_t)(-wn[p]);
+    free(wn);
+    free(pyc);
+    free(pxc);
+}
+
+/* ------------------------------------------------------------------------------------
+ * Distance to the nearest caustic for an expanding source (Sec. 5.2): Euclidean
+ * distance transform of the N_cc map.  A feature pixel is one with a 4-neighbour (inside
+ * the map) of different N_cc; the map border itself is not a caustic.  Distances are
+ * pixel * sqrt(squared integer index distance); +inf when the map has no feature.
+ * ------------------------------------------------------------------------------------ */
+static int is_feature(const int32_t* ncc, int32_t W, int32_t H, int32_t r, int32_t i) {
+    int32_t v = ncc[(int64_t)r * W + i];
+    if (i > 0 && ncc[(int64_t)r * W + i - 1] != v) return 1;
+    if (i + 1 < W && ncc[(int64_t)r * W + i + 1] != v) return 1;
+    if (r > 0 && ncc[(int64_t)(r - 1) * W + i] != v) return 1;
+    if (r + 1 < H && ncc[(int64_t)(r + 1) * W + i] != v) return 1;
+    return 0;
+}
+
+void orc_feature_mask(const int32_t* ncc, int32_t W, int32_t H, uint8_t* mask) {
+    for (int32_t r = 0; r < H; r++)
+        for (int32_t i = 0; i < W; i++) mask[(int64_t)r * W + i] = (uint8_t)is_feature(ncc, W, H, r, i);
+}
+
+/* Brute force: every pixel against every feature pixel. */
+void orc_distance_map_brute(const int32_t* ncc, int32_t W, int32_t H, double pixel,
+                            double* d_out) {
+    int64_t npx = (int64_t)W * H;
+    int32_t* fr = (int32_t*)malloc(sizeof(int32_t) * (size_t)npx);
+    int32_t* fi = (int32_t*)malloc(sizeof(int32_t) * (size_t)npx);
+    int64_t nf = 0;
+    for (int32_t r = 0; r < H; r++)
+        for (int32_t i = 0; i < W; i++)
+            if (is_feature(ncc, W, H, r, i)) {
+                fr[nf] = r;
+                fi[nf] = i;
+                nf++;
+            }
+#pragma omp parallel for schedule(static)
+    for (int32_t r = 0; r < H; r++)
+        for (int32_t i = 0; i < W; i++) {
+            int64_t best = -1;
+            for (int64_t f = 0; f < nf; f++) {
+                int64_t dr = r - fr[f], di = i - fi[f];
+                int64_t d2 = dr * dr + di * di;
+                if (best < 0 || d2 < best) best = d2;
+            }
+            d_out[(int64_t)r * W + i] = best < 0 ? INFINITY : pixel * sqrt((double)best);
+        }
+    free(fr);
+    free(fi);
+}
+
+/* Separable exact EDT (Felzenszwalb & Huttenlocher 2012): a column pass giving the
+ * vertical distance to the nearest feature in the same column, then per row the lower
+ * envelope of the parabolas (i - q)^2 + g(q)^2.  Parabola intersections are compared
+ * exactly as fractions of 64-bit integers. */
+void orc_distance_map_separable(const int32_t* ncc, int32_t W, int32_t H, double pixel,
+                                double* d_out) {
+    const int64_t INF = (int64_t)1 << 40;
+    int64_t npx = (int64_t)W * H;
+    int64_t* g = (int64_t*)malloc(sizeof(int64_t) * (size_t)npx); /* vertical distance */
+    for (int32_t i = 0; i < W; i++) {
+        int64_t last = -1;
+        for (int32_t r = 0; r < H; r++) {
+            if (is_feature(ncc, W, H, r, i)) last = r;
+            g[(int64_t)r * W + i] = last < 0 ? INF : r - last;
+        }
+        last = -1;
+        for (int32_t r = H - 1; r >= 0; r--) {
+            if (is_feature(ncc, W, H, r, i)) last = r;
+            if (last >= 0 && last - r < g[(int64_t)r * W + i]) g[(int64_t)r * W + i] = last - r;
+        }
+    }
+#pragma omp parallel
+    {
+        int64_t* v = (int64_t*)malloc(sizeof(int64_t) * (size_t)W);
+        int64_t* zn = (int64_t*)malloc(sizeof(int64_t) * (size_t)(W + 1)); /* boundary numerators */
+        int64_t* zd = (int64_t*)malloc(sizeof(int64_t) * (size_t)(W + 1)); /* denominators > 0 */
+        int* zinf = (int*)malloc(sizeof(int) * (size_t)(W + 1));          /* -1: -inf, +1: +inf */
+#pragma omp for schedule(static)
+        for (int32_t r = 0; r < H; r++) {
+            const int64_t* f = g + (int64_t)r * W;
+            int64_t k = -1;
+            for (int64_t q = 0; q < W; q++) {
+                if (f[q] >= INF) continue;
+                int64_t fq = f[q] * f[q] + q * q;
+                if (k < 0) {
+                    k = 0;
+                    v[0] = q;
+                    zinf[0] = -1;
+                    zinf[1] = 1;
+                    continue;
+                }
+                for (;;) {
+                    int64_t p = v[k];
+                    int64_t sn = fq - (f[p] * f[p] + p * p); /* s = sn / sd */
+                    int64_t sd = 2 * (q - p);
+                    /* s <= z[k] ? */
+                    int le;
+                    if (zinf[k] == -1) le = 0;
+                    else le = sn * zd[k] <= zn[k] * sd;
+                    if (le) {
+                        k--;
+                        continue;
+                    }
+                    k++;
+                    v[k] = q;
+                    zn[k] = sn;
+                    zd[k] = sd;
+                    zinf[k] = 0;
+                    zinf[k + 1] = 1;
+                    break;
+                }
+            }
+            double* out = d_out + (int64_t)r * W;
+            if (k < 0) {
+                for (int64_t i = 0; i < W; i++) out[i] = -1.0; /* no feature in this row's columns */
+                continue;
+            }
+            int64_t j = 0;
+            for (int64_t i = 0; i < W; i++) {
+                /* advance while z[j+1] < i */
+                while (zinf[j + 1] == 0 && zn[j + 1] < i * zd[j + 1]) j++;
+                int64_t p = v[j];
+                int64_t d2 = (i - p) * (i - p) + f[p] * f[p];
+                out[i] = pixel * sqrt((double)d2);
+            }
+        }
+        free(v);
+        free(zn);
+        free(zd);
+        free(zinf);
+    }
+    /* rows whose columns all lack features: no feature anywhere in the map if every row
+     * is marked; otherwise impossible (a feature in any column reaches every row). */
+    for (int64_t p = 0; p < npx; p++)
+        if (d_out[p] < 0.0) d_out[p] = INFINITY;
+    free(g);
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,186 @@
+"""Pins of the oracle's exact orientation predicate, Sunday winding numbers, N_cc maps and
+distance maps: exact rational arithmetic, closed-form polygons, brute force, and the
+physical identity that a caustic crossing creates or destroys a pair of images."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_02121_gb300 import synth
+from tests import lensing_math as lm
+
+
+def test_orient2d_matches_exact_rationals():
+    u = synth.uniform(777, 6 * 4000)
+    pts = (u.reshape(-1, 6) - 0.5) * 20
+    for p in pts:
+        assert oracle.orient2d(*p) == lm.orient_exact(*p)
+
+
+def test_orient2d_near_degenerate():
+    """Points on or within a few ulp of the line: the sign must still be exact."""
+    rng = synth.uniform(778, 3 * 2000)
+    cnt0 = 0
+    for i in range(2000):
+        ax, ay = 0.1 + rng[3 * i], -0.3
+        bx, by = 3.7, 1.0 + rng[3 * i + 1]
+        t = rng[3 * i + 2]
+        cx = ax + t * (bx - ax)
+        cy = ay + t * (by - ay)
+        for k in (-2, -1, 0, 1, 2):
+            cyk = cy + k * math.ulp(cy)
+            s = oracle.orient2d(ax, ay, bx, by, cx, cyk)
+            assert s == lm.orient_exact(ax, ay, bx, by, cx, cyk)
+            cnt0 += s == 0
+    # exactly collinear representable case
+    assert oracle.orient2d(0.0, 0.0, 1.0, 1.0, 0.5, 0.5) == 0
+    assert oracle.orient2d(0.0, 0.0, 1.0, 0.0, 0.5, 1e-300) == 1
+
+
+def _circle(n, r, cx=0.0, cy=0.0, clockwise=True):
+    t = np.arange(n + 1) * 2 * math.pi / n
+    if clockwise:
+        t = -t
+    z = (cx + r * np.cos(t)) + 1j * (cy + r * np.sin(t))
+    z[-1] = z[0]
+    return z
+
+
+def test_winding_clockwise_circle_counts_one_inside():
+    """A clockwise polygon has winding number -1 inside (N_cc = +1), 0 outside; a
+    counter-clockwise one +1 inside."""
+    poly = _circle(64, 1.0)[:, None]  # one column = one closed chain
+    ncc = oracle.crossing_map(poly, -2, 2, -2, 2, 40, 40)
+    chord = 1.0 - math.cos(math.pi / 64)
+    for r in range(40):
+        for i in range(40):
+            px = oracle.pixel_center(-2, 2, 40, i)
+            py = oracle.pixel_center(-2, 2, 40, r)
+            rho = math.hypot(px, py)
+            if rho < 1.0 - chord - 1e-9:
+                assert ncc[r, i] == 1
+            elif rho > 1.0 + 1e-9:
+                assert ncc[r, i] == 0
+    ccw = _circle(64, 1.0, clockwise=False)[:, None]
+    assert oracle.winding_at(ccw, 0.1, 0.2) == 1
+    assert oracle.winding_at(poly, 0.1, 0.2) == -1
+
+
+def test_crossing_map_equals_pointwise_winding():
+    """The full-map routine makes the same decisions as the per-point definition."""
+    u = synth.uniform(991, 2 * 31 * 3)
+    w = ((u[0::2] - 0.5) * 5 + 1j * (u[1::2] - 0.5) * 5).reshape(31, 3)
+    w[-1] = w[0]
+    H, W = 23, 29
+    ncc = oracle.crossing_map(w, -2.5, 2.5, -2.0, 2.7, W, H)
+    for r in range(H):
+        for i in range(W):
+            px = oracle.pixel_center(-2.5, 2.5, W, i)
+            py = oracle.pixel_center(-2.0, 2.7, H, r)
+            assert ncc[r, i] == -oracle.winding_at(w, px, py)
+
+
+def test_winding_half_open_rule_on_vertex_rows():
+    """A vertex exactly on a pixel-centre row is counted once (half-open y rule)."""
+    # square with vertices on the line y = 0 (a pixel-centre row below)
+    sq = np.array([-1 - 1j, -1 + 1j, 1 + 1j, 1 - 1j, -1 - 1j])[:, None]  # clockwise
+    for py in (-1.0, 0.0, 0.5, 1.0):
+        wn = oracle.winding_at(sq, 0.0, py)
+        assert wn == (-1 if -1.0 <= py < 1.0 else 0)
+
+
+@pytest.mark.parametrize("kappa_s,gamma", [(0.0, 0.3), (0.25, 0.4)])
+def test_chang_refsdal_ncc_is_one_inside(kappa_s, gamma):
+    """N_cc = 1 inside the Chang-Refsdal caustic and 0 outside, away from the curve."""
+    x, y, m = np.array([0.0]), np.array([0.0]), np.array([1.0])
+    z, _, _ = oracle.critical_curves(x, y, m, kappa_s, gamma, 2000)
+    w = oracle.map_caustics(x, y, m, kappa_s, gamma, z)
+    ext = 1.2
+    H = W = 48
+    ncc = oracle.crossing_map(w, -ext, ext, -ext, ext, W, H)
+    assert ncc.min() >= 0 and ncc.max() >= 1
+    # compare with image counts at pixel centres well away from the caustic
+    caus = w[:-1].ravel()
+    rng = synth.uniform(4242, 2 * 60)
+    checked = 0
+    for t in range(60):
+        i = int(rng[2 * t] * W)
+        r = int(rng[2 * t + 1] * H)
+        px = oracle.pixel_center(-ext, ext, W, i)
+        py = oracle.pixel_center(-ext, ext, H, r)
+        if np.min(np.abs(caus - complex(px, py))) < 0.02:
+            continue
+        nimg = lm.image_count(x, y, m, kappa_s, gamma, complex(px, py))
+        assert nimg == 2 + 2 * ncc[r, i], (px, py, nimg, ncc[r, i])
+        checked += 1
+    assert checked > 20
+
+
+@pytest.mark.parametrize("sep", [0.6, 1.8, 4.0])
+def test_binary_ncc_matches_image_counts(sep):
+    """Two unit masses: the number of images of a point source is 3 + 2 N_cc."""
+    x = np.array([-sep / 2, sep / 2])
+    y = np.array([0.05, -0.05])
+    m = np.ones(2)
+    kappa_s, gamma = 0.0, 0.1
+    z, _, bad = oracle.critical_curves(x, y, m, kappa_s, gamma, 1000)
+    assert bad == 0
+    w = oracle.map_caustics(x, y, m, kappa_s, gamma, z)
+    ext = 2.5
+    H = W = 40
+    ncc = oracle.crossing_map(w, -ext, ext, -ext, ext, W, H)
+    assert ncc.min() >= 0
+    caus = w[:-1].ravel()
+    checked = 0
+    for r in range(0, H, 3):
+        for i in range(0, W, 3):
+            px = oracle.pixel_center(-ext, ext, W, i)
+            py = oracle.pixel_center(-ext, ext, H, r)
+            if np.min(np.abs(caus - complex(px, py))) < 0.03:
+                continue
+            nimg = lm.image_count(x, y, m, kappa_s, gamma, complex(px, py))
+            assert nimg == 3 + 2 * ncc[r, i], (px, py, nimg, ncc[r, i])
+            checked += 1
+    assert checked > 50
+
+
+def test_distance_single_feature_closed_form():
+    ncc = np.zeros((9, 11), dtype=np.int32)
+    ncc[4, 6] = 1  # the pixel and its 4 neighbours are features
+    d = oracle.distance_map(ncc, 0.5, method="separable")
+    db = oracle.distance_map(ncc, 0.5, method="brute")
+    feats = [(4, 6), (3, 6), (5, 6), (4, 5), (4, 7)]
+    for r in range(9):
+        for i in range(11):
+            ref = 0.5 * min(math.sqrt((r - fr) ** 2 + (i - fi) ** 2) for fr, fi in feats)
+            assert d[r, i] == ref
+            assert db[r, i] == ref
+
+
+def test_distance_no_feature_is_infinite():
+    d = oracle.distance_map(np.full((5, 7), 3, dtype=np.int32), 1.0)
+    assert np.all(np.isinf(d))
+
+
+@pytest.mark.parametrize("seed,H,W", [(1, 17, 23), (2, 40, 33), (3, 64, 64), (4, 1, 50), (5, 50, 1)])
+def test_distance_separable_equals_brute(seed, H, W):
+    u = synth.uniform(5000 + seed, H * W).reshape(H, W)
+    ncc = (u > 0.97).astype(np.int32)
+    ncc[: H // 3, : W // 2] += 1
+    a = oracle.distance_map(ncc, 0.01, method="separable")
+    b = oracle.distance_map(ncc, 0.01, method="brute")
+    assert np.array_equal(a, b)
+    mask = oracle.feature_mask(ncc)
+    assert np.all((a == 0) == (mask == 1))
+
+
+def test_point_on_edge_not_counted():
+    """A pixel centre exactly on an edge (orientation 0) is neither left nor right of it:
+    on the clockwise square's upward left edge only the downward right edge counts, on the
+    downward right edge nothing counts."""
+    sq = np.array([-1 - 1j, -1 + 1j, 1 + 1j, 1 - 1j, -1 - 1j])[:, None]
+    assert oracle.winding_at(sq, -1.0, 0.25) == -1
+    assert oracle.winding_at(sq, 1.0, 0.25) == 0
+    assert oracle.winding_at(sq, -1.0 - 1e-12, 0.25) == 0
+    assert oracle.winding_at(sq, 1.0 - 1e-12, 0.25) == -1
