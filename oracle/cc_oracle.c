@@ -214,7 +214,10 @@ static void initial_guesses(const double* x, const double* y, int64_t n, cplx* z
 }
 
 /* Solve one phi row from a given start (warm) or from the star guesses (z_in == NULL),
- * then Newton-polish.  Output: z_out[2n] complex.  Returns the unfrozen count. */
+ * then Newton-polish.  Output: z_out[2n] complex.  Returns the unfrozen count.
+ * A warm start assumes a small phase step (Sec. 3.2); when it does not converge within
+ * max_iter (e.g. a phase step of pi for an isolated star, whose warm start then lies on a
+ * line the iteration never leaves), the row is solved again from the star guesses. */
 int64_t orc_solve_row(const double* x, const double* y, const double* m, int64_t n,
                       double kappa_s, double gamma, double phi, const double* z_in,
                       double* z_out, int max_iter, double tol, int32_t* iters) {
@@ -225,6 +228,10 @@ int64_t orc_solve_row(const double* x, const double* y, const double* m, int64_t
     else
         initial_guesses(x, y, n, z);
     int64_t left = aberth_jacobi(x, y, m, n, kappa_s, gamma, phi, z, max_iter, tol, iters);
+    if (left > 0 && z_in) {
+        initial_guesses(x, y, n, z);
+        left = aberth_jacobi(x, y, m, n, kappa_s, gamma, phi, z, max_iter, tol, iters);
+    }
     newton_polish(x, y, m, n, kappa_s, gamma, phi, z, nr);
     return left;
 }

@@ -24,12 +24,13 @@ def _random_field(n, seed, spread=3.0, mass="unit"):
 def test_chang_refsdal_closed_form(kappa_s, gamma):
     """One star with shear: every row matches z0 +- sqrt(m / ((1-kappa_s)e^{-i phi} - gamma))."""
     x, y, m = np.array([0.7]), np.array([-0.4]), np.array([0.6])
-    z, it, bad = oracle.critical_curves(x, y, m, kappa_s, gamma, 64)
-    assert bad == 0
-    for j in range(65):
-        ref = lm.chang_refsdal_roots(complex(x[0], y[0]), m[0], kappa_s, gamma, oracle.phi(j, 64))
-        err, _ = lm.match_rows(z[j], ref)
-        assert err < 1e-12
+    for msteps in (2, 64):  # m = 2: phase steps of pi, the warm start of Sec. 3.2 stalls
+        z, it, bad = oracle.critical_curves(x, y, m, kappa_s, gamma, msteps)
+        assert bad == 0
+        for j in range(msteps + 1):
+            ref = lm.chang_refsdal_roots(complex(x[0], y[0]), m[0], kappa_s, gamma, oracle.phi(j, msteps))
+            err, _ = lm.match_rows(z[j], ref)
+            assert err < 1e-12
 
 
 @pytest.mark.parametrize("kappa_s,gamma", [(0.0, 0.2), (0.3, 0.5), (0.0, 1.3)])
