@@ -1,0 +1,190 @@
+/*
+ * cc.h -- C ABI of libccgpu: microlensing critical curves, caustics, caustic-crossing
+ * maps and distance-to-caustic maps on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Weisenbach (2025), "A GPU Code for Finding Microlensing Critical Curves and
+ * Caustics".  Units: theta_* = 1 (Einstein radius of a unit mass).  Lens model: N point
+ * masses (x_i, y_i, m_i), smooth convergence kappa_s and external shear gamma, with the
+ * compensating mass sheet extended to infinity (Appendix A), so
+ *     w(z)     = (1 - kappa_s) z + gamma conj(z) - sum_i m_i / conj(z - z_i)     (Sec. 3.1)
+ *     F(z,phi) = gamma + sum_i m_i / (z - z_i)^2 - (1 - kappa_s) e^{-i phi}      (Sec. 3.1)
+ * and for every phase phi the n_r = 2N critical points are the roots of F(., phi)
+ * (Sec. 3.1, rationalised polynomial P = F prod (z - z_i)^2).
+ *
+ * Conventions for every call
+ *   - Return value: a cc_status (CC_OK = 0).  On error, cc_last_error() gives a message
+ *     (thread-local, valid until the next call on the same thread).
+ *   - Complex arrays are interleaved (re, im) pairs of IEEE doubles (complex128).
+ *   - Device buffers are allocated and owned by the caller; the library never frees
+ *     them.  Unless stated otherwise, pointers are device pointers on the field's device.
+ *   - Calls taking a stream enqueue work on it and return without waiting; results are
+ *     valid once the stream has reached that point.  A NULL stream is the legacy default
+ *     stream.  cc_stream_t is binary-compatible with cudaStream_t.
+ *   - The library allocates device memory only in cc_field_create (a few arrays of N
+ *     entries, freed by cc_field_destroy); every other call works in caller memory.
+ */
+#ifndef CC_H_
+#define CC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cc_stream_t;
+typedef struct cc_field cc_field;
+
+typedef enum cc_status {
+    CC_OK = 0,
+    CC_EINVAL = 1,       /* bad argument (NULL pointer, odd m, size out of range, ...) */
+    CC_ENOMEM = 2,       /* device allocation failed (cc_field_create) or workspace too small */
+    CC_ENOCONV = 3,      /* reported by cc_field_report: some roots did not converge */
+    CC_EDEGENERATE = 4,  /* |1 - kappa_s - gamma| < 1e-12: a root runs to infinity at phi = 0 */
+    CC_ECUDA = 5,        /* a CUDA runtime call failed (message has the CUDA error string) */
+    CC_ETIMEOUT = 6      /* a device-side bounded wait gave up (status written, no hang) */
+} cc_status;
+
+/* Arithmetic of the root tracer (Sec. 3.2 iteration, Sec. 4.4 runtime). */
+typedef enum cc_precision {
+    /* Aberth-Ehrlich in FP32 (compensated, cascaded star sums), then a certified
+     * high-precision Newton polish on F fused with the caustic mapping. */
+    CC_MIXED = 0,
+    /* Aberth-Ehrlich entirely in FP64 with the |dz| < tol_abs stop rule, as in the
+     * paper's double-precision code; caustics by a separate FP64 lens-map pass. */
+    CC_FP64 = 1
+} cc_precision;
+
+/* Arithmetic of the polish / caustic-mapping star sums. */
+typedef enum cc_hp_arith {
+    CC_HP_DFLOAT = 0, /* double-float (pairs of FP32, ~48-bit significand) on the FP32 pipes */
+    CC_HP_FP64 = 1    /* native FP64 */
+} cc_hp_arith;
+
+typedef struct cc_options {
+    double tol_abs;      /* freeze a root when |z^{a+1} - z^a| < tol_abs (Sec. 3.2 footnote: 1e-9) */
+    double mu_max;       /* also freeze when |mu| > mu_max (Sec. 3.2 footnote: 1e9); 0 = off.
+                            Used by CC_FP64 only; the mixed form never freezes on |mu|. */
+    double tol_cert;     /* polish stops when the estimated Newton error < tol_cert (2e-11) */
+    int32_t max_iter_cold; /* Aberth iteration cap at a subchain's centre row (500) */
+    int32_t max_iter_warm; /* cap for warm-started rows (200) */
+    int32_t max_polish;    /* polish passes per point (4) */
+    int32_t precision;     /* cc_precision */
+    int32_t hp_arith;      /* cc_hp_arith (polish and cc_map_caustics) */
+    int32_t subchains;     /* phi sub-ranges grown in parallel (Sec. 4.3); 0 = automatic */
+    int32_t predictor;     /* 1: warm start by linear extrapolation of the last two rows; 0: copy
+                              the previous row (Sec. 3.2 last paragraph) */
+    int32_t block_threads; /* threads per tracing CTA (0 = automatic) */
+} cc_options;
+
+/* Solve statistics of the last cc_critical_curves on a field (host copy). */
+typedef struct cc_report {
+    int64_t rows;              /* m + 1 */
+    int64_t n_roots;           /* n_r = 2N */
+    int64_t subchains;         /* sub-ranges used */
+    int64_t root_iterations;   /* Aberth updates executed (all rows, all roots) */
+    int64_t cold_root_iterations; /* of which at the subchain centre rows */
+    int64_t unconverged;       /* root-rows that hit the Aberth cap */
+    int64_t polish_passes;     /* star-sum passes of the polish (all points) */
+    int64_t uncertified;       /* points whose final error estimate exceeds tol_cert */
+    int64_t seam_ambiguous;    /* sub-range joins that were not a clean 1:1 match */
+    int32_t max_iter_row;      /* largest per-root iteration count in any row */
+    int32_t timeout;           /* nonzero if a bounded device wait gave up */
+    double max_err_est;        /* largest polish error estimate (theta_*) */
+    /* Device time of each stage of the last solve (CUDA events on the caller's stream):
+     * tracing (Aberth), joining sub-ranges, polish + caustics (mixed form) or
+     * reordering + caustics (FP64 form). */
+    float trace_ms, join_ms, polish_ms;
+} cc_report;
+
+/* Fill *opt with the defaults listed above. */
+int cc_options_default(cc_options* opt);
+
+/* Create a field on the current CUDA device.
+ *   x, y, mass: n star positions and masses, FP64, host OR device pointers (copied in).
+ *   kappa_s: smooth convergence (Sec. 2.1 with Appendix A: 1 - kappa - dalpha_s/dz
+ *            = 1 - kappa_s); gamma >= 0: shear (Sec. 2.1).
+ *   opt: NULL for defaults.
+ * Errors: CC_EINVAL (n < 1, NULL pointer, non-finite value, mass <= 0),
+ *         CC_EDEGENERATE (|1 - kappa_s - gamma| < 1e-12), CC_ENOMEM, CC_ECUDA.
+ * Blocks until the stars are on the device. */
+int cc_field_create(const double* x, const double* y, const double* mass, int64_t n,
+                    double kappa_s, double gamma, const cc_options* opt, cc_field** out);
+
+/* Free the field's device arrays.  NULL is accepted. */
+int cc_field_destroy(cc_field* field);
+
+/* Number of stars and roots (n_r = 2N, Sec. 3.1) of a field. */
+int cc_field_size(const cc_field* field, int64_t* n_stars, int64_t* n_roots);
+
+/* Device scratch bytes that cc_critical_curves needs for m phi steps. */
+int cc_critical_curves_workspace_bytes(const cc_field* field, int64_t m, size_t* bytes);
+
+/* Critical curves on the phi grid phi_j = 2 pi j / m, j = 0..m (Sec. 3.1, chain matrix of
+ * Sec. 4.3; m even, >= 2).  Roots are found by simultaneous Aberth-Ehrlich iteration
+ * (Sec. 3.2) from the z_i +- 1 guesses at the centre of each phi sub-range, then grown
+ * row by row toward both ends of the sub-range, each row warm-started from its
+ * neighbour (Secs. 3.2, 4.3).  Sub-ranges are joined so that column k of every row
+ * follows one chain.
+ *   z_out:     (m+1) x n_r complex128, row j holds the roots at phi_j (device).
+ *   w_out:     optional (NULL to skip), same layout: the caustic point w(z) of each root
+ *              (Sec. 5.1), computed in the same pass as the polish.
+ *   iters_out: optional (NULL to skip), (m+1) x n_r int32: Aberth iterations per root.
+ *   workspace: device scratch of at least cc_critical_curves_workspace_bytes bytes,
+ *              256-byte aligned; its contents on entry do not matter.
+ * Errors: CC_EINVAL (odd/small m, NULL z_out or workspace, misaligned or too small
+ *         workspace), CC_ECUDA.  Convergence problems are not errors of this call: see
+ *         cc_field_report. */
+int cc_critical_curves(cc_field* field, int64_t m, double* z_out, double* w_out,
+                       int32_t* iters_out, void* workspace, size_t workspace_bytes,
+                       cc_stream_t stream);
+
+/* Wait for the field's last cc_critical_curves and copy its statistics.  Returns CC_OK,
+ * CC_ENOCONV if any root-row hit the iteration cap or any point is uncertified, or
+ * CC_ETIMEOUT if a device-side wait gave up. */
+int cc_field_report(cc_field* field, cc_report* out);
+
+/* Caustic points (Sec. 3.1 lens equation, Sec. 5.1): w_out[p] = w(z[p]) for count points.
+ * z, w_out: count complex128 (device).  Arithmetic follows the field's hp_arith option.
+ * Errors: CC_EINVAL, CC_ECUDA. */
+int cc_map_caustics(cc_field* field, const double* z, int64_t count, double* w_out,
+                    cc_stream_t stream);
+
+/* Number of caustic crossings N_cc on a W x H source-plane grid (Sec. 5.1): minus the
+ * winding number (Sunday's crossing rule, exact orientation predicate) of the caustic
+ * polygons, which are the columns of the rows x n_r vertex matrix w (segment
+ * (w[j][k], w[j+1][k]) for j = 0..rows-2).  Pixel centres are
+ *   x_i = x0 + (i + 0.5) * ((x1 - x0) / W),  y_r = y0 + (r + 0.5) * ((y1 - y0) / H)
+ * in IEEE FP64 without fused multiply-add.  A segment counts for pixel centres with
+ * min(a.y, b.y) <= y < max(a.y, b.y) lying strictly left (upward) / right (downward).
+ *   w: rows x n_r complex128 (device).  ncc_out: H x W int32, row 0 at y0 (device).
+ * Errors: CC_EINVAL (W, H < 1, x1 <= x0, y1 <= y0, rows < 1, NULL), CC_ECUDA. */
+int cc_crossing_map(const double* w, int64_t rows, int64_t n_r, double x0, double x1, double y0,
+                    double y1, int32_t W, int32_t H, int32_t* ncc_out, cc_stream_t stream);
+
+/* Device scratch bytes that cc_distance_map needs for a W x H map. */
+int cc_distance_map_workspace_bytes(int32_t W, int32_t H, size_t* bytes);
+
+/* Distance from each pixel to the nearest caustic for an expanding source (Sec. 5.2):
+ * the exact Euclidean distance transform of the N_cc map.  A caustic (feature) pixel
+ * has a 4-neighbour inside the map with a different N_cc; the map border is not a
+ * caustic.  d_out[p] = pixel * sqrt(squared index distance to the nearest feature);
+ * +inf if the map has no feature.
+ *   ncc: H x W int32 (device).  d_out: H x W double (device).
+ *   workspace: >= cc_distance_map_workspace_bytes, 256-byte aligned (device).
+ * Errors: CC_EINVAL, CC_ECUDA. */
+int cc_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, double* d_out,
+                    void* workspace, size_t workspace_bytes, cc_stream_t stream);
+
+/* Last error message of this thread ("" if none). */
+const char* cc_last_error(void);
+
+/* Library version string. */
+const char* cc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_H_ */

@@ -1,0 +1,551 @@
+// Critical-curve tracer: simultaneous Aberth-Ehrlich iteration on the roots of
+// P(z) = F(z, phi) prod_i (z - z_i)^2 (Sec. 3.2), grown along the phi grid from the centre
+// of each phi sub-range toward both of its ends (Sec. 4.3), each row warm-started from its
+// neighbour (Sec. 3.2).
+//
+// One CTA owns one sub-range ("subchain") for the whole launch: no grid-wide barrier, no
+// host round trip per iteration.  Inside the CTA every Aberth iteration is a Jacobi sweep
+// over the still-active roots of the (one or two) rows being solved:
+//   - active roots are compacted into a list; g lanes (power of two, <= 32) share one root
+//     so that a handful of late roots still keep every lane busy; the g partial sums are
+//     combined by a butterfly of warp shuffles (fixed order: deterministic results);
+//   - star records are staged in shared memory once (resident) or per tile, the current
+//     roots of both rows are streamed through shared memory in tiles;
+//   - per root the star sums  C = sum 1/d,  A = sum m/d^2,  B = sum m/d^3  and the root
+//     sum  D = sum_{r != k} 1/(z_k - z_r)  give  F = gamma + A - (1-kappa_s) e^{-i phi},
+//     F' = -2B,  P'/P = F'/F + 2C  and the update  z_k -= 1/(P'/P - D)  (Sec. 3.2).
+// Two arithmetics: FP32 (the mixed form; its result is polished afterwards) and FP64 (the
+// plain form with the |dz| < tol stop rule of Sec. 3.2).
+#include <float.h>
+
+#include "cc_internal.h"
+
+namespace ccg {
+
+template <typename T>
+struct CT;
+template <>
+struct CT<float> {
+    using C = float2;
+    using Star = float4;
+    static constexpr int TS = 4096;  // stars per shared-memory tile
+};
+template <>
+struct CT<double> {
+    using C = double2;
+    using Star = StarD;
+    static constexpr int TS = 2048;
+};
+constexpr int TR = 1024;  // roots per direction per shared-memory tile
+
+template <typename T>
+struct Acc {
+    T Cx, Cy, Ax, Ay, Bx, By, Dx, Dy;
+};
+
+__device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+// Per-update divisions: the FP32 tracer is polished afterwards, so the hardware reciprocal
+// (about 1 ulp) is enough there; the FP64 tracer divides exactly.
+__device__ __forceinline__ float qdiv(float a, float b) { return a * rcp_approx(b); }
+__device__ __forceinline__ float qsqrt(float a) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+__device__ __forceinline__ double qsqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ double qdiv(double a, double b) { return a / b; }
+
+// One star: d = z - z_i, u = 1/d = conj(d)/|d|^2; C += u, A += m u^2, B += m u^3.
+template <typename T, typename S>
+__device__ __forceinline__ void acc_star(T zx, T zy, const S& s, Acc<T>& a) {
+    T dx = zx - (T)s.x, dy = zy - (T)s.y;
+    T r2 = fma(dx, dx, dy * dy);
+    T inv = recip(r2);
+    T ux = dx * inv, uy = -dy * inv;
+    a.Cx += ux;
+    a.Cy += uy;
+    T tx = fma(ux, ux, -uy * uy);
+    T ty = (ux + ux) * uy;
+    T mx = (T)s.z * tx, my = (T)s.z * ty;
+    a.Ax += mx;
+    a.Ay += my;
+    a.Bx = fma(mx, ux, fma(-my, uy, a.Bx));
+    a.By = fma(mx, uy, fma(my, ux, a.By));
+}
+
+// One other root: D += 1/(z_k - z_r); the root itself (|d| == 0) contributes nothing.
+template <typename T, typename C>
+__device__ __forceinline__ void acc_root(T zx, T zy, const C& r, Acc<T>& a) {
+    T dx = zx - r.x, dy = zy - r.y;
+    T r2 = fma(dx, dx, dy * dy);
+    T inv = r2 > (T)0 ? recip(r2) : (T)0;
+    a.Dx = fma(dx, inv, a.Dx);
+    a.Dy = fma(-dy, inv, a.Dy);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_x(T v, int off) {
+    return __shfl_xor_sync(0xffffffffu, v, off);
+}
+
+struct TK {
+    const void* stars;
+    int n, nr;
+    double kappa_s, gamma;
+    int64_t m;
+    int S;
+    const double2* phase;
+    void* zrows;
+    void* seam;
+    int32_t* iters;
+    char* work;
+    size_t work_stride;
+    DevReport* rep;
+    double tol_abs, mu_max;
+    int max_iter_cold, max_iter_warm, predictor;
+};
+
+template <typename T>
+struct Ctx {
+    using C = typename CT<T>::C;
+    using Star = typename CT<T>::Star;
+    const TK* k;
+    Star* s_star;
+    C* s_root;  // [2][TR]
+    C *cur, *nxt, *prev;
+    float* dprev;
+    int *conv, *it, *act;
+    bool resident;
+};
+
+// Run Jacobi Aberth sweeps on the active rows (dir 0: row0, dir 1: row1) until every root
+// is frozen or max_iter sweeps were made.  Called by all threads of the CTA.
+template <typename T>
+__device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int64_t row0, int64_t row1,
+                                          int max_iter, bool cold, bool report, int* s_count, int* s_maxit) {
+    using C = typename CT<T>::C;
+    constexpr int TS = CT<T>::TS;
+    const TK& K = *x.k;
+    const int tid = threadIdx.x, P = blockDim.x;
+    const int nr = K.nr, n = K.n;
+    const T oms = (T)(1.0 - K.kappa_s);
+    const T gam = (T)K.gamma;
+    T cph0 = 0, sph0 = 0, cph1 = 0, sph1 = 0;
+    if (a0) {
+        double2 ph = K.phase[row0];
+        cph0 = (T)ph.x;
+        sph0 = (T)ph.y;
+    }
+    if (a1) {
+        double2 ph = K.phase[row1];
+        cph1 = (T)ph.x;
+        sph1 = (T)ph.y;
+    }
+    for (int iter = 0;; iter++) {
+        __syncthreads();
+        if (tid == 0) *s_count = 0;
+        __syncthreads();
+        for (int key = tid; key < 2 * nr; key += P) {
+            bool on = key < nr ? a0 : a1;
+            if (on && !x.conv[key]) x.act[atomicAdd(s_count, 1)] = key;
+        }
+        __syncthreads();
+        const int A = *s_count;
+        if (A == 0) break;
+        if (iter >= max_iter) {
+            if (tid == 0 && report) atomicAdd(&K.rep->unconverged, (unsigned long long)A);
+            break;
+        }
+        if (tid == 0) {
+            atomicAdd(&K.rep->root_iterations, (unsigned long long)A);
+            if (cold) atomicAdd(&K.rep->cold_root_iterations, (unsigned long long)A);
+        }
+        int g = P / A;
+        g = g < 1 ? 1 : (g > 32 ? 32 : g);
+        g = 1 << (31 - __clz(g));  // power of two
+        const int groups = P / g;
+        const int lane = tid & (g - 1);
+        const int gid = tid / g;
+        for (int base = 0; base < A; base += groups) {
+            const int slot = base + gid;
+            const bool valid = slot < A;
+            const int key = valid ? x.act[slot] : 0;
+            const int d = key >= nr;
+            const C z = x.cur[key];
+            Acc<T> acc = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int t0 = 0; t0 < n; t0 += TS) {
+                const int tn = min(TS, n - t0);
+                if (!x.resident) {
+                    __syncthreads();
+                    const typename CT<T>::Star* gs = (const typename CT<T>::Star*)K.stars;
+                    for (int j = tid; j < tn; j += P) x.s_star[j] = gs[t0 + j];
+                    __syncthreads();
+                }
+                if (valid)
+                    for (int j = lane; j < tn; j += g) acc_star(z.x, z.y, x.s_star[j], acc);
+            }
+            for (int t0 = 0; t0 < nr; t0 += TR) {
+                const int tn = min(TR, nr - t0);
+                __syncthreads();
+                for (int j = tid; j < tn; j += P) {
+                    if (a0) x.s_root[j] = x.cur[t0 + j];
+                    if (a1) x.s_root[TR + j] = x.cur[nr + t0 + j];
+                }
+                __syncthreads();
+                if (valid) {
+                    const C* rr = x.s_root + d * TR;
+                    for (int j = lane; j < tn; j += g) acc_root(z.x, z.y, rr[j], acc);
+                }
+            }
+            for (int off = g >> 1; off > 0; off >>= 1) {
+                acc.Cx += shfl_x(acc.Cx, off);
+                acc.Cy += shfl_x(acc.Cy, off);
+                acc.Ax += shfl_x(acc.Ax, off);
+                acc.Ay += shfl_x(acc.Ay, off);
+                acc.Bx += shfl_x(acc.Bx, off);
+                acc.By += shfl_x(acc.By, off);
+                acc.Dx += shfl_x(acc.Dx, off);
+                acc.Dy += shfl_x(acc.Dy, off);
+            }
+            if (valid && lane == 0) {
+                const T cph = d ? cph1 : cph0, sph = d ? sph1 : sph0;
+                // F = gamma + A - (1 - kappa_s) e^{-i phi}
+                const T Fx = gam + acc.Ax - oms * cph;
+                const T Fy = acc.Ay + oms * sph;
+                C zn = z;
+                T ad = 0;
+                if (Fx != (T)0 || Fy != (T)0) {
+                    const T dFx = (T)-2 * acc.Bx, dFy = (T)-2 * acc.By;
+                    const T fden = Fx * Fx + Fy * Fy;
+                    const T qx = qdiv(dFx * Fx + dFy * Fy, fden);
+                    const T qy = qdiv(dFy * Fx - dFx * Fy, fden);
+                    const T px = qx + (T)2 * acc.Cx - acc.Dx;
+                    const T py = qy + (T)2 * acc.Cy - acc.Dy;
+                    const T pden = px * px + py * py;
+                    const T delx = qdiv(px, pden), dely = qdiv(-py, pden);
+                    zn.x = z.x - delx;
+                    zn.y = z.y - dely;
+                    ad = qsqrt(delx * delx + dely * dely);
+                }
+                const int its = x.it[key] + 1;
+                x.it[key] = its;
+                atomicMax(s_maxit, its);
+                bool done;
+                if (sizeof(T) == 4) {
+                    // FP32: freeze at the absolute tolerance, at a few ulp of |z|, or when
+                    // the corrections stop shrinking near that level (rounding floor).
+                    const T sc = (T)1 + qsqrt(z.x * z.x + z.y * z.y);
+                    const T tolz = fmax((T)K.tol_abs, (T)(8.0 * FLT_EPSILON) * sc);
+                    done = !(ad >= tolz) ||
+                           (its >= 3 && ad > (T)0.25 * (T)x.dprev[key] && ad < (T)32 * tolz);
+                } else {
+                    done = !(ad >= (T)K.tol_abs);
+                    if (!done && K.mu_max > 0) {
+                        const T gx = gam + acc.Ax, gy = acc.Ay;
+                        const T detj = oms * oms - (gx * gx + gy * gy);
+                        done = fabs((double)detj) * K.mu_max < 1.0;
+                    }
+                }
+                x.dprev[key] = (float)ad;
+                if (done) x.conv[key] = 1;
+                x.nxt[key] = zn;
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < A; i += P) {
+            const int key = x.act[i];
+            x.cur[key] = x.nxt[key];
+        }
+    }
+    // directions that still hold unfrozen roots
+    bool b0 = false, b1 = false;
+    for (int key = tid; key < 2 * nr; key += P) {
+        if (x.conv[key]) continue;
+        if (key < nr) b0 |= a0;
+        else b1 |= a1;
+    }
+    const int m0 = __syncthreads_or(b0), m1 = __syncthreads_or(b1);
+    return (m0 ? 1 : 0) | (m1 ? 2 : 0);
+}
+
+// Star guesses z_i +- 1 (Sec. 3.2) into direction d, tilted to z_i +- (1 + i/64):
+// [2i] = z_i + (1 + i/64), [2i+1] = z_i - (1 + i/64).  The tilt breaks the mirror symmetry
+// about the line through a star parallel to the real axis, which FP32 arithmetic keeps
+// exactly (an isolated star at phi = pi would otherwise never leave that line).  A guess
+// equal to an earlier one moves by 1e-3 (1 + i) per earlier copy.
+template <typename T>
+__device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
+    using C = typename CT<T>::C;
+    using Star = typename CT<T>::Star;
+    const TK& K = *x.k;
+    const int nr = K.nr;
+    const Star* gs = (const Star*)K.stars;
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+        const Star si = gs[k >> 1];
+        const T sg = (k & 1) ? (T)-1 : (T)1;
+        const T gx = (T)si.x + sg, gy = (T)si.y + sg * (T)0.015625;
+        int dup = 0;
+        for (int a = 0; a < k; a++) {
+            const Star sa = gs[a >> 1];
+            const T sa_g = (a & 1) ? (T)-1 : (T)1;
+            const T ax = (T)sa.x + sa_g, ay = (T)sa.y + sa_g * (T)0.015625;
+            dup += (ax == gx && ay == gy);
+        }
+        C z;
+        z.x = gx + (T)1e-3 * (T)dup;
+        z.y = gy + (T)1e-3 * (T)dup;
+        const int key = d * nr + k;
+        x.cur[key] = z;
+        x.conv[key] = 0;
+        x.it[key] = 0;
+        x.dprev[key] = FLT_MAX;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
+    using C = typename CT<T>::C;
+    using Star = typename CT<T>::Star;
+    constexpr int TS = CT<T>::TS;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_count, s_maxit;
+    const int tid = threadIdx.x, P = blockDim.x;
+    const int s = blockIdx.x;
+    const int nr = K.nr, n = K.n;
+    const int64_t b0 = subchain_begin(s, K.m, K.S), b1 = subchain_begin(s + 1, K.m, K.S);
+    const int64_t c = (b0 + b1) / 2;
+
+    Ctx<T> x;
+    x.k = &K;
+    x.s_star = (Star*)smem;
+    x.s_root = (C*)(smem + sizeof(Star) * TS);
+    char* w = K.work + (size_t)s * K.work_stride;
+    x.cur = (C*)w;
+    x.nxt = x.cur + 2 * nr;
+    x.prev = x.nxt + 2 * nr;
+    x.dprev = (float*)(x.prev + 2 * nr);
+    x.conv = (int*)(x.dprev + 2 * nr);
+    x.it = x.conv + 2 * nr;
+    x.act = x.it + 2 * nr;
+    x.resident = n <= TS;
+    const Star* gs = (const Star*)K.stars;
+    if (x.resident)
+        for (int j = tid; j < n; j += P) x.s_star[j] = gs[j];
+    if (tid == 0) s_maxit = 0;
+
+    seed_guesses<T>(x, 0);
+    for (int k = tid; k < nr; k += P) x.conv[nr + k] = 1;
+    solve_rows<T>(x, true, false, c, -1, K.max_iter_cold, true, true, &s_count, &s_maxit);
+
+    C* zrows = (C*)K.zrows;
+    C* seam = (C*)K.seam;
+    auto dst = [&](int64_t row) -> C* {
+        return (row == b1 && s < K.S - 1) ? seam + (size_t)s * nr : zrows + (size_t)row * nr;
+    };
+    {
+        C* o = dst(c);
+        for (int k = tid; k < nr; k += P) {
+            o[k] = x.cur[k];
+            x.cur[nr + k] = x.cur[k];
+            K.iters[(size_t)c * nr + k] = x.it[k];
+        }
+    }
+    for (int64_t t = 1;; t++) {
+        const bool a0 = c - t >= b0, a1 = c + t <= b1;
+        if (!a0 && !a1) break;
+        const int64_t r0 = c - t, r1 = c + t;
+        __syncthreads();
+        for (int k = tid; k < 2 * nr; k += P) {
+            const bool on = k < nr ? a0 : a1;
+            if (!on) {
+                x.conv[k] = 1;
+                continue;
+            }
+            const C zc = x.cur[k];
+            C g = zc;
+            if (t >= 2 && K.predictor) {
+                const C zp = x.prev[k];
+                g.x = zc.x + (zc.x - zp.x);
+                g.y = zc.y + (zc.y - zp.y);
+            }
+            x.prev[k] = zc;
+            x.cur[k] = g;
+            x.conv[k] = 0;
+            x.it[k] = 0;
+            x.dprev[k] = FLT_MAX;
+        }
+        const int bad = solve_rows<T>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, &s_count, &s_maxit);
+        if (bad) {
+            // A warm start that does not settle (e.g. a phase step so large that the previous
+            // row sits on a symmetric, non-converging configuration) restarts that row from
+            // the star guesses.
+            __syncthreads();
+            if (bad & 1) seed_guesses<T>(x, 0);
+            if (bad & 2) seed_guesses<T>(x, 1);
+            solve_rows<T>(x, bad & 1, (bad & 2) != 0, r0, r1, K.max_iter_cold, true, true, &s_count, &s_maxit);
+        }
+        if (a0) {
+            C* o = dst(r0);
+            for (int k = tid; k < nr; k += P) {
+                o[k] = x.cur[k];
+                K.iters[(size_t)r0 * nr + k] = x.it[k];
+            }
+        }
+        if (a1) {
+            C* o = dst(r1);
+            for (int k = tid; k < nr; k += P) {
+                o[k] = x.cur[nr + k];
+                if (!(r1 == b1 && s < K.S - 1)) K.iters[(size_t)r1 * nr + k] = x.it[nr + k];
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
+}
+
+size_t tracer_smem_bytes(bool fp64) {
+    return fp64 ? CT<double>::TS * sizeof(StarD) + 2 * TR * sizeof(double2)
+                : CT<float>::TS * sizeof(float4) + 2 * TR * sizeof(float2);
+}
+
+size_t tracer_work_stride(int64_t nr, size_t elem) {
+    size_t b = (size_t)(2 * nr) * (3 * elem + 4 * 4);
+    return (b + 255) / 256 * 256;
+}
+
+int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms) {
+    int64_t S = o.subchains;
+    if (S <= 0) {
+        // two resident tracing CTAs per SM; each subchain keeps at least 8 rows
+        S = 2 * (int64_t)sms;
+        if (S > m / 8) S = m / 8;
+    }
+    if (S > m / 2) S = m / 2;
+    if (S < 1) S = 1;
+    return (int)S;
+}
+
+cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
+    TK K;
+    K.n = (int)a.f->n;
+    K.nr = (int)(2 * a.f->n);
+    K.stars = fp64 ? (const void*)a.f->star64 : (const void*)a.f->star32;
+    K.kappa_s = a.f->kappa_s;
+    K.gamma = a.f->gamma;
+    K.m = a.m;
+    K.S = a.S;
+    K.phase = a.phase;
+    K.zrows = a.zrows;
+    K.seam = a.seam;
+    K.iters = a.iters;
+    K.work = (char*)a.work;
+    K.work_stride = a.work_stride;
+    K.rep = a.rep;
+    K.tol_abs = a.tol_abs;
+    K.mu_max = a.mu_max;
+    K.max_iter_cold = a.max_iter_cold;
+    K.max_iter_warm = a.max_iter_warm;
+    K.predictor = a.predictor;
+    const size_t smem = tracer_smem_bytes(fp64);
+    cudaError_t e;
+    if (fp64) {
+        e = cudaFuncSetAttribute(trace_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        trace_kernel<double><<<a.S, a.threads, smem, st>>>(K);
+    } else {
+        e = cudaFuncSetAttribute(trace_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        trace_kernel<float><<<a.S, a.threads, smem, st>>>(K);
+    }
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Joining the subchains: the up-end row of subchain s and the first row of subchain s+1
+// are the same root set (Sec. 4.3 footnote: the end of one chain is the start of the
+// next); each of s's columns is matched to its nearest root of s+1's row, and the column
+// permutations are composed so that global column g follows one chain across all rows.
+// ----------------------------------------------------------------------------------
+template <typename C, typename T>
+__global__ void seam_match_kernel(const C* zrows, const C* seam, int64_t m, int S, int nr,
+                                  int32_t* match, int32_t* hits, DevReport* rep) {
+    // Distances in the tracer's own precision: roots of one row are separated by far more
+    // than the tracer's rounding error, so FP32 suffices for the mixed form.
+    const int s = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr) return;
+    const int64_t row = subchain_begin(s + 1, m, S);
+    const C q = seam[(size_t)s * nr + k];
+    const C* B = zrows + (size_t)row * nr;
+    T best = (T)3.0e38, second = (T)3.0e38;
+    int bi = 0;
+    for (int j = 0; j < nr; j++) {
+        const C b = B[j];
+        const T dx = b.x - q.x, dy = b.y - q.y;
+        const T d2 = dx * dx + dy * dy;
+        if (d2 < best) {
+            second = best;
+            best = d2;
+            bi = j;
+        } else if (d2 < second) {
+            second = d2;
+        }
+    }
+    match[(size_t)s * nr + k] = bi;
+    atomicAdd(&hits[(size_t)s * nr + bi], 1);
+    if (!(best <= (T)1e-4 * second)) atomicAdd(&rep->seam_ambiguous, 1ull);
+}
+
+__global__ void compose_perm_kernel(int S, int nr, const int32_t* match, const int32_t* hits,
+                                    int32_t* perm, DevReport* rep) {
+    const int tid = threadIdx.x, P = blockDim.x;
+    for (int g = tid; g < nr; g += P) perm[g] = g;
+    for (int s = 0; s + 1 < S; s++) {
+        __syncthreads();
+        int bad = 0;
+        for (int g = tid; g < nr; g += P) {
+            perm[(size_t)(s + 1) * nr + g] = match[(size_t)s * nr + perm[(size_t)s * nr + g]];
+            bad += hits[(size_t)s * nr + g] != 1;
+        }
+        if (bad) atomicAdd(&rep->seam_ambiguous, (unsigned long long)bad);
+    }
+}
+
+cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int S, int64_t nr,
+                             bool fp64, int32_t* match, int32_t* hits, int32_t* perm,
+                             DevReport* rep, cudaStream_t st) {
+    if (S > 1) {
+        cudaError_t e = cudaMemsetAsync(hits, 0, sizeof(int32_t) * (size_t)(S - 1) * nr, st);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)((nr + 255) / 256), (unsigned)(S - 1));
+        if (fp64)
+            seam_match_kernel<double2, double><<<grid, 256, 0, st>>>((const double2*)zrows, (const double2*)seam,
+                                                              m, S, (int)nr, match, hits, rep);
+        else
+            seam_match_kernel<float2, float><<<grid, 256, 0, st>>>((const float2*)zrows, (const float2*)seam,
+                                                             m, S, (int)nr, match, hits, rep);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    compose_perm_kernel<<<1, 1024, 0, st>>>(S, (int)nr, match, hits, perm, rep);
+    return cudaGetLastError();
+}
+
+// cos(phi_j), sin(phi_j) with phi_j = 2 pi j / m (Sec. 4.3), FP64.
+__global__ void phase_kernel(double2* ph, int64_t m) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j > m) return;
+    const double p = 2.0 * 3.14159265358979323846 * (double)j / (double)m;
+    double sn, cs;
+    sincos(p, &sn, &cs);
+    ph[j] = make_double2(cs, sn);
+}
+
+cudaError_t launch_phase_table(double2* phase, int64_t m, cudaStream_t st) {
+    const int64_t rows = m + 1;
+    phase_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(phase, m);
+    return cudaGetLastError();
+}
+
+}  // namespace ccg

@@ -1,0 +1,422 @@
+// C ABI of libccgpu (declared in include/cc.h): argument checks, field set-up, workspace
+// layout and the order of kernel launches.  Every compute step runs in the kernels of
+// aberth.cu, polish.cu and raster.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "cc_internal.h"
+
+using namespace ccg;
+
+struct cc_field {
+    FieldDev dev;
+    cc_options opt;
+    int device;
+    DevReport* d_rep;
+    cudaEvent_t done;
+    cudaEvent_t ev[4];  // stage boundaries: start, after trace, after join, end
+    bool solved;
+    int64_t last_m;
+    int last_S;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(CC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CC_CUDA(call, what)                          \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+int sm_count(int device) {
+    static std::mutex mu;
+    static std::vector<int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= device) cache.resize(device + 1, 0);
+    if (cache[device] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 1;
+        cache[device] = v;
+    }
+    return cache[device];
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Workspace layout of cc_critical_curves.
+CurveLayout curve_layout(const cc_field* f, int64_t m) {
+    CurveLayout L;
+    const int64_t nr = 2 * f->dev.n;
+    const bool fp64 = f->opt.precision == CC_FP64;
+    L.elem = fp64 ? sizeof(double2) : sizeof(float2);
+    L.S = subchain_count(m, nr, f->opt, sm_count(f->device));
+    L.threads = f->opt.block_threads > 0 ? f->opt.block_threads : 512;
+    L.work_stride = tracer_work_stride(nr, L.elem);
+    size_t o = 0;
+    L.off_report = o;
+    o += align256(sizeof(DevReport));
+    L.off_phase = o;
+    o += align256(sizeof(double2) * (size_t)(m + 1));
+    L.off_zrows = o;
+    o += align256(L.elem * (size_t)(m + 1) * nr);
+    L.off_seam = o;
+    o += align256(L.elem * (size_t)L.S * nr);
+    L.off_iters = o;
+    o += align256(sizeof(int32_t) * (size_t)(m + 1) * nr);
+    L.off_match = o;
+    o += align256(sizeof(int32_t) * (size_t)L.S * nr);
+    L.off_hits = o;
+    o += align256(sizeof(int32_t) * (size_t)L.S * nr);
+    L.off_perm = o;
+    o += align256(sizeof(int32_t) * (size_t)L.S * nr);
+    L.off_work = o;
+    o += L.work_stride * (size_t)L.S;
+    L.total = o;
+    return L;
+}
+
+// Copy n doubles from a host or device pointer to host memory.  Host (or unregistered)
+// memory is copied directly, so argument checks need no device.
+int fetch_host(double* dst, const double* src, int64_t n, const char* what) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, src);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        memcpy(dst, src, sizeof(double) * (size_t)n);
+        return CC_OK;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        e = cudaMemcpy(dst, src, sizeof(double) * (size_t)n, cudaMemcpyDefault);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+        return CC_OK;
+    }
+    memcpy(dst, src, sizeof(double) * (size_t)n);
+    return CC_OK;
+}
+
+bool finite3(double a, double b, double c) { return std::isfinite(a) && std::isfinite(b) && std::isfinite(c); }
+
+}  // namespace
+
+extern "C" {
+
+int cc_options_default(cc_options* opt) {
+    if (!opt) return fail(CC_EINVAL, "cc_options_default: opt is NULL");
+    opt->tol_abs = 1e-9;
+    opt->mu_max = 0.0;
+    opt->tol_cert = 2e-11;
+    opt->max_iter_cold = 500;
+    opt->max_iter_warm = 200;
+    opt->max_polish = 4;
+    opt->precision = CC_MIXED;
+    opt->hp_arith = CC_HP_DFLOAT;
+    opt->subchains = 0;
+    opt->predictor = 1;
+    opt->block_threads = 0;
+    return CC_OK;
+}
+
+int cc_field_create(const double* x, const double* y, const double* mass, int64_t n, double kappa_s,
+                    double gamma, const cc_options* opt, cc_field** out) {
+    if (!out) return fail(CC_EINVAL, "cc_field_create: out is NULL");
+    *out = nullptr;
+    if (!x || !y || !mass) return fail(CC_EINVAL, "cc_field_create: NULL star array");
+    if (n < 1 || n > (int64_t)1 << 26) return fail(CC_EINVAL, "cc_field_create: n = %lld out of range [1, 2^26]", (long long)n);
+    if (!std::isfinite(kappa_s) || !std::isfinite(gamma))
+        return fail(CC_EINVAL, "cc_field_create: kappa_s and gamma must be finite");
+    if (std::fabs(1.0 - kappa_s) < 1e-12 || std::fabs(std::fabs(1.0 - kappa_s) - std::fabs(gamma)) < 1e-12)
+        return fail(CC_EDEGENERATE,
+                    "cc_field_create: |1 - kappa_s| = |gamma| (or 1 - kappa_s = 0): a critical point runs to infinity");
+    cc_options o;
+    cc_options_default(&o);
+    if (opt) o = *opt;
+    if (o.precision != CC_MIXED && o.precision != CC_FP64) return fail(CC_EINVAL, "cc_field_create: bad precision");
+    if (o.hp_arith != CC_HP_DFLOAT && o.hp_arith != CC_HP_FP64) return fail(CC_EINVAL, "cc_field_create: bad hp_arith");
+    if (!(o.tol_abs > 0) || !(o.tol_cert > 0) || o.max_iter_cold < 1 || o.max_iter_warm < 1 || o.max_polish < 1 ||
+        o.mu_max < 0 || o.subchains < 0)
+        return fail(CC_EINVAL, "cc_field_create: bad options");
+    if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 512 || (o.block_threads & 31)))
+        return fail(CC_EINVAL, "cc_field_create: block_threads must be 0 or a multiple of 32 in [32, 512]");
+
+    std::vector<double> hx(n), hy(n), hm(n);
+    if (int r = fetch_host(hx.data(), x, n, "x")) return r;
+    if (int r = fetch_host(hy.data(), y, n, "y")) return r;
+    if (int r = fetch_host(hm.data(), mass, n, "mass")) return r;
+    bool unit = true;
+    for (int64_t i = 0; i < n; i++) {
+        if (!finite3(hx[i], hy[i], hm[i])) return fail(CC_EINVAL, "cc_field_create: star %lld is not finite", (long long)i);
+        if (!(hm[i] > 0)) return fail(CC_EINVAL, "cc_field_create: star %lld has mass <= 0", (long long)i);
+        unit = unit && hm[i] == 1.0;
+    }
+    std::vector<float4> s32(n), sdp(n);
+    std::vector<float2> sdm(n);
+    std::vector<StarD> s64(n);
+    auto split = [](double v, float& hi, float& lo) {
+        hi = (float)v;
+        lo = (float)(v - (double)hi);
+    };
+    for (int64_t i = 0; i < n; i++) {
+        s32[i] = make_float4((float)hx[i], (float)hy[i], (float)hm[i], 0.f);
+        s64[i] = StarD{hx[i], hy[i], hm[i], 0.0};
+        float a, b, c, d, e, g;
+        split(hx[i], a, b);
+        split(hy[i], c, d);
+        split(hm[i], e, g);
+        sdp[i] = make_float4(a, b, c, d);
+        sdm[i] = make_float2(e, g);
+    }
+    cc_field* f = new cc_field();
+    f->opt = o;
+    f->dev.n = n;
+    f->dev.kappa_s = kappa_s;
+    f->dev.gamma = gamma;
+    f->dev.unit_mass = unit;
+    f->solved = false;
+    cudaGetDevice(&f->device);
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMalloc(&f->dev.star32, sizeof(float4) * n);
+    e = e ? e : cudaMalloc(&f->dev.star64, sizeof(StarD) * n);
+    e = e ? e : cudaMalloc(&f->dev.star_dfp, sizeof(float4) * n);
+    e = e ? e : cudaMalloc(&f->dev.star_dfm, sizeof(float2) * n);
+    e = e ? e : cudaMalloc(&f->d_rep, sizeof(DevReport));
+    e = e ? e : cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming);
+    for (int i = 0; i < 4; i++) e = e ? e : cudaEventCreate(&f->ev[i]);
+    if (e != cudaSuccess) {
+        cc_field_destroy(f);
+        return fail(e == cudaErrorMemoryAllocation ? CC_ENOMEM : CC_ECUDA, "cc_field_create: %s", cudaGetErrorString(e));
+    }
+    e = e ? e : cudaMemcpy(f->dev.star32, s32.data(), sizeof(float4) * n, cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(f->dev.star64, s64.data(), sizeof(StarD) * n, cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(f->dev.star_dfp, sdp.data(), sizeof(float4) * n, cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(f->dev.star_dfm, sdm.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemset(f->d_rep, 0, sizeof(DevReport));
+    if (e != cudaSuccess) {
+        cc_field_destroy(f);
+        return cuda_fail(e, "cc_field_create upload");
+    }
+    *out = f;
+    return CC_OK;
+}
+
+int cc_field_destroy(cc_field* f) {
+    if (!f) return CC_OK;
+    if (f->done) cudaEventSynchronize(f->done);
+    cudaFree(f->dev.star32);
+    cudaFree(f->dev.star64);
+    cudaFree(f->dev.star_dfp);
+    cudaFree(f->dev.star_dfm);
+    cudaFree(f->d_rep);
+    if (f->done) cudaEventDestroy(f->done);
+    for (int i = 0; i < 4; i++)
+        if (f->ev[i]) cudaEventDestroy(f->ev[i]);
+    delete f;
+    return CC_OK;
+}
+
+int cc_field_size(const cc_field* f, int64_t* n_stars, int64_t* n_roots) {
+    if (!f) return fail(CC_EINVAL, "cc_field_size: field is NULL");
+    if (n_stars) *n_stars = f->dev.n;
+    if (n_roots) *n_roots = 2 * f->dev.n;
+    return CC_OK;
+}
+
+static int check_m(int64_t m) {
+    if (m < 2 || (m & 1)) return fail(CC_EINVAL, "m = %lld must be even and >= 2", (long long)m);
+    if (m > ((int64_t)1 << 30)) return fail(CC_EINVAL, "m = %lld too large", (long long)m);
+    return CC_OK;
+}
+
+int cc_critical_curves_workspace_bytes(const cc_field* f, int64_t m, size_t* bytes) {
+    if (!f || !bytes) return fail(CC_EINVAL, "cc_critical_curves_workspace_bytes: NULL argument");
+    if (int r = check_m(m)) return r;
+    *bytes = curve_layout(f, m).total;
+    return CC_OK;
+}
+
+int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int32_t* iters_out,
+                       void* workspace, size_t workspace_bytes, cc_stream_t stream) {
+    if (!f) return fail(CC_EINVAL, "cc_critical_curves: field is NULL");
+    if (int r = check_m(m)) return r;
+    if (!z_out) return fail(CC_EINVAL, "cc_critical_curves: z_out is NULL");
+    if (!workspace) return fail(CC_EINVAL, "cc_critical_curves: workspace is NULL");
+    if ((uintptr_t)workspace % 256) return fail(CC_EINVAL, "cc_critical_curves: workspace must be 256-byte aligned");
+    const CurveLayout L = curve_layout(f, m);
+    if (workspace_bytes < L.total)
+        return fail(CC_ENOMEM, "cc_critical_curves: workspace has %zu bytes, needs %zu", workspace_bytes, L.total);
+    CC_CUDA(cudaSetDevice(f->device), "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    const int64_t nr = 2 * f->dev.n;
+    const bool fp64 = f->opt.precision == CC_FP64;
+    DevReport* rep = f->d_rep;
+    CC_CUDA(cudaMemsetAsync(rep, 0, sizeof(DevReport), st), "clear report");
+    double2* phase = (double2*)(ws + L.off_phase);
+    CC_CUDA(cudaEventRecord(f->ev[0], st), "event record");
+    CC_CUDA(launch_phase_table(phase, m, st), "phase table");
+    TraceArgs ta;
+    ta.f = &f->dev;
+    ta.m = m;
+    ta.S = L.S;
+    ta.phase = phase;
+    ta.zrows = ws + L.off_zrows;
+    ta.seam = ws + L.off_seam;
+    ta.iters = (int32_t*)(ws + L.off_iters);
+    ta.work = ws + L.off_work;
+    ta.work_stride = L.work_stride;
+    ta.rep = rep;
+    ta.tol_abs = f->opt.tol_abs;
+    ta.mu_max = f->opt.mu_max;
+    ta.max_iter_cold = f->opt.max_iter_cold;
+    ta.max_iter_warm = f->opt.max_iter_warm;
+    ta.predictor = f->opt.predictor;
+    ta.threads = L.threads;
+    CC_CUDA(launch_trace(ta, fp64, st), "trace");
+    CC_CUDA(cudaEventRecord(f->ev[1], st), "event record");
+    int32_t* perm = (int32_t*)(ws + L.off_perm);
+    CC_CUDA(launch_seam_join(ws + L.off_zrows, ws + L.off_seam, m, L.S, nr, fp64, (int32_t*)(ws + L.off_match),
+                             (int32_t*)(ws + L.off_hits), perm, rep, st),
+            "seam join");
+    CC_CUDA(cudaEventRecord(f->ev[2], st), "event record");
+    if (fp64) {
+        FinalizeArgs fa;
+        fa.m = m;
+        fa.S = L.S;
+        fa.nr = nr;
+        fa.zrows = (const double2*)(ws + L.off_zrows);
+        fa.perm = perm;
+        fa.iters_in = (const int32_t*)(ws + L.off_iters);
+        fa.z_out = (double2*)z_out;
+        fa.iters_out = iters_out;
+        CC_CUDA(launch_finalize_fp64(fa, st), "finalize");
+        if (w_out)
+            CC_CUDA(launch_map_caustics(f->dev, (const double2*)z_out, (m + 1) * nr, (double2*)w_out,
+                                        f->opt.hp_arith == CC_HP_FP64, st),
+                    "map caustics");
+    } else {
+        PolishArgs pa;
+        pa.f = &f->dev;
+        pa.m = m;
+        pa.S = L.S;
+        pa.nr = nr;
+        pa.phase = phase;
+        pa.zrows = (const float2*)(ws + L.off_zrows);
+        pa.perm = perm;
+        pa.iters_in = (const int32_t*)(ws + L.off_iters);
+        pa.z_out = (double2*)z_out;
+        pa.w_out = (double2*)w_out;
+        pa.iters_out = iters_out;
+        pa.rep = rep;
+        pa.tol_cert = f->opt.tol_cert;
+        pa.max_polish = f->opt.max_polish;
+        pa.hp_fp64 = f->opt.hp_arith == CC_HP_FP64;
+        CC_CUDA(launch_polish(pa, st), "polish");
+    }
+    CC_CUDA(cudaEventRecord(f->ev[3], st), "event record");
+    CC_CUDA(cudaEventRecord(f->done, st), "event record");
+    f->solved = true;
+    f->last_m = m;
+    f->last_S = L.S;
+    return CC_OK;
+}
+
+int cc_field_report(cc_field* f, cc_report* out) {
+    if (!f || !out) return fail(CC_EINVAL, "cc_field_report: NULL argument");
+    if (!f->solved) return fail(CC_EINVAL, "cc_field_report: no cc_critical_curves call on this field yet");
+    CC_CUDA(cudaEventSynchronize(f->done), "wait");
+    DevReport r;
+    CC_CUDA(cudaMemcpy(&r, f->d_rep, sizeof r, cudaMemcpyDeviceToHost), "read report");
+    memset(out, 0, sizeof *out);
+    out->rows = f->last_m + 1;
+    out->n_roots = 2 * f->dev.n;
+    out->subchains = f->last_S;
+    out->root_iterations = (int64_t)r.root_iterations;
+    out->cold_root_iterations = (int64_t)r.cold_root_iterations;
+    out->unconverged = (int64_t)r.unconverged;
+    out->polish_passes = (int64_t)r.polish_passes;
+    out->uncertified = (int64_t)r.uncertified;
+    out->seam_ambiguous = (int64_t)r.seam_ambiguous;
+    out->max_iter_row = r.max_iter_row;
+    out->timeout = r.timeout;
+    out->max_err_est = r.max_err_est;
+    CC_CUDA(cudaEventElapsedTime(&out->trace_ms, f->ev[0], f->ev[1]), "stage time");
+    CC_CUDA(cudaEventElapsedTime(&out->join_ms, f->ev[1], f->ev[2]), "stage time");
+    CC_CUDA(cudaEventElapsedTime(&out->polish_ms, f->ev[2], f->ev[3]), "stage time");
+    if (r.timeout) return fail(CC_ETIMEOUT, "a device-side wait gave up");
+    if (r.unconverged || r.uncertified)
+        return fail(CC_ENOCONV, "%lld root-rows hit the iteration cap, %lld points uncertified",
+                    (long long)r.unconverged, (long long)r.uncertified);
+    return CC_OK;
+}
+
+int cc_map_caustics(cc_field* f, const double* z, int64_t count, double* w_out, cc_stream_t stream) {
+    if (!f) return fail(CC_EINVAL, "cc_map_caustics: field is NULL");
+    if (count < 0) return fail(CC_EINVAL, "cc_map_caustics: count < 0");
+    if (count == 0) return CC_OK;
+    if (!z || !w_out) return fail(CC_EINVAL, "cc_map_caustics: NULL buffer");
+    CC_CUDA(cudaSetDevice(f->device), "cudaSetDevice");
+    CC_CUDA(launch_map_caustics(f->dev, (const double2*)z, count, (double2*)w_out, f->opt.hp_arith == CC_HP_FP64,
+                                (cudaStream_t)stream),
+            "map caustics");
+    return CC_OK;
+}
+
+int cc_crossing_map(const double* w, int64_t rows, int64_t n_r, double x0, double x1, double y0, double y1,
+                    int32_t W, int32_t H, int32_t* ncc_out, cc_stream_t stream) {
+    if (!ncc_out) return fail(CC_EINVAL, "cc_crossing_map: ncc_out is NULL");
+    if (W < 1 || H < 1) return fail(CC_EINVAL, "cc_crossing_map: W, H must be >= 1");
+    if (!(std::isfinite(x0) && std::isfinite(x1) && std::isfinite(y0) && std::isfinite(y1)) || !(x1 > x0) ||
+        !(y1 > y0))
+        return fail(CC_EINVAL, "cc_crossing_map: need finite x0 < x1 and y0 < y1");
+    if (rows < 0 || n_r < 0) return fail(CC_EINVAL, "cc_crossing_map: rows, n_r must be >= 0");
+    if (rows * n_r > 0 && !w) return fail(CC_EINVAL, "cc_crossing_map: w is NULL");
+    CC_CUDA(launch_crossing_map((const double2*)w, rows, n_r, x0, x1, y0, y1, W, H, ncc_out, (cudaStream_t)stream),
+            "crossing map");
+    return CC_OK;
+}
+
+int cc_distance_map_workspace_bytes(int32_t W, int32_t H, size_t* bytes) {
+    if (!bytes || W < 1 || H < 1) return fail(CC_EINVAL, "cc_distance_map_workspace_bytes: bad argument");
+    *bytes = distance_workspace_bytes(W, H);
+    return CC_OK;
+}
+
+int cc_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, double* d_out, void* workspace,
+                    size_t workspace_bytes, cc_stream_t stream) {
+    if (!ncc || !d_out || !workspace) return fail(CC_EINVAL, "cc_distance_map: NULL buffer");
+    if (W < 1 || H < 1) return fail(CC_EINVAL, "cc_distance_map: W, H must be >= 1");
+    if (!(pixel > 0) || !std::isfinite(pixel)) return fail(CC_EINVAL, "cc_distance_map: pixel must be finite and > 0");
+    if ((uintptr_t)workspace % 256) return fail(CC_EINVAL, "cc_distance_map: workspace must be 256-byte aligned");
+    if (workspace_bytes < distance_workspace_bytes(W, H))
+        return fail(CC_ENOMEM, "cc_distance_map: workspace has %zu bytes, needs %zu", workspace_bytes,
+                    distance_workspace_bytes(W, H));
+    CC_CUDA(launch_distance_map(ncc, W, H, pixel, d_out, workspace, (cudaStream_t)stream), "distance map");
+    return CC_OK;
+}
+
+const char* cc_last_error(void) { return g_err.c_str(); }
+
+const char* cc_version(void) { return "ccgpu 0.1 (sm_103a)"; }
+
+}  // extern "C"

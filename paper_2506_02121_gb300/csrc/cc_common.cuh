@@ -1,0 +1,131 @@
+// Shared device helpers of libccgpu: FP32/FP64 complex arithmetic and double-float
+// ("df": an unevaluated sum hi + lo of two FP32 numbers, ~48-bit significand) built from
+// error-free transformations.  Used only by the CUDA library.
+//
+// Error-free transformations (all with IEEE round-to-nearest intrinsics that the compiler
+// never contracts or reassociates):
+//   two_sum      Knuth (TAOCP vol. 2, 4.2.2): s + e == a + b exactly.
+//   fast_two_sum Dekker (1971), requires |a| >= |b| (or a == 0).
+//   two_prod     with one FMA: p + e == a * b exactly.
+// Reciprocal: one Newton-Raphson step y' = y + y (1 - a y) on the hardware FP32
+// reciprocal approximation, with the residual 1 - a y formed from an exact product.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ccg {
+
+// ----------------------------------------------------------------------------------
+// FP32
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ----------------------------------------------------------------------------------
+// double-float
+// ----------------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_make(float h) { return df{h, 0.0f}; }
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return df{s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return df{s, e};
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    float e = __fmaf_rn(a, b, -p);
+    return df{p, e};
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+
+// a + b; absolute error O(2^-48 (|a| + |b|)), enough here because every sum either has
+// operands of one sign or is a difference whose result is used in absolute terms.
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+// a (double-float) minus b (plain float), e.g. a root coordinate minus nothing.
+__device__ __forceinline__ df df_sub_f(df a, float b) {
+    df s = two_sum(a.hi, -b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    df p = two_prod(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.lo, p.lo);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    df p = two_prod(a.hi, b);
+    float e = __fmaf_rn(a.lo, b, p.lo);
+    return fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ df df_sqr(df a) {
+    df p = two_prod(a.hi, a.hi);
+    float e = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, p.lo);
+    return fast_two_sum(p.hi, e);
+}
+
+// 1 / a for a > 0 (a.hi normal): relative error ~2^-46.
+__device__ __forceinline__ df df_rcp(df a) {
+    float y = rcp_approx(a.hi);
+    df p = two_prod(a.hi, y);                // a.hi * y exactly
+    float t = __fsub_rn(1.0f, p.hi);          // exact: p.hi is within 2^-22 of 1
+    t = __fsub_rn(t, p.lo);
+    t = __fmaf_rn(-a.lo, y, t);               // t = 1 - a * y (to ~2^-47 relative)
+    return fast_two_sum(y, __fmul_rn(y, t));
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df df_from_double(double x) {
+    float h = __double2float_rn(x);
+    float l = __double2float_rn(x - (double)h);
+    return df{h, l};
+}
+
+// ----------------------------------------------------------------------------------
+// Status words shared by the kernels (device-side report, reduced by atomics)
+// ----------------------------------------------------------------------------------
+struct DevReport {
+    unsigned long long root_iterations;
+    unsigned long long cold_root_iterations;
+    unsigned long long unconverged;
+    unsigned long long polish_passes;
+    unsigned long long uncertified;
+    unsigned long long seam_ambiguous;
+    unsigned long long jumped;   // polish moved a root further than the tracer's scale
+    int max_iter_row;
+    int timeout;
+    double max_err_est;          // stored as the bit pattern of a non-negative double
+};
+
+__device__ __forceinline__ void atomic_max_double_nonneg(double* addr, double v) {
+    // non-negative doubles order like their bit patterns as signed 64-bit integers
+    atomicMax((long long*)addr, __double_as_longlong(v));
+}
+
+}  // namespace ccg

@@ -1,0 +1,120 @@
+// Internal interfaces between the translation units of libccgpu (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/cc.h"
+#include "cc_common.cuh"
+
+namespace ccg {
+
+// FP64 star record for the plain-FP64 tracer (32 bytes, two 16-byte loads).
+struct __align__(32) StarD {
+    double x, y, z, w;  // position (x, y), mass z, padding w
+};
+
+// Device-side copy of a field's stars in the layouts the kernels read.
+struct FieldDev {
+    int64_t n;
+    double kappa_s, gamma;
+    bool unit_mass;
+    float4* star32;   // (x, y, m, 0) rounded to FP32
+    StarD* star64;    // FP64
+    float4* star_dfp; // (x_hi, x_lo, y_hi, y_lo) double-float positions
+    float2* star_dfm; // (m_hi, m_lo)
+};
+
+// Tracing (Aberth) launch arguments shared by the FP32 and FP64 tracers.
+struct TraceArgs {
+    const FieldDev* f;     // host pointer to the field description (values copied into kernel args)
+    int64_t m;             // phi steps
+    int S;                 // subchains
+    const double2* phase;  // (m+1) x (cos phi_j, sin phi_j)
+    void* zrows;           // (m+1) x nr complex (T): each row in its subchain's column order
+    void* seam;            // S x nr complex (T): up-end row of subchain s, s < S-1
+    int32_t* iters;        // (m+1) x nr
+    void* work;            // per-CTA scratch
+    size_t work_stride;    // bytes per CTA (multiple of 256)
+    DevReport* rep;
+    double tol_abs, mu_max;
+    int max_iter_cold, max_iter_warm, predictor;
+    int threads;
+};
+
+// Workspace layout of cc_critical_curves (byte offsets from the workspace base).
+struct CurveLayout {
+    int S;
+    int threads;
+    size_t elem;           // bytes per tracer complex (8 FP32, 16 FP64)
+    size_t off_phase, off_zrows, off_seam, off_iters, off_match, off_hits, off_perm, off_work,
+        off_report, total;
+    size_t work_stride;
+};
+
+size_t tracer_work_stride(int64_t nr, size_t elem);
+size_t tracer_smem_bytes(bool fp64);
+int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms);
+
+cudaError_t launch_phase_table(double2* phase, int64_t m, cudaStream_t st);
+cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st);
+cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int S, int64_t nr,
+                             bool fp64, int32_t* match, int32_t* hits, int32_t* perm,
+                             DevReport* rep, cudaStream_t st);
+
+// Polish + caustic (mixed form) and the FP64 finalisation.
+struct PolishArgs {
+    const FieldDev* f;
+    int64_t m;
+    int S;
+    int64_t nr;
+    const double2* phase;
+    const float2* zrows;    // tracer output (FP32)
+    const int32_t* perm;    // S x nr
+    const int32_t* iters_in;
+    double2* z_out;
+    double2* w_out;         // may be null
+    int32_t* iters_out;     // may be null
+    DevReport* rep;
+    double tol_cert;
+    int max_polish;
+    int hp_fp64;            // 1: native FP64 star sums, 0: double-float
+};
+cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st);
+
+struct FinalizeArgs {
+    int64_t m;
+    int S;
+    int64_t nr;
+    const double2* zrows;
+    const int32_t* perm;
+    const int32_t* iters_in;
+    double2* z_out;
+    int32_t* iters_out;
+};
+cudaError_t launch_finalize_fp64(const FinalizeArgs& a, cudaStream_t st);
+
+cudaError_t launch_map_caustics(const FieldDev& f, const double2* z, int64_t count, double2* w,
+                                int hp_fp64, cudaStream_t st);
+
+// Rasterisation.
+cudaError_t launch_crossing_map(const double2* w, int64_t rows, int64_t nr, double x0, double x1,
+                                double y0, double y1, int32_t W, int32_t H, int32_t* ncc,
+                                cudaStream_t st);
+size_t distance_workspace_bytes(int32_t W, int32_t H);
+cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel,
+                                double* d_out, void* ws, cudaStream_t st);
+
+// Subchain of a row: rows [b_s, b_{s+1}) belong to s, row m to S-1; b_s = floor(s m / S).
+__host__ __device__ __forceinline__ int64_t subchain_begin(int64_t s, int64_t m, int64_t S) {
+    return (s * m) / S;
+}
+__host__ __device__ __forceinline__ int subchain_of_row(int64_t j, int64_t m, int64_t S) {
+    if (j >= m) return (int)(S - 1);
+    int64_t s = (j * S) / m;
+    while (s + 1 < S && subchain_begin(s + 1, m, S) <= j) s++;
+    while (s > 0 && subchain_begin(s, m, S) > j) s--;
+    return (int)s;
+}
+
+}  // namespace ccg

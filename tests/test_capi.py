@@ -1,0 +1,60 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads, and it
+exports every function that include/cc.h declares; the binding declares the same set."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cc_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_02121_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_five_calls():
+    names = _declared()
+    for n in ["cc_field_create", "cc_critical_curves", "cc_map_caustics", "cc_crossing_map", "cc_distance_map"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header(lib):
+    from paper_2506_02121_gb300 import cc
+    assert sorted(cc.EXPORTED) == _declared()
+
+
+def test_host_only_calls(lib):
+    from paper_2506_02121_gb300 import cc
+    o = cc.cc_options_default()
+    assert o.tol_abs == 1e-9 and o.precision == cc.CC_MIXED
+    assert cc.cc_version().startswith("ccgpu")
+    assert cc.cc_distance_map_workspace_bytes(4096, 4096) >= 2 * 4096 * 4096 * 4
+    with pytest.raises(cc.CCError) as e:
+        cc.cc_distance_map_workspace_bytes(0, 5)
+    assert e.value.status == cc.CC_EINVAL
+
+
+def test_degenerate_field_rejected_before_any_device_work(lib):
+    import numpy as np
+    from paper_2506_02121_gb300 import cc
+    with pytest.raises(cc.CCError) as e:
+        cc.cc_field_create(np.zeros(1), np.zeros(1), np.ones(1), 0.2, 0.8)
+    assert e.value.status == cc.CC_EDEGENERATE
+    with pytest.raises(cc.CCError) as e:
+        cc.cc_field_create(np.zeros(1), np.zeros(1), -np.ones(1), 0.0, 0.3)
+    assert e.value.status == cc.CC_EINVAL

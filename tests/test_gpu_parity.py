@@ -1,0 +1,195 @@
+"""GPU-vs-oracle parity through the C ABI: critical points and caustics within 1e-9
+theta_E of the FP64 oracle, crossing counts and distance maps bit-exact."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_02121_gb300 import cc, synth
+from tests import lensing_math as lm
+from tests.gpu_util import compare_chain, match_row
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+def _opts(**kw):
+    o = cc.cc_options_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _solve(x, y, m_, ks, g, msteps, **kw):
+    field = cc.cc_field_create(x, y, m_, ks, g, _opts(**kw))
+    z, w, it = cc.critical_curves(field, msteps, caustics=True, iters=True)
+    status, rep = cc.cc_field_report(field)
+    return z.cpu().numpy(), w.cpu().numpy(), it.cpu().numpy(), status, rep
+
+
+def _check_against_oracle(x, y, m_, ks, g, msteps, **kw):
+    zg, wg, it, status, rep = _solve(x, y, m_, ks, g, msteps, **kw)
+    assert status == cc.CC_OK, str(rep)
+    zo, _, bad = oracle.critical_curves(x, y, m_, ks, g, msteps)
+    assert bad == 0
+    worst, pairs = compare_chain(zg, zo, TOL)
+    wo = oracle.map_caustics(x, y, m_, ks, g, zo)
+    wworst = 0.0
+    for j, idx in enumerate(pairs):
+        wworst = max(wworst, float(np.abs(wg[j] - wo[j][idx]).max()))
+    assert wworst < TOL, f"caustics differ by {wworst}"
+    assert it.min() >= 0
+    return worst, wworst, rep
+
+
+def test_small_field_mixed():
+    f = synth.workload_small().fields[0]
+    worst, wworst, rep = _check_against_oracle(f.x, f.y, f.m, f.kappa_s, f.gamma, 1000)
+    assert rep["unconverged"] == 0 and rep["uncertified"] == 0 and rep["seam_ambiguous"] == 0
+
+
+def test_small_field_fp64():
+    f = synth.workload_small().fields[0]
+    _check_against_oracle(f.x, f.y, f.m, f.kappa_s, f.gamma, 1000, precision=cc.CC_FP64, hp_arith=cc.CC_HP_FP64)
+
+
+def test_small_field_mixed_native_fp64_polish():
+    f = synth.workload_small().fields[0]
+    _check_against_oracle(f.x, f.y, f.m, f.kappa_s, f.gamma, 200, hp_arith=cc.CC_HP_FP64)
+
+
+@pytest.mark.parametrize("n,msteps,subchains,ks,g,mass", [
+    (1, 2, 0, 0.0, 0.3, "unit"),
+    (1, 64, 3, 0.3, 1.3, "unit"),
+    (2, 10, 1, 0.0, 0.1, "loguniform"),
+    (3, 98, 7, 0.2, 0.6, "loguniform"),
+    (17, 40, 0, 0.1, 0.05, "unit"),
+    (33, 26, 13, 0.0, 0.45, "loguniform"),
+])
+def test_ragged_sizes(n, msteps, subchains, ks, g, mass):
+    f = synth.disc_field(n, 0.3, ks, g, synth.stream_seed(9, n), mass)
+    _check_against_oracle(f.x, f.y, f.m, ks, g, msteps, subchains=subchains)
+
+
+def test_no_predictor_and_small_blocks():
+    f = synth.disc_field(40, 0.5, 0.1, 0.3, synth.stream_seed(10, 1), "loguniform")
+    _check_against_oracle(f.x, f.y, f.m, 0.1, 0.3, 60, predictor=0, block_threads=64)
+
+
+@pytest.mark.parametrize("sep,loops", [(0.6, 3), (1.8, 1), (4.0, 2)])
+def test_binary_topology_from_gpu_chains(sep, loops):
+    """Chains joined across sub-ranges still close into 3 / 1 / 2 loops."""
+    x = np.array([-sep / 2, sep / 2])
+    zg, _, _, status, rep = _solve(x, np.zeros(2), np.ones(2), 0.0, 0.0, 400, subchains=8)
+    assert status == cc.CC_OK and rep["seam_ambiguous"] == 0
+    found, _ = lm.join_chains(zg)
+    assert len(found) == loops
+    # each chain is continuous: consecutive rows move by much less than the root spacing
+    steps = np.abs(np.diff(zg, axis=0))
+    assert steps.max() < 0.2
+
+
+def test_chains_continuous_across_seams():
+    f = synth.disc_field(60, 0.4, 0.0, 0.4, synth.stream_seed(11, 0), "loguniform")
+    zg, _, _, status, rep = _solve(f.x, f.y, f.m, 0.0, 0.4, 2000, subchains=16)
+    assert status == cc.CC_OK and rep["seam_ambiguous"] == 0
+    zo, _, _ = oracle.critical_curves(f.x, f.y, f.m, 0.0, 0.4, 2000)
+    # same chain decomposition: per-step jumps of the GPU chains are as small as the oracle's
+    assert np.abs(np.diff(zg, axis=0)).max() <= 1.01 * np.abs(np.diff(zo, axis=0)).max() + 1e-12
+
+
+def test_map_caustics_standalone():
+    f = synth.workload_small().fields[0]
+    u = synth.uniform(123, 2 * 5000)
+    z = (u[0::2] - 0.5) * 12 + 1j * (u[1::2] - 0.5) * 12
+    zs = f.x + 1j * f.y
+    z = z[np.min(np.abs(z[:, None] - zs[None, :]), axis=1) > 0.05]
+    for hp in (cc.CC_HP_DFLOAT, cc.CC_HP_FP64):
+        field = cc.cc_field_create(f.x, f.y, f.m, f.kappa_s, f.gamma, _opts(hp_arith=hp))
+        zt = torch.from_numpy(z).cuda()
+        wt = torch.empty_like(zt)
+        cc.cc_map_caustics(field, zt, wt)
+        wo = oracle.map_caustics(f.x, f.y, f.m, f.kappa_s, f.gamma, z)
+        assert np.abs(wt.cpu().numpy() - wo).max() < TOL
+
+
+def test_crossing_map_bit_exact_on_oracle_vertices():
+    f = synth.workload_small().fields[0]
+    zo, _, _ = oracle.critical_curves(f.x, f.y, f.m, f.kappa_s, f.gamma, 1000)
+    wo = oracle.map_caustics(f.x, f.y, f.m, f.kappa_s, f.gamma, zo)
+    ref = oracle.crossing_map(wo, -3, 3, -3, 3, 256, 256)
+    got = cc.crossing_map(torch.from_numpy(wo).cuda(), -3, 3, -3, 3, 256, 256).cpu().numpy()
+    assert np.array_equal(got, ref)
+    assert ref.max() >= 1 and ref.min() >= 0
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 37), (29, 1), (33, 17), (64, 65)])
+def test_crossing_map_ragged_grids(W, H):
+    u = synth.uniform(400 + W + H, 2 * 41 * 5)
+    w = ((u[0::2] - 0.5) * 6 + 1j * (u[1::2] - 0.5) * 6).reshape(41, 5)
+    ref = oracle.crossing_map(w, -2.0, 2.5, -2.2, 1.9, W, H)
+    got = cc.crossing_map(torch.from_numpy(w).cuda(), -2.0, 2.5, -2.2, 1.9, W, H).cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+def test_crossing_map_vertices_on_pixel_centres():
+    """Vertices and edges through pixel centres exercise the exact predicate and the
+    half-open row rule."""
+    W = H = 16
+    xs = [oracle.pixel_center(-1, 1, W, i) for i in range(W)]
+    ys = [oracle.pixel_center(-1, 1, H, r) for r in range(H)]
+    poly = np.array([xs[2] + 1j * ys[3], xs[2] + 1j * ys[12], xs[13] + 1j * ys[12], xs[13] + 1j * ys[3],
+                     xs[7] + 1j * ys[7], xs[2] + 1j * ys[3]])
+    w = np.stack([poly, poly[::-1]], axis=1)  # clockwise and counter-clockwise copies
+    w2 = poly[:, None]
+    for ww in (w, w2):
+        ref = oracle.crossing_map(ww, -1, 1, -1, 1, W, H)
+        got = cc.crossing_map(torch.from_numpy(np.ascontiguousarray(ww)).cuda(), -1, 1, -1, 1, W, H).cpu().numpy()
+        assert np.array_equal(got, ref)
+
+
+def test_crossing_map_long_and_outside_segments():
+    w = np.array([[-50 - 50j, 0.1 + 0j], [50 + 40j, 30 + 0.5j], [-50 + 60j, 0.2 + 1j], [-50 - 50j, 0.1 + 0j]])
+    ref = oracle.crossing_map(w, -1, 1, -1, 1, 40, 30)
+    got = cc.crossing_map(torch.from_numpy(w).cuda(), -1, 1, -1, 1, 40, 30).cpu().numpy()
+    assert np.array_equal(got, ref)
+    empty = torch.zeros((1, 3), dtype=torch.complex128, device="cuda")
+    assert int(cc.crossing_map(empty, -1, 1, -1, 1, 8, 8).abs().sum()) == 0
+
+
+@pytest.mark.parametrize("W,H,density", [(1, 1, 0.0), (1, 50, 0.05), (50, 1, 0.05), (64, 48, 0.01),
+                                         (200, 130, 0.001), (97, 101, 0.0)])
+def test_distance_map_bit_exact(W, H, density):
+    u = synth.uniform(77 + W * H, W * H).reshape(H, W)
+    ncc = (u < density).astype(np.int32)
+    ncc[: H // 2, : W // 3] += 2 if density > 0 else 0
+    ref = oracle.distance_map(ncc, 0.0123)
+    got = cc.distance_map(torch.from_numpy(ncc).cuda(), 0.0123).cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+def test_degenerate_and_invalid_arguments():
+    f = synth.workload_small().fields[0]
+    field = cc.cc_field_create(f.x, f.y, f.m, f.kappa_s, f.gamma)
+    z = torch.empty((12, field.n_roots), dtype=torch.complex128, device="cuda")
+    with pytest.raises(cc.CCError) as e:
+        cc.cc_critical_curves(field, 11, z, workspace=cc.workspace(16))
+    assert e.value.status == cc.CC_EINVAL
+    z = torch.empty((11, field.n_roots), dtype=torch.complex128, device="cuda")
+    with pytest.raises(cc.CCError) as e:
+        cc.cc_critical_curves(field, 10, z, workspace=cc.workspace(16))
+    assert e.value.status == cc.CC_ENOMEM
+    with pytest.raises(cc.CCError):
+        cc.crossing_map(torch.zeros((2, 2), dtype=torch.complex128, device="cuda"), 1, -1, 0, 1, 4, 4)
+
+
+def test_device_star_arrays_accepted():
+    f = synth.workload_small().fields[0]
+    field = cc.cc_field_create(torch.from_numpy(f.x).cuda(), torch.from_numpy(f.y).cuda(),
+                               torch.from_numpy(f.m).cuda(), f.kappa_s, f.gamma)
+    z, _, _ = cc.critical_curves(field, 20, caustics=False)
+    zo, _, _ = oracle.critical_curves(f.x, f.y, f.m, f.kappa_s, f.gamma, 20)
+    compare_chain(z.cpu().numpy(), zo, TOL)
