@@ -66,7 +66,7 @@ typedef struct cc_options {
     double tol_abs;      /* freeze a root when |z^{a+1} - z^a| < tol_abs (Sec. 3.2 footnote: 1e-9) */
     double mu_max;       /* also freeze when |mu| > mu_max (Sec. 3.2 footnote: 1e9); 0 = off.
                             Used by CC_FP64 only; the mixed form never freezes on |mu|. */
-    double tol_cert;     /* polish stops when the estimated Newton error < tol_cert (2e-11) */
+    double tol_cert;     /* polish stops when the estimated Newton error < tol_cert (1e-10) */
     int32_t max_iter_cold; /* Aberth iteration cap at a subchain's centre row (500) */
     int32_t max_iter_warm; /* cap for warm-started rows (200) */
     int32_t max_polish;    /* polish passes per point (4) */

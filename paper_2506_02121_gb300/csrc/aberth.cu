@@ -182,8 +182,10 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                     for (int j = tid; j < tn; j += P) x.s_star[j] = gs[t0 + j];
                     __syncthreads();
                 }
-                if (valid)
+                if (valid) {
+#pragma unroll 4
                     for (int j = lane; j < tn; j += g) acc_star(z.x, z.y, x.s_star[j], acc);
+                }
             }
             for (int t0 = 0; t0 < nr; t0 += TR) {
                 const int tn = min(TR, nr - t0);
@@ -195,6 +197,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 __syncthreads();
                 if (valid) {
                     const C* rr = x.s_root + d * TR;
+#pragma unroll 4
                     for (int j = lane; j < tn; j += g) acc_root(z.x, z.y, rr[j], acc);
                 }
             }

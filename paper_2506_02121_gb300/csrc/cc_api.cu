@@ -126,7 +126,7 @@ int cc_options_default(cc_options* opt) {
     if (!opt) return fail(CC_EINVAL, "cc_options_default: opt is NULL");
     opt->tol_abs = 1e-9;
     opt->mu_max = 0.0;
-    opt->tol_cert = 2e-11;
+    opt->tol_cert = 1e-10;
     opt->max_iter_cold = 500;
     opt->max_iter_warm = 200;
     opt->max_polish = 4;
