@@ -177,6 +177,27 @@ int cc_distance_map_workspace_bytes(int32_t W, int32_t H, size_t* bytes);
 int cc_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, double* d_out,
                     void* workspace, size_t workspace_bytes, cc_stream_t stream);
 
+/* Largest map (W * H pixels) that cc_distance_map_static accepts. */
+#define CC_DISTANCE_MAP_STATIC_MAX_PIXELS 1048576
+
+/* The distance map of cc_distance_map, for callers that cannot allocate device memory
+ * when they call it (a plugin whose host application owns all device memory through its
+ * own allocator, a process whose device-memory budget is fully reserved, a loop that must
+ * never enter the allocator).  The paper has no counterpart: this is an interface of this
+ * library only.  The call allocates nothing: its scratch is a fixed array of
+ * CC_DISTANCE_MAP_STATIC_MAX_PIXELS * 8 + 512 bytes in this library's device memory,
+ * held by every GPU that loads the library until the process exits.
+ *   ncc, d_out, W, H, pixel: as for cc_distance_map (caller-allocated device buffers).
+ * The first call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture on the device.  All calls
+ * share the one array and it keeps the last call's contents (nothing needs clearing:
+ * every scratch entry is written before it is read); calls that overlap on the GPU race
+ * on it, so order them on one stream or serialise them.
+ * Errors: CC_EINVAL (W * H > CC_DISTANCE_MAP_STATIC_MAX_PIXELS, NULL, bad size or
+ *         pixel), CC_ECUDA. */
+int cc_distance_map_static(const int32_t* ncc, int32_t W, int32_t H, double pixel, double* d_out,
+                           cc_stream_t stream);
+
 /* Last error message of this thread ("" if none). */
 const char* cc_last_error(void);
 

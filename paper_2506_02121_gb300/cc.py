@@ -68,6 +68,7 @@ _sig = {
     "cc_crossing_map": ([_vp, _i64, _i64, _dbl, _dbl, _dbl, _dbl, _i32, _i32, _vp, _vp], ctypes.c_int),
     "cc_distance_map_workspace_bytes": ([_i32, _i32, ctypes.POINTER(_sz)], ctypes.c_int),
     "cc_distance_map": ([_vp, _i32, _i32, _dbl, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "cc_distance_map_static": ([_vp, _i32, _i32, _dbl, _vp, _vp], ctypes.c_int),
     "cc_last_error": ([], ctypes.c_char_p),
     "cc_version": ([], ctypes.c_char_p),
 }
@@ -225,6 +226,18 @@ def cc_distance_map(ncc, pixel: float, d_out, workspace, stream=None):
     _check(_lib.cc_distance_map(_dev_ptr(ncc, torch.int32), int(W), int(H), float(pixel),
                                 _dev_ptr(d_out, torch.float64, (H, W)), _ptr(workspace),
                                 workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+DISTANCE_MAP_STATIC_MAX_PIXELS = 1048576
+
+
+def cc_distance_map_static(ncc, pixel: float, d_out, stream=None):
+    """Distance map for callers that cannot allocate device memory: the library's fixed
+    static scratch replaces the workspace (maps up to DISTANCE_MAP_STATIC_MAX_PIXELS
+    pixels).  Allocates nothing; ncc and d_out are the caller's buffers."""
+    H, W = ncc.shape
+    _check(_lib.cc_distance_map_static(_dev_ptr(ncc, torch.int32), int(W), int(H), float(pixel),
+                                       _dev_ptr(d_out, torch.float64, (H, W)), _stream(stream)))
 
 
 # --------------------------------------------------------------------------------------

@@ -120,6 +120,8 @@ bool finite3(double a, double b, double c) { return std::isfinite(a) && std::isf
 
 }  // namespace
 
+int ccg::api_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 int cc_options_default(cc_options* opt) {

@@ -105,6 +105,9 @@ size_t distance_workspace_bytes(int32_t W, int32_t H);
 cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel,
                                 double* d_out, void* ws, cudaStream_t st);
 
+// Set the thread's last-error message (as the C ABI functions do) and return code.
+int api_error(int code, const char* msg);
+
 // Subchain of a row: rows [b_s, b_{s+1}) belong to s, row m to S-1; b_s = floor(s m / S).
 __host__ __device__ __forceinline__ int64_t subchain_begin(int64_t s, int64_t m, int64_t S) {
     return (s * m) / S;
