@@ -305,7 +305,9 @@ def run_ours(args):
         "stages_ms": {k: round(v, 3) for k, v in stage.items()},
         "kernels": extra,
         "accuracy": {"max_err_est": rep["max_err_est"], "uncertified": rep["uncertified"],
-                     "unconverged": rep["unconverged"], "status_ok": status_ok},
+                     "unconverged": rep["unconverged"], "status_ok": status_ok,
+                     "polish_passes_per_point": round(rep["polish_passes"] / roots_per_step, 4),
+                     "tracer_iterations_per_point": round(rep["root_iterations"] / roots_per_step, 4)},
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
         "wall_s": round(wall, 3),

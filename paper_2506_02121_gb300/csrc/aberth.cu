@@ -417,11 +417,33 @@ size_t tracer_work_stride(int64_t nr, size_t elem) {
     return (b + 255) / 256 * 256;
 }
 
-int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms) {
+// Tracing CTAs that fit on one SM at once (registers and shared memory).
+int tracer_blocks_per_sm(bool fp64, int threads) {
+    int b = 0;
+    const size_t smem = tracer_smem_bytes(fp64);
+    cudaError_t e;
+    if (fp64) {
+        e = cudaFuncSetAttribute(trace_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<double>, threads, smem);
+    } else {
+        e = cudaFuncSetAttribute(trace_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_kernel<float>, threads, smem);
+    }
+    if (e != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
+int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms, int blocks_per_sm) {
     int64_t S = o.subchains;
     if (S <= 0) {
-        // two resident tracing CTAs per SM; each subchain keeps at least 8 rows
-        S = 2 * (int64_t)sms;
+        // one wave of tracing CTAs (every sub-range pays one cold start); each sub-range
+        // keeps at least 8 rows
+        S = (int64_t)sms * (blocks_per_sm < 1 ? 1 : blocks_per_sm);
         if (S > m / 8) S = m / 8;
     }
     if (S > m / 2) S = m / 2;

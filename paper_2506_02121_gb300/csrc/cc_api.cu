@@ -63,6 +63,17 @@ int sm_count(int device) {
     return cache[device];
 }
 
+// Resident tracing CTAs per SM, per (device, precision, block size); cached.
+int tracer_occupancy(int device, bool fp64, int threads) {
+    static std::mutex mu;
+    static std::vector<int> cache;  // index: (device * 2 + fp64) * 17 + threads / 32
+    std::lock_guard<std::mutex> lk(mu);
+    const size_t key = ((size_t)device * 2 + (fp64 ? 1 : 0)) * 17 + (size_t)(threads / 32);
+    if (cache.size() <= key) cache.resize(key + 1, 0);
+    if (cache[key] == 0) cache[key] = tracer_blocks_per_sm(fp64, threads);
+    return cache[key];
+}
+
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Workspace layout of cc_critical_curves.
@@ -71,8 +82,8 @@ CurveLayout curve_layout(const cc_field* f, int64_t m) {
     const int64_t nr = 2 * f->dev.n;
     const bool fp64 = f->opt.precision == CC_FP64;
     L.elem = fp64 ? sizeof(double2) : sizeof(float2);
-    L.S = subchain_count(m, nr, f->opt, sm_count(f->device));
     L.threads = f->opt.block_threads > 0 ? f->opt.block_threads : 512;
+    L.S = subchain_count(m, nr, f->opt, sm_count(f->device), tracer_occupancy(f->device, fp64, L.threads));
     L.work_stride = tracer_work_stride(nr, L.elem);
     size_t o = 0;
     L.off_report = o;

@@ -54,7 +54,8 @@ struct CurveLayout {
 
 size_t tracer_work_stride(int64_t nr, size_t elem);
 size_t tracer_smem_bytes(bool fp64);
-int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms);
+int tracer_blocks_per_sm(bool fp64, int threads);
+int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms, int blocks_per_sm);
 
 cudaError_t launch_phase_table(double2* phase, int64_t m, cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st);

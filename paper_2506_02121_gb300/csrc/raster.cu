@@ -123,7 +123,20 @@ struct CrossK {
     double x0, sx, y0, sy;
     int W, H;
     int* D;
+    float y0f, inv_syf;  // FP32 copies for the quick rejection test
 };
+
+// True when [lo, hi) certainly contains no pixel-centre row (FP32 estimate of the
+// continuous row index with a margin that covers its rounding; undecided cases go to
+// the exact test).
+__device__ __forceinline__ bool no_row_between(const CrossK& K, double lo, double hi) {
+    const float flo = (float)lo, fhi = (float)hi;
+    const float tl = (flo - K.y0f) * K.inv_syf - 0.5f;
+    const float th = (fhi - K.y0f) * K.inv_syf - 0.5f;
+    const float eps = 1e-3f + 1e-6f * ((fabsf(flo) + fabsf(K.y0f)) * fabsf(K.inv_syf) + fabsf(tl) + fabsf(th));
+    if (!(th + eps >= 0.0f) || !(tl - eps <= (float)K.H)) return true;  // outside the map's rows
+    return ceilf(tl - eps) > th + eps;                                   // no integer in between
+}
 
 __global__ void __launch_bounds__(256) crossing_scatter_kernel(CrossK K) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -133,6 +146,7 @@ __global__ void __launch_bounds__(256) crossing_scatter_kernel(CrossK K) {
     if (a.y == b.y) return;
     const bool up = a.y < b.y;
     const double lo = up ? a.y : b.y, hi = up ? b.y : a.y;
+    if (no_row_between(K, lo, hi)) return;
     const int64_t r0 = first_at_or_above(K.y0, K.sy, K.H, lo);
     const int64_t r1 = first_at_or_above(K.y0, K.sy, K.H, hi);
     const int sgn = up ? 1 : -1;
@@ -211,6 +225,8 @@ cudaError_t launch_crossing_map(const double2* w, int64_t rows, int64_t nr, doub
         K.W = W;
         K.H = H;
         K.D = ncc;
+        K.y0f = (float)y0;
+        K.inv_syf = (float)(1.0 / K.sy);
         const int64_t segs = (rows - 1) * nr;
         crossing_scatter_kernel<<<(unsigned)((segs + 255) / 256), 256, 0, st>>>(K);
         e = cudaGetLastError();
@@ -234,25 +250,115 @@ __device__ __forceinline__ bool feature_at(const int32_t* ncc, int W, int H, int
     return false;
 }
 
-// g[r][i] = |r - nearest feature row in column i| (DIST_INF if the column has none).
-__global__ void edt_column_kernel(const int32_t* ncc, int W, int H, int32_t* g) {
+constexpr int EDT_CHUNK = 128;  // rows per column-pass chunk
+
+// Feature flags (1 byte per pixel) into the stack plane, which the row pass reuses later.
+__global__ void edt_feature_kernel(const int32_t* ncc, int W, int H, uint8_t* feat) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= (int64_t)W * H) return;
+    const int r = (int)(p / W), i = (int)(p - (int64_t)r * W);
+    feat[p] = feature_at(ncc, W, H, r, i) ? 1 : 0;
+}
+
+// First and last feature row of every (chunk, column); -1 when none.
+__global__ void edt_chunk_kernel(const uint8_t* feat, int W, int H, int2* summ) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
     if (i >= W) return;
-    int last = -1;
-    for (int r = 0; r < H; r++) {
-        if (feature_at(ncc, W, H, r, i)) last = r;
+    const int r0 = c * EDT_CHUNK, r1 = min(H, r0 + EDT_CHUNK);
+    int first = -1, last = -1;
+    for (int r = r0; r < r1; r++)
+        if (feat[(int64_t)r * W + i]) {
+            if (first < 0) first = r;
+            last = r;
+        }
+    summ[(int64_t)c * W + i] = make_int2(first, last);
+}
+
+// g[r][i] = |r - nearest feature row in column i| (DIST_INF if the column has none), one
+// thread per (chunk, column) seeded with the nearest features of the other chunks.
+__global__ void edt_column_kernel(const uint8_t* feat, const int2* summ, int W, int H, int nchunk,
+                                  int32_t* g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (i >= W) return;
+    int above = -1, below = -1;
+    for (int q = c - 1; q >= 0 && above < 0; q--) above = summ[(int64_t)q * W + i].y;
+    for (int q = c + 1; q < nchunk && below < 0; q++) below = summ[(int64_t)q * W + i].x;
+    const int r0 = c * EDT_CHUNK, r1 = min(H, r0 + EDT_CHUNK);
+    int last = above;
+    for (int r = r0; r < r1; r++) {
+        if (feat[(int64_t)r * W + i]) last = r;
         g[(int64_t)r * W + i] = last < 0 ? DIST_INF : r - last;
     }
-    int next = -1;
-    for (int r = H - 1; r >= 0; r--) {
+    int next = below;
+    for (int r = r1 - 1; r >= r0; r--) {
         const int64_t o = (int64_t)r * W + i;
-        const int gv = g[o];
-        if (gv == 0) next = r;
-        if (next >= 0 && next - r < gv) g[o] = next - r;
+        if (feat[o]) next = r;
+        if (next >= 0 && next - r < g[o]) g[o] = next - r;
     }
 }
 
-// Row pass: lower envelope of parabolas q -> (i - q)^2 + g[q]^2 over the finite g[q].
+__device__ __forceinline__ long long edt_key(const int32_t* f, int q) {
+    return (long long)f[q] * f[q] + (long long)q * q;
+}
+
+// Row pass, one warp per row: the row's g values and the envelope stack live in shared
+// memory; lane 0 builds the lower envelope of the parabolas (i - q)^2 + g[q]^2 (exact
+// integer comparisons of the intersection abscissae), then every lane finds the owning
+// parabola of its pixels by binary search over the envelope and writes the distance.
+constexpr int EDT_ROW_SMEM_MAX_W = 12288;
+__global__ void __launch_bounds__(32) edt_row_smem_kernel(const int32_t* g, int W, int H, double pixel,
+                                                          double* d_out) {
+    extern __shared__ int32_t sh[];
+    int32_t* f = sh;       // [W]
+    int32_t* v = sh + W;   // [W]
+    __shared__ int s_k;
+    const int r = blockIdx.x;
+    const int lane = threadIdx.x;
+    const int32_t* gr = g + (int64_t)r * W;
+    for (int q = lane; q < W; q += 32) f[q] = gr[q];
+    __syncwarp();
+    if (lane == 0) {
+        int k = -1;
+        for (int q = 0; q < W; q++) {
+            if (f[q] >= DIST_INF) continue;
+            const long long fq = edt_key(f, q);
+            while (k >= 1) {
+                const int p = v[k], pp = v[k - 1];
+                const long long n1 = fq - edt_key(f, p), d1 = 2LL * (q - p);
+                const long long n2 = edt_key(f, p) - edt_key(f, pp), d2 = 2LL * (p - pp);
+                if (n1 * d2 <= n2 * d1) k--;
+                else break;
+            }
+            v[++k] = q;
+        }
+        s_k = k;
+    }
+    __syncwarp();
+    const int k = s_k;
+    double* out = d_out + (int64_t)r * W;
+    if (k < 0) {
+        for (int i = lane; i < W; i += 32) out[i] = __longlong_as_double(0x7ff0000000000000LL);
+        return;
+    }
+    for (int i = lane; i < W; i += 32) {
+        // largest j in [0, k] whose left boundary s(v[j-1], v[j]) is <= i (boundary of j = 0 is -inf)
+        int lo = 0, hi = k;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const int p = v[mid - 1], q = v[mid];
+            const long long n = edt_key(f, q) - edt_key(f, p), d = 2LL * (q - p);
+            if (n <= (long long)i * d) lo = mid;  // s <= i: parabola mid owns i (ties: either is minimal)
+            else hi = mid - 1;
+        }
+        const int p = v[lo];
+        const long long d2 = (long long)(i - p) * (i - p) + (long long)f[p] * f[p];
+        out[i] = pixel * sqrt((double)d2);
+    }
+}
+
+// Row pass for very wide maps: one thread per row, envelope stack in global memory.
 __global__ void edt_row_kernel(const int32_t* g, int W, int H, double pixel, int32_t* vstack,
                                double* d_out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -260,16 +366,14 @@ __global__ void edt_row_kernel(const int32_t* g, int W, int H, double pixel, int
     const int32_t* f = g + (int64_t)r * W;
     int32_t* v = vstack + (int64_t)r * W;
     double* out = d_out + (int64_t)r * W;
-    // intersection abscissa of parabolas p < q: num / den, den = 2 (q - p) > 0
-    auto key = [&](int q) -> long long { return (long long)f[q] * f[q] + (long long)q * q; };
     int k = -1;
     for (int q = 0; q < W; q++) {
         if (f[q] >= DIST_INF) continue;
-        const long long fq = key(q);
+        const long long fq = edt_key(f, q);
         while (k >= 1) {
             const int p = v[k], pp = v[k - 1];
-            const long long n1 = fq - key(p), d1 = 2LL * (q - p);        // s(p, q)
-            const long long n2 = key(p) - key(pp), d2 = 2LL * (p - pp);   // s(pp, p)
+            const long long n1 = fq - edt_key(f, p), d1 = 2LL * (q - p);
+            const long long n2 = edt_key(f, p) - edt_key(f, pp), d2 = 2LL * (p - pp);
             if (n1 * d2 <= n2 * d1) k--;
             else break;
         }
@@ -283,7 +387,7 @@ __global__ void edt_row_kernel(const int32_t* g, int W, int H, double pixel, int
     for (int i = 0; i < W; i++) {
         while (j < k) {
             const int p = v[j], q = v[j + 1];
-            const long long n = key(q) - key(p), d = 2LL * (q - p);
+            const long long n = edt_key(f, q) - edt_key(f, p), d = 2LL * (q - p);
             if (n < (long long)i * d) j++;
             else break;
         }
@@ -298,15 +402,34 @@ size_t distance_workspace_bytes(int32_t W, int32_t H) {
     return 2 * plane;
 }
 
+// Scratch: plane 0 = g (int32 per pixel); plane 1 = feature flags (bytes) during the
+// column pass, then the envelope stacks of the global-memory row pass.  The chunk
+// summaries of the column pass live in d_out, which the row pass overwrites entirely.
 cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel,
                                 double* d_out, void* ws, cudaStream_t st) {
     const size_t plane = ((size_t)W * H * sizeof(int32_t) + 255) / 256 * 256;
     int32_t* g = (int32_t*)ws;
     int32_t* v = (int32_t*)((char*)ws + plane);
-    edt_column_kernel<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(ncc, W, H, g);
+    uint8_t* feat = (uint8_t*)v;
+    int2* summ = (int2*)d_out;  // nchunk * W int2 <= W * H doubles
+    const int nchunk = (H + EDT_CHUNK - 1) / EDT_CHUNK;
+    const int64_t npx = (int64_t)W * H;
+    edt_feature_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(ncc, W, H, feat);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    edt_row_kernel<<<(unsigned)((H + 63) / 64), 64, 0, st>>>(g, W, H, pixel, v, d_out);
+    dim3 cg((unsigned)((W + 127) / 128), (unsigned)nchunk);
+    edt_chunk_kernel<<<cg, 128, 0, st>>>(feat, W, H, summ);
+    edt_column_kernel<<<cg, 128, 0, st>>>(feat, summ, W, H, nchunk, g);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (W <= EDT_ROW_SMEM_MAX_W) {
+        const size_t smem = 2 * sizeof(int32_t) * (size_t)W;
+        e = cudaFuncSetAttribute(edt_row_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        edt_row_smem_kernel<<<(unsigned)H, 32, smem, st>>>(g, W, H, pixel, d_out);
+    } else {
+        edt_row_kernel<<<(unsigned)((H + 63) / 64), 64, 0, st>>>(g, W, H, pixel, v, d_out);
+    }
     return cudaGetLastError();
 }
 
