@@ -177,6 +177,48 @@ int cc_distance_map_workspace_bytes(int32_t W, int32_t H, size_t* bytes);
 int cc_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, double* d_out,
                     void* workspace, size_t workspace_bytes, cc_stream_t stream);
 
+/* ---------------------------------------------------------------------------------
+ * Batched critical curves: many fields of uneven N in one persistent launch (each field
+ * as cc_critical_curves computes it; the paper solves one field at a time, Sec. 4.4).
+ * Work items are (field, phi sub-range) pairs sized in proportion to each field's work
+ * and handed out most expensive first to the resident CTAs of one launch; the chain
+ * joining and the polish then run once over all fields.
+ * --------------------------------------------------------------------------------- */
+typedef struct cc_batch cc_batch;
+
+/* Plan a batch of count fields (all CC_MIXED, one device) with m[f] phi steps each.
+ * The fields must outlive the batch.  Tolerances and caps come from fields[0]'s options.
+ * Tile shape: block_threads (tracing CTA size, multiple of 32 in [32, 512]; 0 = the
+ * field's option or 512) and items_per_cta (work items per resident CTA the fields are cut
+ * into, 0 = 4); an autotuner may pick both.  Errors: CC_EINVAL, CC_ECUDA. */
+int cc_batch_create(cc_field* const* fields, int32_t count, const int64_t* m, int32_t block_threads,
+                    int32_t items_per_cta, cc_batch** out);
+
+/* Device scratch bytes the batch needs (tables, tracer rows, joins, per-field reports). */
+int cc_batch_workspace_bytes(const cc_batch* batch, size_t* bytes);
+
+/* Bind outputs and workspace: z_out[f] / w_out[f] are device pointers to (m[f]+1) x n_r[f]
+ * complex128 (w_out may be NULL, or hold NULL entries); workspace >= the size above,
+ * 256-byte aligned.  Uploads the batch's device tables (blocking).  Errors: CC_EINVAL,
+ * CC_ENOMEM, CC_ECUDA. */
+int cc_batch_bind(cc_batch* batch, double* const* z_out, double* const* w_out, void* workspace,
+                  size_t workspace_bytes);
+
+/* Enqueue the whole batch on stream.  use_graph != 0: the launch sequence is captured
+ * once into a CUDA graph (per stream; needs a non-default stream) and replayed on later
+ * calls; rebinding discards the graph.  Errors: CC_EINVAL, CC_ECUDA. */
+int cc_batch_launch(cc_batch* batch, int32_t use_graph, cc_stream_t stream);
+
+/* Wait for the last launch; per_field (count entries) and total may be NULL.  Stage times
+ * are in total.  Returns CC_OK, CC_ENOCONV or CC_ETIMEOUT like cc_field_report. */
+int cc_batch_report(cc_batch* batch, cc_report* per_field, cc_report* total);
+
+/* Work items, persistent grid size and block size of the batch. */
+int cc_batch_info(const cc_batch* batch, int32_t* items, int32_t* grid, int32_t* threads);
+
+/* Free the batch (not the fields, outputs or workspace). */
+int cc_batch_destroy(cc_batch* batch);
+
 /* Largest map (W * H pixels) that cc_distance_map_static accepts. */
 #define CC_DISTANCE_MAP_STATIC_MAX_PIXELS 1048576
 

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libccgpu.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["cc_api.cu", "aberth.cu", "polish.cu", "raster.cu", "static_scratch.cu"]
+SOURCES = ["cc_api.cu", "aberth.cu", "polish.cu", "raster.cu", "static_scratch.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

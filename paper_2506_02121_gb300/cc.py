@@ -69,6 +69,13 @@ _sig = {
     "cc_distance_map_workspace_bytes": ([_i32, _i32, ctypes.POINTER(_sz)], ctypes.c_int),
     "cc_distance_map": ([_vp, _i32, _i32, _dbl, _vp, _vp, _sz, _vp], ctypes.c_int),
     "cc_distance_map_static": ([_vp, _i32, _i32, _dbl, _vp, _vp], ctypes.c_int),
+    "cc_batch_create": ([ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), _i32, _i32, ctypes.POINTER(_vp)], ctypes.c_int),
+    "cc_batch_workspace_bytes": ([_vp, ctypes.POINTER(_sz)], ctypes.c_int),
+    "cc_batch_bind": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _sz], ctypes.c_int),
+    "cc_batch_launch": ([_vp, _i32, _vp], ctypes.c_int),
+    "cc_batch_report": ([_vp, ctypes.POINTER(Report), ctypes.POINTER(Report)], ctypes.c_int),
+    "cc_batch_info": ([_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)], ctypes.c_int),
+    "cc_batch_destroy": ([_vp], ctypes.c_int),
     "cc_last_error": ([], ctypes.c_char_p),
     "cc_version": ([], ctypes.c_char_p),
 }
@@ -238,6 +245,93 @@ def cc_distance_map_static(ncc, pixel: float, d_out, stream=None):
     H, W = ncc.shape
     _check(_lib.cc_distance_map_static(_dev_ptr(ncc, torch.int32), int(W), int(H), float(pixel),
                                        _dev_ptr(d_out, torch.float64, (H, W)), _stream(stream)))
+
+
+class Batch:
+    """Owner of a cc_batch handle; keeps its fields, outputs and workspace alive."""
+
+    def __init__(self, handle, fields, msteps):
+        self._h = handle
+        self.fields = list(fields)
+        self.msteps = list(msteps)
+        self.z = self.w = self.workspace = None
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("batch was destroyed")
+        return self._h
+
+    def __del__(self):
+        try:
+            cc_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def cc_batch_create(fields, msteps, block_threads: int = 0, items_per_cta: int = 0) -> Batch:
+    n = len(fields)
+    hs = (ctypes.c_void_p * n)(*[f.handle for f in fields])
+    ms = (ctypes.c_int64 * n)(*[int(v) for v in msteps])
+    h = ctypes.c_void_p()
+    _check(_lib.cc_batch_create(hs, n, ms, int(block_threads), int(items_per_cta), ctypes.byref(h)))
+    return Batch(h, fields, msteps)
+
+
+def cc_batch_workspace_bytes(batch: Batch) -> int:
+    b = _sz()
+    _check(_lib.cc_batch_workspace_bytes(batch.handle, ctypes.byref(b)))
+    return b.value
+
+
+def cc_batch_bind(batch: Batch, z_out, w_out, workspace):
+    n = len(batch.fields)
+    for f, (fld, m) in enumerate(zip(batch.fields, batch.msteps)):
+        _dev_ptr(z_out[f], torch.complex128, (m + 1, fld.n_roots))
+        if w_out is not None and w_out[f] is not None:
+            _dev_ptr(w_out[f], torch.complex128, (m + 1, fld.n_roots))
+    zp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in z_out])
+    wp = None
+    if w_out is not None:
+        wp = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in w_out])
+    _check(_lib.cc_batch_bind(batch.handle, zp, wp, _ptr(workspace), workspace.numel() * workspace.element_size()))
+    batch.z, batch.w, batch.workspace = z_out, w_out, workspace
+
+
+def cc_batch_launch(batch: Batch, use_graph: bool = False, stream=None):
+    _check(_lib.cc_batch_launch(batch.handle, 1 if use_graph else 0, _stream(stream)))
+
+
+def cc_batch_report(batch: Batch):
+    n = len(batch.fields)
+    per = (Report * n)()
+    tot = Report()
+    st = _check(_lib.cc_batch_report(batch.handle, per, ctypes.byref(tot)), allow=(CC_ENOCONV, CC_ETIMEOUT))
+    return st, [p.as_dict() for p in per], tot.as_dict()
+
+
+def cc_batch_info(batch: Batch):
+    a, b, c = _i32(), _i32(), _i32()
+    _check(_lib.cc_batch_info(batch.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"items": a.value, "grid": b.value, "threads": c.value}
+
+
+def cc_batch_destroy(batch: Batch):
+    if batch._h is not None:
+        _lib.cc_batch_destroy(batch._h)
+        batch._h = None
+
+
+def batch_critical_curves(fields, msteps, caustics: bool = True, use_graph: bool = False, stream=None,
+                          block_threads: int = 0, items_per_cta: int = 0):
+    """Plan, bind and launch a batch; returns the Batch (outputs in batch.z / batch.w)."""
+    b = cc_batch_create(fields, msteps, block_threads, items_per_cta)
+    z = [torch.empty((m + 1, f.n_roots), dtype=torch.complex128, device="cuda") for f, m in zip(fields, msteps)]
+    w = [torch.empty_like(t) for t in z] if caustics else None
+    ws = workspace(cc_batch_workspace_bytes(b))
+    cc_batch_bind(b, z, w, ws)
+    cc_batch_launch(b, use_graph, stream)
+    return b
 
 
 # --------------------------------------------------------------------------------------

@@ -306,15 +306,17 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
     }
 }
 
+// One sub-range s of one field, start to end, by the whole CTA: cold start at its centre
+// row, then both directions row by row.  w: this CTA's Jacobi scratch.
 template <typename T>
-__global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
+__device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, unsigned char* smem,
+                                             int* s_count_p, int* s_maxit_p) {
     using C = typename CT<T>::C;
     using Star = typename CT<T>::Star;
     constexpr int TS = CT<T>::TS;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_count, s_maxit;
+    int& s_count = *s_count_p;
+    int& s_maxit = *s_maxit_p;
     const int tid = threadIdx.x, P = blockDim.x;
-    const int s = blockIdx.x;
     const int nr = K.nr, n = K.n;
     const int64_t b0 = subchain_begin(s, K.m, K.S), b1 = subchain_begin(s + 1, K.m, K.S);
     const int64_t c = (b0 + b1) / 2;
@@ -323,7 +325,6 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
     x.k = &K;
     x.s_star = (Star*)smem;
     x.s_root = (C*)(smem + sizeof(Star) * TS);
-    char* w = K.work + (size_t)s * K.work_stride;
     x.cur = (C*)w;
     x.nxt = x.cur + 2 * nr;
     x.prev = x.nxt + 2 * nr;
@@ -335,7 +336,6 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
     const Star* gs = (const Star*)K.stars;
     if (x.resident)
         for (int j = tid; j < n; j += P) x.s_star[j] = gs[j];
-    if (tid == 0) s_maxit = 0;
 
     seed_guesses<T>(x, 0);
     for (int k = tid; k < nr; k += P) x.conv[nr + k] = 1;
@@ -404,7 +404,56 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
         }
     }
     __syncthreads();
-    if (tid == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_count, s_maxit;
+    if (threadIdx.x == 0) s_maxit = 0;
+    run_subchain<T>(K, blockIdx.x, K.work + (size_t)blockIdx.x * K.work_stride, smem, &s_count, &s_maxit);
+    if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
+}
+
+// Many fields in one persistent launch: resident CTAs take (field, sub-range) items from a
+// global counter, most expensive first, until the list is exhausted (a bounded loop).
+template <typename T>
+__global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_count, s_maxit, s_item;
+    char* w = (char*)B.work + (size_t)blockIdx.x * B.work_stride;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(B.queue, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= B.nitems) break;
+        const int2 fs = B.items[item];
+        const TraceTask& t = B.tasks[fs.x];
+        TK K;
+        K.stars = t.stars;
+        K.n = t.n;
+        K.nr = t.nr;
+        K.kappa_s = t.kappa_s;
+        K.gamma = t.gamma;
+        K.m = t.m;
+        K.S = t.S;
+        K.phase = t.phase;
+        K.zrows = t.zrows;
+        K.seam = t.seam;
+        K.iters = t.iters;
+        K.work = nullptr;
+        K.work_stride = 0;
+        K.rep = t.rep;
+        K.tol_abs = B.tol_abs;
+        K.mu_max = 0.0;
+        K.max_iter_cold = B.max_iter_cold;
+        K.max_iter_warm = B.max_iter_warm;
+        K.predictor = B.predictor;
+        if (threadIdx.x == 0) s_maxit = 0;
+        run_subchain<T>(K, fs.y, w, smem, &s_count, &s_maxit);
+        if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
+    }
 }
 
 size_t tracer_smem_bytes(bool fp64) {
@@ -493,13 +542,10 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
 // permutations are composed so that global column g follows one chain across all rows.
 // ----------------------------------------------------------------------------------
 template <typename C, typename T>
-__global__ void seam_match_kernel(const C* zrows, const C* seam, int64_t m, int S, int nr,
-                                  int32_t* match, int32_t* hits, DevReport* rep) {
+__device__ __forceinline__ void seam_match_one(const C* zrows, const C* seam, int64_t m, int S, int nr, int s,
+                                               int k, int32_t* match, int32_t* hits, DevReport* rep) {
     // Distances in the tracer's own precision: roots of one row are separated by far more
     // than the tracer's rounding error, so FP32 suffices for the mixed form.
-    const int s = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nr) return;
     const int64_t row = subchain_begin(s + 1, m, S);
     const C q = seam[(size_t)s * nr + k];
     const C* B = zrows + (size_t)row * nr;
@@ -522,8 +568,26 @@ __global__ void seam_match_kernel(const C* zrows, const C* seam, int64_t m, int 
     if (!(best <= (T)1e-4 * second)) atomicAdd(&rep->seam_ambiguous, 1ull);
 }
 
-__global__ void compose_perm_kernel(int S, int nr, const int32_t* match, const int32_t* hits,
-                                    int32_t* perm, DevReport* rep) {
+template <typename C, typename T>
+__global__ void seam_match_kernel(const C* zrows, const C* seam, int64_t m, int S, int nr,
+                                  int32_t* match, int32_t* hits, DevReport* rep) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nr) return;
+    seam_match_one<C, T>(zrows, seam, m, S, nr, blockIdx.y, k, match, hits, rep);
+}
+
+// Batched: blockIdx.y indexes all seams of all fields.
+__global__ void seam_match_batch_kernel(const TraceTask* tasks, const int2* seams) {
+    const int2 fs = seams[blockIdx.y];
+    const TraceTask& t = tasks[fs.x];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= t.nr) return;
+    seam_match_one<float2, float>((const float2*)t.zrows, (const float2*)t.seam, t.m, t.S, t.nr, fs.y, k,
+                                  t.match, t.hits, t.rep);
+}
+
+__device__ __forceinline__ void compose_perm_body(int S, int nr, const int32_t* match, const int32_t* hits,
+                                                  int32_t* perm, DevReport* rep) {
     const int tid = threadIdx.x, P = blockDim.x;
     for (int g = tid; g < nr; g += P) perm[g] = g;
     for (int s = 0; s + 1 < S; s++) {
@@ -535,6 +599,16 @@ __global__ void compose_perm_kernel(int S, int nr, const int32_t* match, const i
         }
         if (bad) atomicAdd(&rep->seam_ambiguous, (unsigned long long)bad);
     }
+}
+
+__global__ void compose_perm_kernel(int S, int nr, const int32_t* match, const int32_t* hits,
+                                    int32_t* perm, DevReport* rep) {
+    compose_perm_body(S, nr, match, hits, perm, rep);
+}
+
+__global__ void compose_perm_batch_kernel(const TraceTask* tasks) {
+    const TraceTask& t = tasks[blockIdx.x];
+    compose_perm_body(t.S, t.nr, t.match, t.hits, t.perm, t.rep);
 }
 
 cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int S, int64_t nr,
@@ -554,6 +628,54 @@ cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int
         if (e != cudaSuccess) return e;
     }
     compose_perm_kernel<<<1, 1024, 0, st>>>(S, (int)nr, match, hits, perm, rep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_batch(const BatchTraceArgs& b, int grid, int threads, cudaStream_t st) {
+    const size_t smem = tracer_smem_bytes(false);
+    cudaError_t e = cudaFuncSetAttribute(trace_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    trace_batch_kernel<float><<<grid, threads, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seam_join_batch(const TraceTask* tasks, int count, const int2* seams, int nseams, int max_nr,
+                                   cudaStream_t st) {
+    if (nseams > 0) {
+        dim3 grid((unsigned)((max_nr + 255) / 256), (unsigned)nseams);
+        seam_match_batch_kernel<<<grid, 256, 0, st>>>(tasks, seams);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    compose_perm_batch_kernel<<<count, 1024, 0, st>>>(tasks);
+    return cudaGetLastError();
+}
+
+int tracer_batch_blocks_per_sm(int threads) {
+    int b = 0;
+    const size_t smem = tracer_smem_bytes(false);
+    cudaError_t e = cudaFuncSetAttribute(trace_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_batch_kernel<float>, threads, smem);
+    if (e != cudaSuccess || b < 1) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b;
+}
+
+__global__ void phase_batch_kernel(const TraceTask* tasks, int count) {
+    const TraceTask& t = tasks[blockIdx.y];
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j > t.m) return;
+    const double p = 2.0 * 3.14159265358979323846 * (double)j / (double)t.m;
+    double sn, cs;
+    sincos(p, &sn, &cs);
+    ((double2*)t.phase)[j] = make_double2(cs, sn);
+}
+
+cudaError_t launch_phase_batch(const TraceTask* tasks, int count, int64_t max_m, cudaStream_t st) {
+    dim3 grid((unsigned)((max_m + 1 + 255) / 256), (unsigned)count);
+    phase_batch_kernel<<<grid, 256, 0, st>>>(tasks, count);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,414 @@
+// Batched critical curves: many fields of uneven N in one persistent tracing launch, one
+// batched seam join and one batched polish, optionally replayed as a CUDA graph.
+//
+// Work items are (field, sub-range) pairs.  Each field gets a number of phi sub-ranges in
+// proportion to its estimated work (rows x n_r x (N + n_r)), so that items are of similar
+// size, and the items are handed out most expensive first (longest-processing-time order)
+// from a global counter to the resident CTAs of one persistent launch.  Tables, scratch
+// and per-field reports all live in the caller's workspace; the library allocates nothing
+// after cc_batch_create.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "cc_internal.h"
+
+using namespace ccg;
+
+
+struct cc_batch {
+    int count = 0;
+    std::vector<const cc_field*> fields;
+    std::vector<FieldDev> dev;
+    std::vector<int64_t> m, nr, rows;
+    std::vector<int> S;
+    int device = 0;
+    cc_options opt;
+    int threads = 512, grid = 1;
+    int nitems = 0, nseams = 0, max_nr = 0;
+    int64_t max_m = 0, total_blocks = 0;
+    // workspace layout
+    std::vector<size_t> off_phase, off_zrows, off_seam, off_iters, off_match, off_perm, off_hits;
+    size_t hits_begin = 0, hits_bytes = 0;
+    size_t off_tasks = 0, off_items = 0, off_seams = 0, off_ptasks = 0, off_reps = 0, off_queue = 0, off_work = 0;
+    size_t work_stride = 0, total = 0;
+    // bound buffers
+    bool bound = false;
+    char* ws = nullptr;
+    // graph
+    bool graph_ok = false;
+    cudaStream_t graph_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool launched = false;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+
+int berr(int code, const char* msg) { return api_error(code, msg); }
+
+void drop_graph(cc_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_ok = false;
+}
+
+// Event records inside a stream capture become external event-record nodes, so that they
+// also fire when the graph is replayed.
+cudaError_t rec(cudaEvent_t ev, cudaStream_t st, bool capturing) {
+    return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
+}
+
+cudaError_t enqueue(cc_batch* b, cudaStream_t st, bool capturing) {
+    char* ws = b->ws;
+    cudaError_t e;
+    if ((e = rec(b->ev[0], st, capturing)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws + b->off_reps, 0, sizeof(DevReport) * b->count, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws + b->off_queue, 0, 256, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws + b->hits_begin, 0, b->hits_bytes, st)) != cudaSuccess) return e;
+    const TraceTask* tasks = (const TraceTask*)(ws + b->off_tasks);
+    if ((e = launch_phase_batch(tasks, b->count, b->max_m, st)) != cudaSuccess) return e;
+    BatchTraceArgs a;
+    a.tasks = tasks;
+    a.items = (const int2*)(ws + b->off_items);
+    a.nitems = b->nitems;
+    a.queue = (unsigned int*)(ws + b->off_queue);
+    a.work = ws + b->off_work;
+    a.work_stride = b->work_stride;
+    a.tol_abs = b->opt.tol_abs;
+    a.max_iter_cold = b->opt.max_iter_cold;
+    a.max_iter_warm = b->opt.max_iter_warm;
+    a.predictor = b->opt.predictor;
+    if ((e = launch_trace_batch(a, b->grid, b->threads, st)) != cudaSuccess) return e;
+    if ((e = rec(b->ev[1], st, capturing)) != cudaSuccess) return e;
+    if ((e = launch_seam_join_batch(tasks, b->count, (const int2*)(ws + b->off_seams), b->nseams, b->max_nr, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = rec(b->ev[2], st, capturing)) != cudaSuccess) return e;
+    if ((e = launch_polish_batch(ws + b->off_ptasks, b->count, b->total_blocks, st)) != cudaSuccess) return e;
+    return rec(b->ev[3], st, capturing);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_batch_create(cc_field* const* fields, int32_t count, const int64_t* m, int32_t block_threads,
+                    int32_t items_per_cta, cc_batch** out) {
+    if (!out) return berr(CC_EINVAL, "cc_batch_create: out is NULL");
+    *out = nullptr;
+    if (!fields || !m || count < 1) return berr(CC_EINVAL, "cc_batch_create: need count >= 1 fields and m values");
+    if (block_threads != 0 && (block_threads < 32 || block_threads > 512 || (block_threads & 31)))
+        return berr(CC_EINVAL, "cc_batch_create: block_threads must be 0 or a multiple of 32 in [32, 512]");
+    if (items_per_cta < 0 || items_per_cta > 64) return berr(CC_EINVAL, "cc_batch_create: items_per_cta in [0, 64]");
+    cc_batch* b = new cc_batch();
+    b->count = count;
+    double total_cost = 0;
+    std::vector<double> cost(count);
+    for (int f = 0; f < count; f++) {
+        if (!fields[f]) {
+            delete b;
+            return berr(CC_EINVAL, "cc_batch_create: NULL field");
+        }
+        int dev = 0;
+        cc_options o;
+        const FieldDev* fd = field_dev(fields[f], &dev, &o);
+        if (o.precision != CC_MIXED) {
+            delete b;
+            return berr(CC_EINVAL, "cc_batch_create: batched launches use the mixed (FP32 + polish) form");
+        }
+        if (m[f] < 2 || (m[f] & 1) || m[f] > ((int64_t)1 << 30)) {
+            delete b;
+            return berr(CC_EINVAL, "cc_batch_create: every m must be even and >= 2");
+        }
+        if (f == 0) {
+            b->device = dev;
+            b->opt = o;
+        } else if (dev != b->device) {
+            delete b;
+            return berr(CC_EINVAL, "cc_batch_create: all fields must live on one device");
+        }
+        b->fields.push_back(fields[f]);
+        b->dev.push_back(*fd);
+        b->m.push_back(m[f]);
+        b->nr.push_back(2 * fd->n);
+        b->rows.push_back(m[f] + 1);
+        cost[f] = (double)(m[f] + 1) * (double)(2 * fd->n) * (double)(3 * fd->n);
+        total_cost += cost[f];
+        b->max_nr = std::max<int>(b->max_nr, (int)(2 * fd->n));
+        b->max_m = std::max<int64_t>(b->max_m, m[f]);
+    }
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) {
+        delete b;
+        return berr(CC_ECUDA, "cc_batch_create: cudaSetDevice failed");
+    }
+    b->threads = block_threads > 0 ? block_threads : (b->opt.block_threads > 0 ? b->opt.block_threads : 512);
+    int sms = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+    b->grid = sms * tracer_batch_blocks_per_sm(b->threads);
+    // sub-ranges per field: about items_per_cta (default 4) items per resident CTA overall,
+    // each field's items of similar size; a sub-range keeps >= 32 rows so its cold start
+    // stays a small overhead
+    const double target = total_cost / ((items_per_cta > 0 ? items_per_cta : 4) * (double)b->grid);
+    for (int f = 0; f < count; f++) {
+        int64_t Sf = b->opt.subchains > 0 ? b->opt.subchains : (int64_t)std::ceil(cost[f] / std::max(target, 1.0));
+        Sf = std::min<int64_t>(Sf, std::max<int64_t>(1, b->m[f] / 32));
+        Sf = std::min<int64_t>(Sf, b->m[f] / 2);
+        Sf = std::max<int64_t>(Sf, 1);
+        b->S.push_back((int)Sf);
+        b->nitems += (int)Sf;
+    }
+    // workspace layout
+    size_t o = 0;
+    b->off_reps = o;
+    o += a256(sizeof(DevReport) * count);
+    b->off_queue = o;
+    o += 256;
+    b->off_tasks = o;
+    o += a256(sizeof(TraceTask) * count);
+    b->off_items = o;
+    o += a256(sizeof(int2) * b->nitems);
+    for (int f = 0; f < count; f++) b->nseams += b->S[f] - 1;
+    b->off_seams = o;
+    o += a256(sizeof(int2) * std::max(1, b->nseams));
+    b->off_ptasks = o;
+    o += a256(polish_task_bytes() * count);
+    b->hits_begin = o;
+    for (int f = 0; f < count; f++) {
+        b->off_hits.push_back(o);
+        o += a256(sizeof(int32_t) * (size_t)b->S[f] * b->nr[f]);
+    }
+    b->hits_bytes = o - b->hits_begin;
+    for (int f = 0; f < count; f++) {
+        const size_t nrf = (size_t)b->nr[f];
+        b->off_phase.push_back(o);
+        o += a256(sizeof(double2) * (size_t)b->rows[f]);
+        b->off_zrows.push_back(o);
+        o += a256(sizeof(float2) * (size_t)b->rows[f] * nrf);
+        b->off_seam.push_back(o);
+        o += a256(sizeof(float2) * (size_t)b->S[f] * nrf);
+        b->off_iters.push_back(o);
+        o += a256(sizeof(int32_t) * (size_t)b->rows[f] * nrf);
+        b->off_match.push_back(o);
+        o += a256(sizeof(int32_t) * (size_t)b->S[f] * nrf);
+        b->off_perm.push_back(o);
+        o += a256(sizeof(int32_t) * (size_t)b->S[f] * nrf);
+    }
+    b->work_stride = tracer_work_stride(b->max_nr, sizeof(float2));
+    b->off_work = o;
+    o += b->work_stride * (size_t)b->grid;
+    b->total = o;
+    for (int i = 0; i < 4; i++) {
+        if (cudaEventCreate(&b->ev[i]) != cudaSuccess) {
+            cc_batch_destroy(b);
+            return berr(CC_ECUDA, "cc_batch_create: cudaEventCreate failed");
+        }
+    }
+    *out = b;
+    return CC_OK;
+}
+
+int cc_batch_destroy(cc_batch* b) {
+    if (!b) return CC_OK;
+    drop_graph(b);
+    for (int i = 0; i < 4; i++)
+        if (b->ev[i]) cudaEventDestroy(b->ev[i]);
+    delete b;
+    return CC_OK;
+}
+
+int cc_batch_workspace_bytes(const cc_batch* b, size_t* bytes) {
+    if (!b || !bytes) return berr(CC_EINVAL, "cc_batch_workspace_bytes: NULL argument");
+    *bytes = b->total;
+    return CC_OK;
+}
+
+int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void* workspace, size_t workspace_bytes) {
+    if (!b || !z_out || !workspace) return berr(CC_EINVAL, "cc_batch_bind: NULL argument");
+    if ((uintptr_t)workspace % 256) return berr(CC_EINVAL, "cc_batch_bind: workspace must be 256-byte aligned");
+    if (workspace_bytes < b->total) return berr(CC_ENOMEM, "cc_batch_bind: workspace too small");
+    for (int f = 0; f < b->count; f++)
+        if (!z_out[f]) return berr(CC_EINVAL, "cc_batch_bind: NULL z_out entry");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return berr(CC_ECUDA, "cc_batch_bind: cudaSetDevice failed");
+    char* ws = (char*)workspace;
+    std::vector<TraceTask> tasks(b->count);
+    std::vector<unsigned char> ptasks(polish_task_bytes() * b->count);
+    std::vector<int2> seams;
+    std::vector<std::pair<double, int2>> items;
+    int64_t block0 = 0;
+    for (int f = 0; f < b->count; f++) {
+        const FieldDev& fd = b->dev[f];
+        TraceTask& t = tasks[f];
+        t.stars = fd.star32;
+        t.n = (int)fd.n;
+        t.nr = (int)b->nr[f];
+        t.kappa_s = fd.kappa_s;
+        t.gamma = fd.gamma;
+        t.m = b->m[f];
+        t.S = b->S[f];
+        t.phase = (const double2*)(ws + b->off_phase[f]);
+        t.zrows = ws + b->off_zrows[f];
+        t.seam = ws + b->off_seam[f];
+        t.iters = (int32_t*)(ws + b->off_iters[f]);
+        t.match = (int32_t*)(ws + b->off_match[f]);
+        t.hits = (int32_t*)(ws + b->off_hits[f]);
+        t.perm = (int32_t*)(ws + b->off_perm[f]);
+        t.rep = (DevReport*)(ws + b->off_reps) + f;
+        for (int s = 0; s + 1 < b->S[f]; s++) seams.push_back(make_int2(f, s));
+        const double cost = (double)b->rows[f] * (double)b->nr[f] * (double)(3 * fd.n);
+        const double per = cost / (double)b->S[f] + 20.0 * (double)b->nr[f] * (double)(3 * fd.n);
+        for (int s = 0; s < b->S[f]; s++) items.push_back({per, make_int2(f, s)});
+        PolishArgs pa;
+        pa.f = &b->dev[f];
+        pa.m = b->m[f];
+        pa.S = b->S[f];
+        pa.nr = b->nr[f];
+        pa.phase = t.phase;
+        pa.zrows = (const float2*)t.zrows;
+        pa.perm = t.perm;
+        pa.iters_in = t.iters;
+        pa.z_out = (double2*)z_out[f];
+        pa.w_out = w_out ? (double2*)w_out[f] : nullptr;
+        pa.iters_out = nullptr;
+        pa.rep = t.rep;
+        pa.tol_cert = b->opt.tol_cert;
+        pa.max_polish = b->opt.max_polish;
+        pa.hp_fp64 = 0;
+        polish_task_fill(pa, block0, ptasks.data() + polish_task_bytes() * f);
+        block0 += polish_blocks(b->rows[f] * b->nr[f]);
+    }
+    b->total_blocks = block0;
+    std::stable_sort(items.begin(), items.end(), [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
+        return x.first > y.first;
+    });
+    std::vector<int2> it(items.size());
+    for (size_t i = 0; i < items.size(); i++) it[i] = items[i].second;
+    b->nseams = (int)seams.size();
+    if ((e = cudaMemcpy(ws + b->off_tasks, tasks.data(), sizeof(TraceTask) * b->count, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(ws + b->off_items, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice)) ||
+        (seams.size() && (e = cudaMemcpy(ws + b->off_seams, seams.data(), sizeof(int2) * seams.size(),
+                                         cudaMemcpyHostToDevice))) ||
+        (e = cudaMemcpy(ws + b->off_ptasks, ptasks.data(), ptasks.size(), cudaMemcpyHostToDevice)))
+        return berr(CC_ECUDA, cudaGetErrorString(e));
+    b->ws = ws;
+    b->bound = true;
+    drop_graph(b);
+    return CC_OK;
+}
+
+int cc_batch_launch(cc_batch* b, int32_t use_graph, cc_stream_t stream) {
+    if (!b) return berr(CC_EINVAL, "cc_batch_launch: batch is NULL");
+    if (!b->bound) return berr(CC_EINVAL, "cc_batch_launch: call cc_batch_bind first");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return berr(CC_ECUDA, "cc_batch_launch: cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!use_graph) {
+        e = enqueue(b, st, false);
+        if (e != cudaSuccess) return berr(CC_ECUDA, cudaGetErrorString(e));
+        b->launched = true;
+        b->last_stream = st;
+        return CC_OK;
+    }
+    if (!st) return berr(CC_EINVAL, "cc_batch_launch: graph replay needs a non-default stream");
+    if (!b->graph_ok || b->graph_stream != st) {
+        drop_graph(b);
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return berr(CC_ECUDA, cudaGetErrorString(e));
+        cudaError_t eq = enqueue(b, st, true);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (eq != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return berr(CC_ECUDA, cudaGetErrorString(eq != cudaSuccess ? eq : e));
+        }
+        b->graph = g;
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (e != cudaSuccess) {
+            drop_graph(b);
+            return berr(CC_ECUDA, cudaGetErrorString(e));
+        }
+        b->graph_ok = true;
+        b->graph_stream = st;
+    }
+    e = cudaGraphLaunch(b->exec, st);
+    if (e != cudaSuccess) return berr(CC_ECUDA, cudaGetErrorString(e));
+    b->launched = true;
+    b->last_stream = st;
+    return CC_OK;
+}
+
+int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
+    if (!b) return berr(CC_EINVAL, "cc_batch_report: batch is NULL");
+    if (!b->launched) return berr(CC_EINVAL, "cc_batch_report: nothing launched yet");
+    cudaError_t e = cudaStreamSynchronize(b->last_stream);
+    if (e != cudaSuccess) return berr(CC_ECUDA, cudaGetErrorString(e));
+    std::vector<DevReport> r(b->count);
+    e = cudaMemcpy(r.data(), b->ws + b->off_reps, sizeof(DevReport) * b->count, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return berr(CC_ECUDA, cudaGetErrorString(e));
+    float t01 = 0, t12 = 0, t23 = 0;
+    if (cudaEventElapsedTime(&t01, b->ev[0], b->ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t12, b->ev[1], b->ev[2]) != cudaSuccess ||
+        cudaEventElapsedTime(&t23, b->ev[2], b->ev[3]) != cudaSuccess) {
+        cudaGetLastError();  // stage times unavailable: leave them at zero
+        t01 = t12 = t23 = 0;
+    }
+    cc_report tot;
+    memset(&tot, 0, sizeof tot);
+    bool bad = false;
+    for (int f = 0; f < b->count; f++) {
+        cc_report q;
+        memset(&q, 0, sizeof q);
+        q.rows = b->rows[f];
+        q.n_roots = b->nr[f];
+        q.subchains = b->S[f];
+        q.root_iterations = (int64_t)r[f].root_iterations;
+        q.cold_root_iterations = (int64_t)r[f].cold_root_iterations;
+        q.unconverged = (int64_t)r[f].unconverged;
+        q.polish_passes = (int64_t)r[f].polish_passes;
+        q.uncertified = (int64_t)r[f].uncertified;
+        q.seam_ambiguous = (int64_t)r[f].seam_ambiguous;
+        q.max_iter_row = r[f].max_iter_row;
+        q.timeout = r[f].timeout;
+        q.max_err_est = r[f].max_err_est;
+        if (per_field) per_field[f] = q;
+        tot.rows += q.rows;
+        tot.n_roots += q.n_roots;
+        tot.subchains += q.subchains;
+        tot.root_iterations += q.root_iterations;
+        tot.cold_root_iterations += q.cold_root_iterations;
+        tot.unconverged += q.unconverged;
+        tot.polish_passes += q.polish_passes;
+        tot.uncertified += q.uncertified;
+        tot.seam_ambiguous += q.seam_ambiguous;
+        tot.max_iter_row = std::max(tot.max_iter_row, q.max_iter_row);
+        tot.timeout |= q.timeout;
+        tot.max_err_est = std::max(tot.max_err_est, q.max_err_est);
+        bad = bad || q.unconverged || q.uncertified;
+    }
+    tot.trace_ms = t01;
+    tot.join_ms = t12;
+    tot.polish_ms = t23;
+    if (total) *total = tot;
+    if (tot.timeout) return berr(CC_ETIMEOUT, "a device-side wait gave up");
+    if (bad) return berr(CC_ENOCONV, "some fields have unconverged or uncertified points");
+    return CC_OK;
+}
+
+int cc_batch_info(const cc_batch* b, int32_t* items, int32_t* grid, int32_t* threads) {
+    if (!b) return berr(CC_EINVAL, "cc_batch_info: batch is NULL");
+    if (items) *items = b->nitems;
+    if (grid) *grid = b->grid;
+    if (threads) *threads = b->threads;
+    return CC_OK;
+}
+
+}  // extern "C"

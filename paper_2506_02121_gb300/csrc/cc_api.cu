@@ -133,6 +133,12 @@ bool finite3(double a, double b, double c) { return std::isfinite(a) && std::isf
 
 int ccg::api_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+const FieldDev* ccg::field_dev(const cc_field* f, int* device, cc_options* opt) {
+    if (device) *device = f->device;
+    if (opt) *opt = f->opt;
+    return &f->dev;
+}
+
 extern "C" {
 
 int cc_options_default(cc_options* opt) {

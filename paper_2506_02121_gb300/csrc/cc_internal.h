@@ -42,6 +42,38 @@ struct TraceArgs {
     int threads;
 };
 
+// One field of a batched launch (device table entry).
+struct TraceTask {
+    const void* stars;     // FP32 star records
+    int n, nr;
+    double kappa_s, gamma;
+    int64_t m;
+    int S;
+    const double2* phase;
+    void* zrows;
+    void* seam;
+    int32_t* iters;
+    int32_t *match, *hits, *perm;
+    DevReport* rep;
+};
+
+struct BatchTraceArgs {
+    const TraceTask* tasks;
+    const int2* items;      // (field, sub-range), most expensive first
+    int nitems;
+    unsigned int* queue;    // work counter, zero before the launch
+    void* work;
+    size_t work_stride;
+    double tol_abs;
+    int max_iter_cold, max_iter_warm, predictor;
+};
+
+int tracer_batch_blocks_per_sm(int threads);
+cudaError_t launch_phase_batch(const TraceTask* tasks, int count, int64_t max_m, cudaStream_t st);
+cudaError_t launch_trace_batch(const BatchTraceArgs& b, int grid, int threads, cudaStream_t st);
+cudaError_t launch_seam_join_batch(const TraceTask* tasks, int count, const int2* seams, int nseams, int max_nr,
+                                   cudaStream_t st);
+
 // Workspace layout of cc_critical_curves (byte offsets from the workspace base).
 struct CurveLayout {
     int S;
@@ -82,6 +114,12 @@ struct PolishArgs {
     int hp_fp64;            // 1: native FP64 star sums, 0: double-float
 };
 cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st);
+// Batched polish: a device table of per-field task records (polish_task_bytes() each,
+// filled on the host by polish_task_fill), blocks of all fields in one launch.
+int64_t polish_blocks(int64_t points);
+size_t polish_task_bytes();
+void polish_task_fill(const PolishArgs& a, int64_t first_block, void* out);
+cudaError_t launch_polish_batch(const void* tasks, int count, int64_t total_blocks, cudaStream_t st);
 
 struct FinalizeArgs {
     int64_t m;
@@ -105,6 +143,9 @@ cudaError_t launch_crossing_map(const double2* w, int64_t rows, int64_t nr, doub
 size_t distance_workspace_bytes(int32_t W, int32_t H);
 cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel,
                                 double* d_out, void* ws, cudaStream_t st);
+
+// Device description, device index and options of a field (cc_field is opaque elsewhere).
+const FieldDev* field_dev(const cc_field* f, int* device, cc_options* opt);
 
 // Set the thread's last-error message (as the C ABI functions do) and return code.
 int api_error(int code, const char* msg);

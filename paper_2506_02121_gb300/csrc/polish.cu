@@ -14,6 +14,7 @@
 // High precision is either double-float (FP32 pairs on the FP32 pipes; GB300 runs FP64
 // at ~1/70 of the FP32 rate) or native FP64.
 #include <float.h>
+#include <string.h>
 
 #include "cc_internal.h"
 
@@ -40,6 +41,8 @@ struct PolishK {
     DevReport* rep;
     double tol_cert;
     int max_polish;
+    int unit_mass;        // batched launches: all masses equal to 1
+    int64_t first_block;  // batched launches: first block of this field
 };
 
 struct Sums {
@@ -167,14 +170,14 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
 }
 
 template <bool UNIT, bool FP64>
-__global__ void __launch_bounds__(PB_THREADS) polish_kernel(PolishK K) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk, unsigned char* smem,
+                                            unsigned long long* s_passes_p) {
     float4* sp = (float4*)smem;
     float2* sm = (float2*)(smem + TSB * sizeof(float4));
     StarD* sd = (StarD*)smem;
-    __shared__ unsigned long long s_passes;
+    unsigned long long& s_passes = *s_passes_p;
     const int tid = threadIdx.x;
-    const int64_t point = blockIdx.x * (int64_t)PB_THREADS + tid;
+    const int64_t point = blk * (int64_t)PB_THREADS + tid;
     const bool valid = point < K.points;
     int64_t row = 0;
     float z0x = 0.f, z0y = 0.f;
@@ -251,7 +254,31 @@ __global__ void __launch_bounds__(PB_THREADS) polish_kernel(PolishK K) {
     if (tid == 0 && s_passes) atomicAdd(&K.rep->polish_passes, s_passes);
 }
 
-cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st) {
+template <bool UNIT, bool FP64>
+__global__ void __launch_bounds__(PB_THREADS) polish_kernel(PolishK K) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_passes;
+    polish_body<UNIT, FP64>(K, blockIdx.x, smem, &s_passes);
+}
+
+// Batched: the blocks of all fields in one launch; each field's points start on a block
+// boundary, so every block polishes points of one field against that field's stars.
+__global__ void __launch_bounds__(PB_THREADS) polish_batch_kernel(const PolishK* tasks, int count) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_passes;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].first_block <= (int64_t)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    const PolishK K = tasks[lo];
+    const int64_t blk = (int64_t)blockIdx.x - K.first_block;
+    if (K.unit_mass) polish_body<true, false>(K, blk, smem, &s_passes);
+    else polish_body<false, false>(K, blk, smem, &s_passes);
+}
+
+static PolishK make_polish_k(const PolishArgs& a) {
     PolishK K;
     K.dfp = a.f->star_dfp;
     K.dfm = a.f->star_dfm;
@@ -273,6 +300,32 @@ cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st) {
     K.rep = a.rep;
     K.tol_cert = a.tol_cert;
     K.max_polish = a.max_polish < 1 ? 1 : a.max_polish;
+    K.unit_mass = a.f->unit_mass ? 1 : 0;
+    K.first_block = 0;
+    return K;
+}
+
+int64_t polish_blocks(int64_t points) { return (points + PB_THREADS - 1) / PB_THREADS; }
+
+size_t polish_task_bytes() { return sizeof(PolishK); }
+
+void polish_task_fill(const PolishArgs& a, int64_t first_block, void* out) {
+    PolishK K = make_polish_k(a);
+    K.first_block = first_block;
+    memcpy(out, &K, sizeof K);
+}
+
+cudaError_t launch_polish_batch(const void* tasks, int count, int64_t total_blocks, cudaStream_t st) {
+    if (total_blocks <= 0) return cudaSuccess;
+    const size_t smem = TSB * (sizeof(float4) + sizeof(float2));
+    cudaError_t e = cudaFuncSetAttribute(polish_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    polish_batch_kernel<<<(unsigned)total_blocks, PB_THREADS, smem, st>>>((const PolishK*)tasks, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st) {
+    PolishK K = make_polish_k(a);
     const unsigned blocks = (unsigned)((K.points + PB_THREADS - 1) / PB_THREADS);
     const size_t smem_df = TSB * (sizeof(float4) + sizeof(float2));
     const size_t smem_d = TSB * sizeof(StarD);
