@@ -53,6 +53,11 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU work for the oracle sample")
     p.add_argument("--msteps", type=int, default=0, help="override the phi steps m (smaller profiling runs)")
     p.add_argument("--map", type=int, default=0, help="override the map size (pixels per side)")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-served", action="store_true")
+    p.add_argument("--batched-fields", type=int, default=64)
+    p.add_argument("--batched-m", type=int, default=1000)
+    p.add_argument("--served-requests", type=int, default=48)
     return p.parse_args()
 
 
@@ -316,6 +321,10 @@ def run_ours(args):
         out["plain_fp64"] = plain_fp64(args, f, m, dev, xs, ys, ms, roots_per_step)
     if not args.no_e2e:
         out["e2e"] = e2e(args, f, m, ext, px, pixel, dev, world)
+    if not args.no_batched and rank == 0:
+        out["batched"] = batched(args, dev)
+    if not args.no_served and rank == 0:
+        out["served"] = served(args, dev)
     if not args.no_cpu_baseline and rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(f, m, args.cpu_seconds)
     if rank == 0:
@@ -392,6 +401,79 @@ def e2e(args, f, m, ext, px, pixel, dev, world):
     d2h = hz.numel() * 16 + hw.numel() * 16 + hn.numel() * 4 + hd.numel() * 8
     return {"value": round(world * rows * nr * steps / el, 1), "unit": UNIT, "steps": steps,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def batched(args, dev):
+    """Many fields in one persistent launch replayed as a CUDA graph: a sample of the
+    batched workload (fields with N log-uniform in [50, 5000], unit masses, kappa_* in
+    U[0.1, 0.8], gamma in U[0, 0.8], kappa_s in U[0, 0.3]), tile shape from the autotuner."""
+    import torch
+    from paper_2506_02121_gb300 import autotune, cc, synth
+    wl = synth.workload_batched(args.batched_fields, args.batched_m)
+    fields = [cc.cc_field_create(f.x, f.y, f.m, f.kappa_s, f.gamma) for f in wl.fields]
+    ms = [wl.msteps] * len(fields)
+    t, items, info = autotune.tune(fields, ms, probe_steps=32, repeats=1)
+    b = cc.cc_batch_create(fields, ms, t, items)
+    z = [torch.empty((m + 1, fl.n_roots), dtype=torch.complex128, device=dev) for fl, m in zip(fields, ms)]
+    w = [torch.empty_like(a) for a in z]
+    ws = cc.workspace(cc.cc_batch_workspace_bytes(b), dev)
+    cc.cc_batch_bind(b, z, w, ws)
+    stream = torch.cuda.Stream(dev)
+    cc.cc_batch_launch(b, True, stream)  # capture + first replay (warm-up)
+    stream.synchronize()
+    times = []
+    for _ in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cc.cc_batch_launch(b, True, stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    st, per, tot = cc.cc_batch_report(b)
+    roots = sum((m + 1) * fl.n_roots for fl, m in zip(fields, ms))
+    ms_ = min(times)
+    ninfo = cc.cc_batch_info(b)
+    del z, w, ws
+    torch.cuda.empty_cache()
+    return {"value": round(roots / (ms_ / 1e3), 1), "unit": UNIT, "ms": round(ms_, 2), "fields": len(fields),
+            "phi_steps": wl.msteps, "roots": roots, "items": ninfo["items"], "grid": ninfo["grid"],
+            "block_threads": t, "items_per_cta": items, "tuned_from_cache": info["cached"],
+            "status_ok": st == cc.CC_OK, "max_err_est": tot["max_err_est"],
+            "stages_ms": {"trace": round(tot["trace_ms"], 2), "join": round(tot["join_ms"], 2),
+                          "polish_caustic": round(tot["polish_ms"], 2)},
+            "workload": f"{len(fields)} fields of the batched distribution (N log-U[50,5000]), m={wl.msteps}, "
+                        f"one persistent launch replayed from a CUDA graph"}
+
+
+def served(args, dev):
+    """Continuous-batching server on a Poisson trace (50 req/s) of critical-curve + caustic +
+    1024^2 crossing-map requests with N log-uniform in [100, 20000], m = 200."""
+    import torch
+    from paper_2506_02121_gb300 import synth
+    from paper_2506_02121_gb300.serve import GpuExecutor, Request, Server, summarize
+    reqs = []
+    for i, (t, f) in enumerate(synth.served_requests(args.served_requests, 50.0)):
+        reqs.append(Request(rid=i, arrival=t, x=f.x, y=f.y, mass=f.m, kappa_s=f.kappa_s, gamma=f.gamma,
+                            msteps=200, map_extent=10.0, map_pixels=1024))
+    slots = 4
+    srv = Server(GpuExecutor(slots=slots, device=dev.index or 0), slots=slots, budget_bytes=96 << 30)
+    warm = Server(GpuExecutor(slots=1, device=dev.index or 0), slots=1, budget_bytes=96 << 30)
+    warm.run([reqs[0]], realtime=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = srv.run(reqs, realtime=True)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    st = summarize(res, wall)
+    out = {"value": round(st["roots_per_s"], 1) if st["roots_per_s"] else None, "unit": UNIT,
+           "p50_latency_s": round(st["p50_s"], 4) if st["p50_s"] is not None else None,
+           "p99_latency_s": round(st["p99_s"], 4) if st["p99_s"] is not None else None,
+           "requests": st["requests"], "ok": st["ok"], "errors": st["errors"], "noconv": st["noconv"],
+           "slots": slots, "arrival_rate_hz": 50.0, "wall_s": round(wall, 3),
+           "workload": "Poisson 50 req/s, N log-U[100,20000], log-U masses, m=200, 1024^2 maps over +-10"}
+    del srv
+    torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(f, m, seconds):

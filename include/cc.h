@@ -69,7 +69,8 @@ typedef struct cc_options {
     double tol_cert;     /* polish stops when the estimated Newton error < tol_cert (1e-10) */
     int32_t max_iter_cold; /* Aberth iteration cap at a subchain's centre row (500) */
     int32_t max_iter_warm; /* cap for warm-started rows (200) */
-    int32_t max_polish;    /* polish passes per point (4) */
+    int32_t max_polish;    /* polish passes per point (8); rows that still hold an uncertified
+                              point are re-solved by FP64 Aberth warm-started from the polish */
     int32_t precision;     /* cc_precision */
     int32_t hp_arith;      /* cc_hp_arith (polish and cc_map_caustics) */
     int32_t subchains;     /* phi sub-ranges grown in parallel (Sec. 4.3); 0 = automatic */
@@ -91,11 +92,15 @@ typedef struct cc_report {
     int64_t seam_ambiguous;    /* sub-range joins that were not a clean 1:1 match */
     int32_t max_iter_row;      /* largest per-root iteration count in any row */
     int32_t timeout;           /* nonzero if a bounded device wait gave up */
-    double max_err_est;        /* largest polish error estimate (theta_*) */
+    double max_err_est;        /* largest error estimate of a certified point (theta_*) */
     /* Device time of each stage of the last solve (CUDA events on the caller's stream):
      * tracing (Aberth), joining sub-ranges, polish + caustics (mixed form) or
      * reordering + caustics (FP64 form). */
     float trace_ms, join_ms, polish_ms;
+    int64_t rescued_points;    /* uncertified points re-solved by FP64 Aberth (root alone, the
+                                  rest of its row fixed) and now converged */
+    int64_t jumped;            /* points the polish moved > 1e-3 (1 + |z|) from the tracer's
+                                  root (a sign of a root swap; diagnostic) */
 } cc_report;
 
 /* Fill *opt with the defaults listed above. */

@@ -17,6 +17,7 @@
 // Two arithmetics: FP32 (the mixed form; its result is polished afterwards) and FP64 (the
 // plain form with the |dz| < tol stop rule of Sec. 3.2).
 #include <float.h>
+#include <string.h>
 
 #include "cc_internal.h"
 
@@ -41,6 +42,7 @@ constexpr int TR = 1024;  // roots per direction per shared-memory tile
 template <typename T>
 struct Acc {
     T Cx, Cy, Ax, Ay, Bx, By, Dx, Dy;
+    T Am;  // sum m/|d|^2 = sum |m/d^2|: scale of the rounding noise of F
 };
 
 __device__ __forceinline__ float recip(float x) { return rcp_approx(x); }
@@ -70,6 +72,7 @@ __device__ __forceinline__ void acc_star(T zx, T zy, const S& s, Acc<T>& a) {
     T mx = (T)s.z * tx, my = (T)s.z * ty;
     a.Ax += mx;
     a.Ay += my;
+    a.Am = fma((T)s.z, inv, a.Am);
     a.Bx = fma(mx, ux, fma(-my, uy, a.Bx));
     a.By = fma(mx, uy, fma(my, ux, a.By));
 }
@@ -173,7 +176,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             const int key = valid ? x.act[slot] : 0;
             const int d = key >= nr;
             const C z = x.cur[key];
-            Acc<T> acc = {0, 0, 0, 0, 0, 0, 0, 0};
+            Acc<T> acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             for (int t0 = 0; t0 < n; t0 += TS) {
                 const int tn = min(TS, n - t0);
                 if (!x.resident) {
@@ -210,6 +213,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 acc.By += shfl_x(acc.By, off);
                 acc.Dx += shfl_x(acc.Dx, off);
                 acc.Dy += shfl_x(acc.Dy, off);
+                acc.Am += shfl_x(acc.Am, off);
             }
             if (valid && lane == 0) {
                 const T cph = d ? cph1 : cph0, sph = d ? sph1 : sph0;
@@ -236,12 +240,20 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 atomicMax(s_maxit, its);
                 bool done;
                 if (sizeof(T) == 4) {
-                    // FP32: freeze at the absolute tolerance, at a few ulp of |z|, or when
-                    // the corrections stop shrinking near that level (rounding floor).
+                    // FP32: freeze at the absolute tolerance or at the rounding floor of this
+                    // root: a few ulp of |z|, or the FP32 noise of F (~eps sum |m/d^2|)
+                    // divided by |F'|; or when the corrections stop shrinking within a few
+                    // times that floor.
                     const T sc = (T)1 + qsqrt(z.x * z.x + z.y * z.y);
-                    const T tolz = fmax((T)K.tol_abs, (T)(8.0 * FLT_EPSILON) * sc);
+                    const T fpa = (T)2 * qsqrt(acc.Bx * acc.Bx + acc.By * acc.By);
+                    const T noise = (T)(4.0 * FLT_EPSILON) * (acc.Am + fabs(gam) + oms);
+                    T tolz = fmax((T)K.tol_abs, (T)(8.0 * FLT_EPSILON) * sc);
+                    if (fpa > (T)0) tolz = fmax(tolz, (T)4 * noise * qdiv((T)1, fpa));
+                    // never looser than 64x the ulp floor: an iterate that runs away where F'
+                    // vanishes must not count as converged
+                    tolz = fmin(tolz, (T)(512.0 * FLT_EPSILON) * sc);
                     done = !(ad >= tolz) ||
-                           (its >= 3 && ad > (T)0.25 * (T)x.dprev[key] && ad < (T)32 * tolz);
+                           (its >= 3 && ad > (T)0.25 * (T)x.dprev[key] && ad < (T)4 * tolz);
                 } else {
                     done = !(ad >= (T)K.tol_abs);
                     if (!done && K.mu_max > 0) {
@@ -628,6 +640,115 @@ cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int
         if (e != cudaSuccess) return e;
     }
     compose_perm_kernel<<<1, 1024, 0, st>>>(S, (int)nr, match, hits, perm, rep);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Rescue of points the polish could not certify: one warp per point runs FP64 Aberth
+// (the paper's arithmetic, stop at |dz| < tol_abs) on that root alone, the other roots of
+// its row held at their polished positions (Aberth's root sum keeps it from the others'
+// basins), then recomputes its caustic point with the FP64 lens equation.  An empty list
+// costs one small launch.
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) rescue_kernel(RescueTask t0, const RescueTask* tasks, const int4* list,
+                                                      const int* nlist, int max_list, double tol_abs, int max_iter) {
+    const int lane = threadIdx.x & 31;
+    const int nwarp = (gridDim.x * blockDim.x) >> 5;
+    const int nl = min(*nlist, max_list);
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < nl; e += nwarp) {
+        const int4 ent = list[e];
+        const RescueTask& t = tasks ? tasks[ent.x] : t0;
+        const int64_t row = ent.y;
+        const int col = ent.z;
+        const int nr = t.nr, n = t.n;
+        const double2* zr = t.z + (size_t)row * nr;
+        double zx = zr[col].x, zy = zr[col].y;
+        const double oms = 1.0 - t.kappa_s;
+        const double2 ph = t.phase[row];
+        bool conv = false;
+        for (int it = 0; it < max_iter && !conv; it++) {
+            double Cx = 0, Cy = 0, Ax = 0, Ay = 0, Bx = 0, By = 0, Dx = 0, Dy = 0;
+            for (int i = lane; i < n; i += 32) {
+                const StarD st = t.stars[i];
+                const double dx = zx - st.x, dy = zy - st.y;
+                const double inv = 1.0 / (dx * dx + dy * dy);
+                const double ux = dx * inv, uy = -dy * inv;
+                Cx += ux;
+                Cy += uy;
+                const double tx = ux * ux - uy * uy, ty = 2.0 * ux * uy;
+                const double mx = st.z * tx, my = st.z * ty;
+                Ax += mx;
+                Ay += my;
+                Bx += mx * ux - my * uy;
+                By += mx * uy + my * ux;
+            }
+            for (int r = lane; r < nr; r += 32) {
+                if (r == col) continue;
+                const double2 q = zr[r];
+                const double dx = zx - q.x, dy = zy - q.y;
+                const double r2 = dx * dx + dy * dy;
+                if (r2 > 0.0) {
+                    Dx += dx / r2;
+                    Dy -= dy / r2;
+                }
+            }
+            Cx = warp_sum_d(Cx);
+            Cy = warp_sum_d(Cy);
+            Ax = warp_sum_d(Ax);
+            Ay = warp_sum_d(Ay);
+            Bx = warp_sum_d(Bx);
+            By = warp_sum_d(By);
+            Dx = warp_sum_d(Dx);
+            Dy = warp_sum_d(Dy);
+            const double Fx = t.gamma + Ax - oms * ph.x, Fy = Ay + oms * ph.y;
+            if (Fx == 0.0 && Fy == 0.0) {
+                conv = true;
+                break;
+            }
+            const double dFx = -2.0 * Bx, dFy = -2.0 * By;
+            const double fd = Fx * Fx + Fy * Fy;
+            const double px = (dFx * Fx + dFy * Fy) / fd + 2.0 * Cx - Dx;
+            const double py = (dFy * Fx - dFx * Fy) / fd + 2.0 * Cy - Dy;
+            const double pd = px * px + py * py;
+            const double delx = px / pd, dely = -py / pd;
+            zx -= delx;
+            zy -= dely;
+            conv = delx * delx + dely * dely < tol_abs * tol_abs;
+        }
+        // caustic point of the new position: w = (1-kappa_s) z + gamma conj(z) - conj(sum m/(z - z_i))
+        double Sx = 0, Sy = 0;
+        for (int i = lane; i < n; i += 32) {
+            const StarD st = t.stars[i];
+            const double dx = zx - st.x, dy = zy - st.y;
+            const double q = st.z / (dx * dx + dy * dy);
+            Sx += q * dx;
+            Sy -= q * dy;
+        }
+        Sx = warp_sum_d(Sx);
+        Sy = warp_sum_d(Sy);
+        if (lane == 0) {
+            t.z[(size_t)row * nr + col] = make_double2(zx, zy);
+            if (t.w) t.w[(size_t)row * nr + col] = make_double2(oms * zx + t.gamma * zx - Sx, oms * zy - t.gamma * zy + Sy);
+            if (conv) {
+                atomicAdd(&t.rep->uncertified, (unsigned long long)(-1LL));
+                atomicAdd(&t.rep->rescued_points, 1ull);
+            }
+        }
+    }
+}
+
+cudaError_t launch_rescue(const RescueTask* host_task, const RescueTask* dev_tasks, const int4* list, const int* nlist,
+                          int max_list, double tol_abs, int max_iter, cudaStream_t st) {
+    RescueTask t0;
+    memset(&t0, 0, sizeof t0);
+    if (host_task) t0 = *host_task;
+    rescue_kernel<<<64, 256, 0, st>>>(t0, dev_tasks, list, nlist, max_list, tol_abs, max_iter);
     return cudaGetLastError();
 }
 

@@ -31,6 +31,7 @@ struct cc_batch {
     // workspace layout
     std::vector<size_t> off_phase, off_zrows, off_seam, off_iters, off_match, off_perm, off_hits;
     size_t hits_begin = 0, hits_bytes = 0;
+    size_t off_rtasks = 0, off_list = 0, off_nlist = 0;
     size_t off_tasks = 0, off_items = 0, off_seams = 0, off_ptasks = 0, off_reps = 0, off_queue = 0, off_work = 0;
     size_t work_stride = 0, total = 0;
     // bound buffers
@@ -73,6 +74,7 @@ cudaError_t enqueue(cc_batch* b, cudaStream_t st, bool capturing) {
     if ((e = cudaMemsetAsync(ws + b->off_reps, 0, sizeof(DevReport) * b->count, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ws + b->off_queue, 0, 256, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(ws + b->hits_begin, 0, b->hits_bytes, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(ws + b->off_nlist, 0, 256, st)) != cudaSuccess) return e;
     const TraceTask* tasks = (const TraceTask*)(ws + b->off_tasks);
     if ((e = launch_phase_batch(tasks, b->count, b->max_m, st)) != cudaSuccess) return e;
     BatchTraceArgs a;
@@ -93,6 +95,10 @@ cudaError_t enqueue(cc_batch* b, cudaStream_t st, bool capturing) {
         return e;
     if ((e = rec(b->ev[2], st, capturing)) != cudaSuccess) return e;
     if ((e = launch_polish_batch(ws + b->off_ptasks, b->count, b->total_blocks, st)) != cudaSuccess) return e;
+    if ((e = launch_rescue(nullptr, (const RescueTask*)(ws + b->off_rtasks), (const int4*)(ws + b->off_list),
+                           (const int*)(ws + b->off_nlist), RESCUE_MAX_POINTS, b->opt.tol_abs, b->opt.max_iter_warm, st)) !=
+        cudaSuccess)
+        return e;
     return rec(b->ev[3], st, capturing);
 }
 
@@ -187,6 +193,12 @@ int cc_batch_create(cc_field* const* fields, int32_t count, const int64_t* m, in
         o += a256(sizeof(int32_t) * (size_t)b->S[f] * b->nr[f]);
     }
     b->hits_bytes = o - b->hits_begin;
+    b->off_rtasks = o;
+    o += a256(sizeof(RescueTask) * count);
+    b->off_list = o;
+    o += a256(sizeof(int4) * (size_t)RESCUE_MAX_POINTS);
+    b->off_nlist = o;
+    o += 256;
     for (int f = 0; f < count; f++) {
         const size_t nrf = (size_t)b->nr[f];
         b->off_phase.push_back(o);
@@ -241,6 +253,7 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
     if (e != cudaSuccess) return berr(CC_ECUDA, "cc_batch_bind: cudaSetDevice failed");
     char* ws = (char*)workspace;
     std::vector<TraceTask> tasks(b->count);
+    std::vector<RescueTask> rtasks(b->count);
     std::vector<unsigned char> ptasks(polish_task_bytes() * b->count);
     std::vector<int2> seams;
     std::vector<std::pair<double, int2>> items;
@@ -283,7 +296,21 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         pa.tol_cert = b->opt.tol_cert;
         pa.max_polish = b->opt.max_polish;
         pa.hp_fp64 = 0;
+        pa.rescue_list = (int4*)(ws + b->off_list);
+        pa.rescue_count = (int*)(ws + b->off_nlist);
+        pa.field_id = f;
         polish_task_fill(pa, block0, ptasks.data() + polish_task_bytes() * f);
+        RescueTask& rt = rtasks[f];
+        rt.stars = fd.star64;
+        rt.n = (int)fd.n;
+        rt.nr = (int)b->nr[f];
+        rt.kappa_s = fd.kappa_s;
+        rt.gamma = fd.gamma;
+        rt.m = b->m[f];
+        rt.phase = t.phase;
+        rt.z = pa.z_out;
+        rt.w = pa.w_out;
+        rt.rep = t.rep;
         block0 += polish_blocks(b->rows[f] * b->nr[f]);
     }
     b->total_blocks = block0;
@@ -297,7 +324,8 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         (e = cudaMemcpy(ws + b->off_items, it.data(), sizeof(int2) * it.size(), cudaMemcpyHostToDevice)) ||
         (seams.size() && (e = cudaMemcpy(ws + b->off_seams, seams.data(), sizeof(int2) * seams.size(),
                                          cudaMemcpyHostToDevice))) ||
-        (e = cudaMemcpy(ws + b->off_ptasks, ptasks.data(), ptasks.size(), cudaMemcpyHostToDevice)))
+        (e = cudaMemcpy(ws + b->off_ptasks, ptasks.data(), ptasks.size(), cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(ws + b->off_rtasks, rtasks.data(), sizeof(RescueTask) * b->count, cudaMemcpyHostToDevice)))
         return berr(CC_ECUDA, cudaGetErrorString(e));
     b->ws = ws;
     b->bound = true;
@@ -379,6 +407,8 @@ int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
         q.max_iter_row = r[f].max_iter_row;
         q.timeout = r[f].timeout;
         q.max_err_est = r[f].max_err_est;
+        q.rescued_points = (int64_t)r[f].rescued_points;
+        q.jumped = (int64_t)r[f].jumped;
         if (per_field) per_field[f] = q;
         tot.rows += q.rows;
         tot.n_roots += q.n_roots;
@@ -392,6 +422,8 @@ int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
         tot.max_iter_row = std::max(tot.max_iter_row, q.max_iter_row);
         tot.timeout |= q.timeout;
         tot.max_err_est = std::max(tot.max_err_est, q.max_err_est);
+        tot.rescued_points += q.rescued_points;
+        tot.jumped += q.jumped;
         bad = bad || q.unconverged || q.uncertified;
     }
     tot.trace_ms = t01;

@@ -1,6 +1,7 @@
 // C ABI of libccgpu (declared in include/cc.h): argument checks, field set-up, workspace
 // layout and the order of kernel launches.  Every compute step runs in the kernels of
 // aberth.cu, polish.cu and raster.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -102,6 +103,10 @@ CurveLayout curve_layout(const cc_field* f, int64_t m) {
     o += align256(sizeof(int32_t) * (size_t)L.S * nr);
     L.off_perm = o;
     o += align256(sizeof(int32_t) * (size_t)L.S * nr);
+    L.off_list = o;
+    o += align256(sizeof(int4) * (size_t)RESCUE_MAX_POINTS);
+    L.off_nlist = o;
+    o += 256;
     L.off_work = o;
     o += L.work_stride * (size_t)L.S;
     L.total = o;
@@ -148,7 +153,7 @@ int cc_options_default(cc_options* opt) {
     opt->tol_cert = 1e-10;
     opt->max_iter_cold = 500;
     opt->max_iter_warm = 200;
-    opt->max_polish = 4;
+    opt->max_polish = 8;
     opt->precision = CC_MIXED;
     opt->hp_arith = CC_HP_DFLOAT;
     opt->subchains = 0;
@@ -350,7 +355,25 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
         pa.tol_cert = f->opt.tol_cert;
         pa.max_polish = f->opt.max_polish;
         pa.hp_fp64 = f->opt.hp_arith == CC_HP_FP64;
+        pa.rescue_list = (int4*)(ws + L.off_list);
+        pa.rescue_count = (int*)(ws + L.off_nlist);
+        pa.field_id = 0;
+        CC_CUDA(cudaMemsetAsync(pa.rescue_count, 0, sizeof(int), st), "clear rescue count");
         CC_CUDA(launch_polish(pa, st), "polish");
+        RescueTask rt;
+        rt.stars = f->dev.star64;
+        rt.n = (int)f->dev.n;
+        rt.nr = (int)nr;
+        rt.kappa_s = f->dev.kappa_s;
+        rt.gamma = f->dev.gamma;
+        rt.m = m;
+        rt.phase = phase;
+        rt.z = (double2*)z_out;
+        rt.w = (double2*)w_out;
+        rt.rep = rep;
+        CC_CUDA(launch_rescue(&rt, nullptr, pa.rescue_list, pa.rescue_count, RESCUE_MAX_POINTS, f->opt.tol_abs,
+                              f->opt.max_iter_warm, st),
+                "rescue");
     }
     CC_CUDA(cudaEventRecord(f->ev[3], st), "event record");
     CC_CUDA(cudaEventRecord(f->done, st), "event record");
@@ -379,6 +402,8 @@ int cc_field_report(cc_field* f, cc_report* out) {
     out->max_iter_row = r.max_iter_row;
     out->timeout = r.timeout;
     out->max_err_est = r.max_err_est;
+    out->rescued_points = (int64_t)r.rescued_points;
+    out->jumped = (int64_t)r.jumped;
     CC_CUDA(cudaEventElapsedTime(&out->trace_ms, f->ev[0], f->ev[1]), "stage time");
     CC_CUDA(cudaEventElapsedTime(&out->join_ms, f->ev[1], f->ev[2]), "stage time");
     CC_CUDA(cudaEventElapsedTime(&out->polish_ms, f->ev[2], f->ev[3]), "stage time");

@@ -118,6 +118,7 @@ struct DevReport {
     unsigned long long uncertified;
     unsigned long long seam_ambiguous;
     unsigned long long jumped;   // polish moved a root further than the tracer's scale
+    unsigned long long rescued_points;  // uncertified points re-solved in FP64 (converged)
     int max_iter_row;
     int timeout;
     double max_err_est;          // stored as the bit pattern of a non-negative double

@@ -68,6 +68,22 @@ struct BatchTraceArgs {
     int max_iter_cold, max_iter_warm, predictor;
 };
 
+// One field's points for the FP64 rescue of uncertified points.
+struct RescueTask {
+    const StarD* stars;
+    int n, nr;
+    double kappa_s, gamma;
+    int64_t m;
+    const double2* phase;
+    double2* z;
+    double2* w;
+    DevReport* rep;
+};
+constexpr int RESCUE_MAX_POINTS = 65536;
+// list entries: (field, row, column, 0); *nlist counts entries (may exceed max_list)
+cudaError_t launch_rescue(const RescueTask* host_task, const RescueTask* dev_tasks, const int4* list, const int* nlist,
+                          int max_list, double tol_abs, int max_iter, cudaStream_t st);
+
 int tracer_batch_blocks_per_sm(int threads);
 cudaError_t launch_phase_batch(const TraceTask* tasks, int count, int64_t max_m, cudaStream_t st);
 cudaError_t launch_trace_batch(const BatchTraceArgs& b, int grid, int threads, cudaStream_t st);
@@ -80,7 +96,7 @@ struct CurveLayout {
     int threads;
     size_t elem;           // bytes per tracer complex (8 FP32, 16 FP64)
     size_t off_phase, off_zrows, off_seam, off_iters, off_match, off_hits, off_perm, off_work,
-        off_report, total;
+        off_report, off_list, off_nlist, total;
     size_t work_stride;
 };
 
@@ -112,6 +128,9 @@ struct PolishArgs {
     double tol_cert;
     int max_polish;
     int hp_fp64;            // 1: native FP64 star sums, 0: double-float
+    int4* rescue_list;      // uncertified points go here (field_id, row, column, 0)
+    int* rescue_count;
+    int field_id;
 };
 cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st);
 // Batched polish: a device table of per-field task records (polish_task_bytes() each,

@@ -43,6 +43,9 @@ struct PolishK {
     int max_polish;
     int unit_mass;        // batched launches: all masses equal to 1
     int64_t first_block;  // batched launches: first block of this field
+    int4* rescue_list;    // uncertified points, for the FP64 rescue
+    int* rescue_count;
+    int field_id;
 };
 
 struct Sums {
@@ -161,11 +164,18 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
         K.w_out[point] = make_double2(wx, wy);
     }
     if (K.iters_out) K.iters_out[point] = it_in;
-    if (est >= K.tol_cert) atomicAdd(&K.rep->uncertified, 1ull);
+    if (est >= K.tol_cert) {
+        atomicAdd(&K.rep->uncertified, 1ull);
+        if (K.rescue_list) {
+            const int idx = atomicAdd(K.rescue_count, 1);
+            if (idx < RESCUE_MAX_POINTS)
+                K.rescue_list[idx] = make_int4(K.field_id, (int)row, (int)(point - row * K.nr), 0);
+        }
+    }
     const double jx = nzx - (double)z0x, jy = nzy - (double)z0y;
     const double zs = 1.0 + sqrt(nzx * nzx + nzy * nzy);
     if (jx * jx + jy * jy > 1e-6 * zs * zs) atomicAdd(&K.rep->jumped, 1ull);
-    atomic_max_double_nonneg(&K.rep->max_err_est, est < DBL_MAX ? est : 1e300);
+    if (est < K.tol_cert) atomic_max_double_nonneg(&K.rep->max_err_est, est);
     return true;
 }
 
@@ -302,6 +312,9 @@ static PolishK make_polish_k(const PolishArgs& a) {
     K.max_polish = a.max_polish < 1 ? 1 : a.max_polish;
     K.unit_mass = a.f->unit_mass ? 1 : 0;
     K.first_block = 0;
+    K.rescue_list = a.rescue_list;
+    K.rescue_count = a.rescue_count;
+    K.field_id = a.field_id;
     return K;
 }
 

@@ -107,59 +107,88 @@ __device__ __forceinline__ double pix(double lo, double step, int64_t i) {
     return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), step));
 }
 
-// Smallest r in [0, cnt] with pix(r) >= v (cnt if none); pix is non-decreasing in r.
-__device__ __forceinline__ int64_t first_at_or_above(double lo, double step, int64_t cnt, double v) {
-    double e = ceil((v - lo) / step - 0.5);
-    e = fmin(fmax(e, 0.0), (double)cnt);
-    int64_t r = (int64_t)e;
-    while (r > 0 && pix(lo, step, r - 1) >= v) r--;
-    while (r < cnt && pix(lo, step, r) < v) r++;
-    return r;
-}
-
 struct CrossK {
     const double2* w;
     int64_t rows, nr;
     double x0, sx, y0, sy;
     int W, H;
     int* D;
-    float y0f, inv_syf;  // FP32 copies for the quick rejection test
+    float x0f, inv_sxf, y0f, inv_syf;  // FP32 copies for estimates (exactness comes from FP64 checks)
 };
 
-// True when [lo, hi) certainly contains no pixel-centre row (FP32 estimate of the
-// continuous row index with a margin that covers its rounding; undecided cases go to
-// the exact test).
-__device__ __forceinline__ bool no_row_between(const CrossK& K, double lo, double hi) {
-    const float flo = (float)lo, fhi = (float)hi;
-    const float tl = (flo - K.y0f) * K.inv_syf - 0.5f;
-    const float th = (fhi - K.y0f) * K.inv_syf - 0.5f;
-    const float eps = 1e-3f + 1e-6f * ((fabsf(flo) + fabsf(K.y0f)) * fabsf(K.inv_syf) + fabsf(tl) + fabsf(th));
-    if (!(th + eps >= 0.0f) || !(tl - eps <= (float)K.H)) return true;  // outside the map's rows
-    return ceilf(tl - eps) > th + eps;                                   // no integer in between
-}
+constexpr int XS_THREADS = 256;
 
-__global__ void __launch_bounds__(256) crossing_scatter_kernel(CrossK K) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (K.rows - 1) * K.nr) return;
-    const double2 a = K.w[t], b = K.w[t + K.nr];
-    if (!(isfinite(a.x) && isfinite(a.y) && isfinite(b.x) && isfinite(b.y))) return;
-    if (a.y == b.y) return;
-    const bool up = a.y < b.y;
-    const double lo = up ? a.y : b.y, hi = up ? b.y : a.y;
-    if (no_row_between(K, lo, hi)) return;
-    const int64_t r0 = first_at_or_above(K.y0, K.sy, K.H, lo);
-    const int64_t r1 = first_at_or_above(K.y0, K.sy, K.H, hi);
-    const int sgn = up ? 1 : -1;
-    const double ex = b.x - a.x, ey = b.y - a.y;
-    for (int64_t r = r0; r < r1; r++) {
+// One thread per segment finds, in FP32 with a margin that covers its rounding, the pixel
+// rows its half-open y-range may contain.  The (segment, candidate row) pairs of a warp
+// are then laid out by a warp prefix sum and processed by all 32 lanes together, so the
+// exact FP64 work (row test, prefix length settled by the exact orientation predicate)
+// runs without divergence however unevenly crossings are spread over segments.
+__global__ void __launch_bounds__(XS_THREADS) crossing_scatter_kernel(CrossK K) {
+    __shared__ double2 s_a[XS_THREADS], s_b[XS_THREADS];
+    __shared__ int s_r0[XS_THREADS], s_excl[XS_THREADS];
+    const int lane = threadIdx.x & 31;
+    const int wbase = threadIdx.x & ~31;
+    const int64_t t = blockIdx.x * (int64_t)XS_THREADS + threadIdx.x;
+    const int64_t nseg = (K.rows - 1) * K.nr;
+    int r0 = 0, cnt = 0;
+    double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+    if (t < nseg) {
+        a = K.w[t];
+        b = K.w[t + K.nr];
+        if (isfinite(a.x) && isfinite(a.y) && isfinite(b.x) && isfinite(b.y) && a.y != b.y) {
+            const float lo = (float)fmin(a.y, b.y), hi = (float)fmax(a.y, b.y);
+            const float tl = (lo - K.y0f) * K.inv_syf - 0.5f;
+            const float th = (hi - K.y0f) * K.inv_syf - 0.5f;
+            const float eps = 1e-3f + 1e-6f * ((fabsf(lo) + fabsf(K.y0f)) * fabsf(K.inv_syf) + fabsf(tl) + fabsf(th));
+            const float fr0 = fmaxf(ceilf(tl - eps), 0.0f);
+            const float fr1 = fminf(floorf(th + eps) + 1.0f, (float)K.H);  // candidates [fr0, fr1)
+            if (fr1 > fr0) {
+                r0 = (int)fr0;
+                cnt = (int)fr1 - r0;
+            }
+        }
+    }
+    // warp prefix sum of candidate counts
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total == 0) return;  // whole warp: nothing to do
+    s_a[threadIdx.x] = a;
+    s_b[threadIdx.x] = b;
+    s_r0[threadIdx.x] = r0;
+    s_excl[threadIdx.x] = incl - cnt;
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+        const int item = base + lane;
+        if (item >= total) break;
+        // owning segment: the last lane j with excl[j] <= item
+        int lo = 0, hi = 31;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_excl[wbase + mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int j = wbase + lo;
+        const double2 sa = s_a[j], sb = s_b[j];
+        const int64_t r = s_r0[j] + (item - s_excl[j]);
+        const bool up = sa.y < sb.y;
+        const double ylo = up ? sa.y : sb.y, yhi = up ? sb.y : sa.y;
         const double py = pix(K.y0, K.sy, r);
-        // prefix length c: centres with orient(a, b, P) == sgn
-        const double xc = a.x + ex * ((py - a.y) / ey);
-        double ce = ceil((xc - K.x0) / K.sx - 0.5);
-        ce = fmin(fmax(ce, 0.0), (double)K.W);
+        if (!(ylo <= py && py < yhi)) continue;  // exact half-open row test
+        const int sgn = up ? 1 : -1;
+        // prefix length c: centres with orient(a, b, P) == sgn; FP32 estimate, exact settle
+        const float exf = (float)(sb.x - sa.x), eyf = (float)(sb.y - sa.y);
+        const float xcf = (float)sa.x + exf * ((float)(py - sa.y) / eyf);
+        float ce = ceilf((xcf - K.x0f) * K.inv_sxf - 0.5f);
+        ce = fminf(fmaxf(ce, 0.0f), (float)K.W);
+        if (!(ce == ce)) ce = 0.0f;  // NaN guard
         int64_t c = (int64_t)ce;
-        while (c > 0 && orient_sign(a.x, a.y, b.x, b.y, pix(K.x0, K.sx, c - 1), py) != sgn) c--;
-        while (c < K.W && orient_sign(a.x, a.y, b.x, b.y, pix(K.x0, K.sx, c), py) == sgn) c++;
+        while (c > 0 && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c - 1), py) != sgn) c--;
+        while (c < K.W && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c), py) == sgn) c++;
         if (c > 0) atomicAdd(&K.D[r * K.W + (c - 1)], sgn);
     }
 }
@@ -225,10 +254,12 @@ cudaError_t launch_crossing_map(const double2* w, int64_t rows, int64_t nr, doub
         K.W = W;
         K.H = H;
         K.D = ncc;
+        K.x0f = (float)x0;
+        K.inv_sxf = (float)(1.0 / K.sx);
         K.y0f = (float)y0;
         K.inv_syf = (float)(1.0 / K.sy);
         const int64_t segs = (rows - 1) * nr;
-        crossing_scatter_kernel<<<(unsigned)((segs + 255) / 256), 256, 0, st>>>(K);
+        crossing_scatter_kernel<<<(unsigned)((segs + XS_THREADS - 1) / XS_THREADS), XS_THREADS, 0, st>>>(K);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
