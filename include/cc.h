@@ -182,6 +182,19 @@ int cc_distance_map_workspace_bytes(int32_t W, int32_t H, size_t* bytes);
 int cc_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, double* d_out,
                     void* workspace, size_t workspace_bytes, cc_stream_t stream);
 
+/* Distance to the nearest caustic for a source moving in direction angle (radians from
+ * the +x axis, i.e. the source-plane y1 axis) (Sec. 5.2, the moving-source map): from each
+ * pixel centre the ray is followed through the pixel grid (cell traversal in pixel units,
+ * IEEE single precision in a fixed order: after k steps the next vertical / horizontal grid
+ * line lies at (0.5 + k) / |cos| and (0.5 + k) / |sin|, the horizontal one on ties) to the
+ * first caustic pixel (same feature rule as cc_distance_map).  d_out = pixel * ray
+ * parameter at entry into that pixel; 0 on a caustic pixel; +inf when the ray leaves the
+ * map first (the border is not a caustic; Sec. 5.2 figure caption).
+ *   ncc: H x W int32 (device).  d_out: H x W double (device).  No scratch.
+ * Errors: CC_EINVAL, CC_ECUDA. */
+int cc_moving_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, double angle,
+                           double* d_out, cc_stream_t stream);
+
 /* ---------------------------------------------------------------------------------
  * Batched critical curves: many fields of uneven N in one persistent launch (each field
  * as cc_critical_curves computes it; the paper solves one field at a time, Sec. 4.4).

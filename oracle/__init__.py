@@ -82,6 +82,8 @@ def _load():
         lib.orc_distance_map_brute.restype = None
         lib.orc_distance_map_separable.argtypes = [_I32P, i32, i32, dbl, _DP]
         lib.orc_distance_map_separable.restype = None
+        lib.orc_moving_distance_map.argtypes = [_I32P, i32, i32, dbl, dbl, _DP]
+        lib.orc_moving_distance_map.restype = None
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -229,4 +231,15 @@ def distance_map(ncc, pixel, method="separable"):
     out = np.zeros((H, W), dtype=np.float64)
     fn = _load().orc_distance_map_brute if method == "brute" else _load().orc_distance_map_separable
     fn(a.ctypes.data_as(_I32P), W, H, float(pixel), out.ctypes.data_as(_DP))
+    return out
+
+
+def moving_distance_map(ncc, pixel, angle):
+    """Distance along direction angle (radians from +x) to the first caustic pixel (Sec. 5.2);
+    +inf when the ray leaves the map first.  FP64 [H, W]."""
+    a = np.ascontiguousarray(ncc, dtype=np.int32)
+    H, W = a.shape
+    out = np.zeros((H, W), dtype=np.float64)
+    _load().orc_moving_distance_map(a.ctypes.data_as(_I32P), W, H, float(pixel), float(angle),
+                                    out.ctypes.data_as(_DP))
     return out

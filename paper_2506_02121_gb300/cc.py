@@ -70,6 +70,7 @@ _sig = {
     "cc_distance_map_workspace_bytes": ([_i32, _i32, ctypes.POINTER(_sz)], ctypes.c_int),
     "cc_distance_map": ([_vp, _i32, _i32, _dbl, _vp, _vp, _sz, _vp], ctypes.c_int),
     "cc_distance_map_static": ([_vp, _i32, _i32, _dbl, _vp, _vp], ctypes.c_int),
+    "cc_moving_distance_map": ([_vp, _i32, _i32, _dbl, _dbl, _vp, _vp], ctypes.c_int),
     "cc_batch_create": ([ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i64), _i32, _i32, ctypes.POINTER(_vp)], ctypes.c_int),
     "cc_batch_workspace_bytes": ([_vp, ctypes.POINTER(_sz)], ctypes.c_int),
     "cc_batch_bind": ([_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _sz], ctypes.c_int),
@@ -234,6 +235,21 @@ def cc_distance_map(ncc, pixel: float, d_out, workspace, stream=None):
     _check(_lib.cc_distance_map(_dev_ptr(ncc, torch.int32), int(W), int(H), float(pixel),
                                 _dev_ptr(d_out, torch.float64, (H, W)), _ptr(workspace),
                                 workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+def cc_moving_distance_map(ncc, pixel: float, angle: float, d_out, stream=None):
+    """Distance along direction angle (radians from +x) to the first caustic pixel; +inf
+    when the ray leaves the map first (Sec. 5.2)."""
+    H, W = ncc.shape
+    _check(_lib.cc_moving_distance_map(_dev_ptr(ncc, torch.int32), int(W), int(H), float(pixel), float(angle),
+                                       _dev_ptr(d_out, torch.float64, (H, W)), _stream(stream)))
+
+
+def moving_distance_map(ncc, pixel, angle, stream=None):
+    H, W = ncc.shape
+    out = torch.empty((H, W), dtype=torch.float64, device="cuda")
+    cc_moving_distance_map(ncc, pixel, angle, out, stream)
+    return out
 
 
 DISTANCE_MAP_STATIC_MAX_PIXELS = 1048576

@@ -459,6 +459,17 @@ int cc_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, doub
     return CC_OK;
 }
 
+int cc_moving_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, double angle, double* d_out,
+                           cc_stream_t stream) {
+    if (!ncc || !d_out) return fail(CC_EINVAL, "cc_moving_distance_map: NULL buffer");
+    if (W < 1 || H < 1) return fail(CC_EINVAL, "cc_moving_distance_map: W, H must be >= 1");
+    if (!(pixel > 0) || !std::isfinite(pixel)) return fail(CC_EINVAL, "cc_moving_distance_map: pixel must be finite and > 0");
+    if (!std::isfinite(angle)) return fail(CC_EINVAL, "cc_moving_distance_map: angle must be finite");
+    const float c = (float)std::cos(angle), s = (float)std::sin(angle);
+    CC_CUDA(launch_moving_distance_map(ncc, W, H, pixel, c, s, d_out, (cudaStream_t)stream), "moving distance map");
+    return CC_OK;
+}
+
 const char* cc_last_error(void) { return g_err.c_str(); }
 
 const char* cc_version(void) { return "ccgpu 0.1 (sm_103a)"; }

@@ -160,6 +160,8 @@ cudaError_t launch_crossing_map(const double2* w, int64_t rows, int64_t nr, doub
                                 double y0, double y1, int32_t W, int32_t H, int32_t* ncc,
                                 cudaStream_t st);
 size_t distance_workspace_bytes(int32_t W, int32_t H);
+cudaError_t launch_moving_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, float c, float s,
+                                       double* d_out, cudaStream_t st);
 cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel,
                                 double* d_out, void* ws, cudaStream_t st);
 

@@ -428,6 +428,76 @@ __global__ void edt_row_kernel(const int32_t* g, int W, int H, double pixel, int
     }
 }
 
+// ----------------------------------------------------------------------------------
+// Distance to the nearest caustic for a source moving along a direction (Sec. 5.2): one
+// thread per pixel follows the ray from the pixel centre through the pixel grid and stops
+// at the first caustic (feature) pixel (0 if it starts on one, +inf if it leaves the map:
+// the border is not a caustic).  The traversal uses IEEE single-precision operations in a
+// fixed order: after k steps the next vertical (horizontal) grid line is crossed at
+// (0.5 + k) * tdx (tdy), tdx = 1/|cos|, tdy = 1/|sin|; the smaller parameter is taken, the
+// horizontal line on ties.
+// ----------------------------------------------------------------------------------
+struct MoveK {
+    const int32_t* ncc;
+    int W, H;
+    double pixel;
+    int sx, sy;
+    float tdx, tdy;
+    double* out;
+};
+
+__global__ void moving_distance_kernel(MoveK K) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (i >= K.W) return;
+    double d;
+    if (feature_at(K.ncc, K.W, K.H, r, i)) {
+        d = 0.0;
+    } else {
+        int x = i, y = r;
+        long long nx = 0, ny = 0;
+        d = __longlong_as_double(0x7ff0000000000000LL);
+        for (;;) {
+            const float tx = K.sx ? __fmul_rn(__fadd_rn(0.5f, (float)nx), K.tdx) : __int_as_float(0x7f800000);
+            const float ty = K.sy ? __fmul_rn(__fadd_rn(0.5f, (float)ny), K.tdy) : __int_as_float(0x7f800000);
+            float t;
+            if (tx < ty) {
+                x += K.sx;
+                nx++;
+                t = tx;
+            } else {
+                y += K.sy;
+                ny++;
+                t = ty;
+            }
+            if (x < 0 || x >= K.W || y < 0 || y >= K.H) break;
+            if (feature_at(K.ncc, K.W, K.H, y, x)) {
+                d = __dmul_rn(K.pixel, (double)t);
+                break;
+            }
+        }
+    }
+    K.out[(int64_t)r * K.W + i] = d;
+}
+
+cudaError_t launch_moving_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel, float c, float s,
+                                       double* d_out, cudaStream_t st) {
+    MoveK K;
+    K.ncc = ncc;
+    K.W = W;
+    K.H = H;
+    K.pixel = pixel;
+    K.sx = c > 0.0f ? 1 : (c < 0.0f ? -1 : 0);
+    K.sy = s > 0.0f ? 1 : (s < 0.0f ? -1 : 0);
+    volatile float one = 1.0f;  // IEEE divisions on the host, as the kernel's traversal expects
+    K.tdx = K.sx ? one / fabsf(c) : 0.0f;
+    K.tdy = K.sy ? one / fabsf(s) : 0.0f;
+    K.out = d_out;
+    dim3 grid((unsigned)((W + 127) / 128), (unsigned)H);
+    moving_distance_kernel<<<grid, 128, 0, st>>>(K);
+    return cudaGetLastError();
+}
+
 size_t distance_workspace_bytes(int32_t W, int32_t H) {
     const size_t plane = ((size_t)W * H * sizeof(int32_t) + 255) / 256 * 256;
     return 2 * plane;

@@ -193,3 +193,25 @@ def test_device_star_arrays_accepted():
     z, _, _ = cc.critical_curves(field, 20, caustics=False)
     zo, _, _ = oracle.critical_curves(f.x, f.y, f.m, f.kappa_s, f.gamma, 20)
     compare_chain(z.cpu().numpy(), zo, TOL)
+
+
+@pytest.mark.parametrize("angle", [0.0, 0.7, math.pi / 2, 2.5, math.pi, 4.4, 3 * math.pi / 2, 6.0])
+def test_moving_distance_map_bit_exact(angle):
+    u = synth.uniform(900 + int(10 * angle), 70 * 90).reshape(70, 90)
+    ncc = (u < 0.004).astype(np.int32)
+    ncc[20:45, 10:60] += 1
+    ref = oracle.moving_distance_map(ncc, 0.02, angle)
+    got = cc.moving_distance_map(torch.from_numpy(ncc).cuda(), 0.02, angle).cpu().numpy()
+    assert np.array_equal(got, ref)
+
+
+def test_moving_distance_map_on_real_caustics():
+    f = synth.workload_small().fields[0]
+    zo, _, _ = oracle.critical_curves(f.x, f.y, f.m, f.kappa_s, f.gamma, 400)
+    wo = oracle.map_caustics(f.x, f.y, f.m, f.kappa_s, f.gamma, zo)
+    ncc = oracle.crossing_map(wo, -3, 3, -3, 3, 128, 128)
+    for angle in (0.25, 1.9):
+        ref = oracle.moving_distance_map(ncc, 6 / 128, angle)
+        got = cc.moving_distance_map(torch.from_numpy(ncc).cuda(), 6 / 128, angle).cpu().numpy()
+        assert np.array_equal(got, ref)
+        assert np.isfinite(ref).any() and np.isinf(ref).any()

@@ -184,3 +184,50 @@ def test_point_on_edge_not_counted():
     assert oracle.winding_at(sq, 1.0, 0.25) == 0
     assert oracle.winding_at(sq, -1.0 - 1e-12, 0.25) == 0
     assert oracle.winding_at(sq, 1.0 - 1e-12, 0.25) == -1
+
+
+@pytest.mark.parametrize("angle", [0.0, math.pi / 2, math.pi, 3 * math.pi / 2])
+def test_moving_distance_axis_aligned_equals_row_scan(angle):
+    """Along the axes the traversal visits the pixels of one row or column in order: the
+    distance is pixel * (k - 0.5) for the k-th pixel ahead, k = 1, 2, ..."""
+    u = synth.uniform(600 + int(angle * 10), 23 * 31).reshape(23, 31)
+    ncc = (u > 0.93).astype(np.int32)
+    feat = oracle.feature_mask(ncc).astype(bool)
+    d = oracle.moving_distance_map(ncc, 0.5, angle)
+    H, W = ncc.shape
+    dx, dy = round(math.cos(angle)), round(math.sin(angle))
+    for r in range(H):
+        for i in range(W):
+            if feat[r, i]:
+                assert d[r, i] == 0.0
+                continue
+            k, x, y, ref = 0, i, r, math.inf
+            while True:
+                x, y, k = x + dx, y + dy, k + 1
+                if not (0 <= x < W and 0 <= y < H):
+                    break
+                if feat[y, x]:
+                    ref = 0.5 * (k - 0.5)
+                    break
+            assert d[r, i] == pytest.approx(ref, rel=1e-6) or (math.isinf(ref) and math.isinf(d[r, i]))
+
+
+@pytest.mark.parametrize("angle", [0.3, 1.1, 2.0, 4.0, 5.5])
+def test_moving_distance_to_a_feature_line_closed_form(angle):
+    """A caustic along one full pixel column i0 (features at columns i0-1..i0+1 after the
+    4-neighbour rule): a ray from (i + 0.5, r + 0.5) with cos > 0 first enters column i0 - 1
+    at t = (i0 - 1 - i - 0.5) / cos, in pixel units, if it is still inside the map there."""
+    H, W, i0 = 40, 50, 30
+    ncc = np.zeros((H, W), dtype=np.int32)
+    ncc[:, i0:] = 1  # boundary between columns i0-1 and i0: features i0-1 and i0
+    d = oracle.moving_distance_map(ncc, 1.0, angle)
+    c, s = math.cos(angle), math.sin(angle)
+    for r in range(H):
+        for i in range(i0 - 1):
+            if c <= 0:
+                assert math.isinf(d[r, i])
+                continue
+            t = (i0 - 1 - i - 0.5) / c
+            yend = r + 0.5 + t * s
+            if 0.0 < yend < H - 1e-6 and abs(yend - round(yend)) > 1e-4:
+                assert d[r, i] == pytest.approx(t, rel=1e-5, abs=1e-5)
