@@ -77,6 +77,9 @@ typedef struct cc_options {
     int32_t predictor;     /* 1: warm start by linear extrapolation of the last two rows; 0: copy
                               the previous row (Sec. 3.2 last paragraph) */
     int32_t block_threads; /* threads per tracing CTA (0 = automatic) */
+    int32_t far_field;     /* 1: polish stars beyond a 5x5 block of cells through local expansions
+                              (Sec. 4.1, fast multipole method; used when N >= 128 and hp_arith is
+                              CC_HP_DFLOAT); 0: every star summed directly */
 } cc_options;
 
 /* Solve statistics of the last cc_critical_curves on a field (host copy). */

@@ -36,7 +36,8 @@ class Options(ctypes.Structure):
     _fields_ = [("tol_abs", ctypes.c_double), ("mu_max", ctypes.c_double), ("tol_cert", ctypes.c_double),
                 ("max_iter_cold", ctypes.c_int32), ("max_iter_warm", ctypes.c_int32),
                 ("max_polish", ctypes.c_int32), ("precision", ctypes.c_int32), ("hp_arith", ctypes.c_int32),
-                ("subchains", ctypes.c_int32), ("predictor", ctypes.c_int32), ("block_threads", ctypes.c_int32)]
+                ("subchains", ctypes.c_int32), ("predictor", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("far_field", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):

@@ -299,6 +299,7 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         pa.rescue_list = (int4*)(ws + b->off_list);
         pa.rescue_count = (int*)(ws + b->off_nlist);
         pa.field_id = f;
+        pa.skip_if = nullptr;
         polish_task_fill(pa, block0, ptasks.data() + polish_task_bytes() * f);
         RescueTask& rt = rtasks[f];
         rt.stars = fd.star64;

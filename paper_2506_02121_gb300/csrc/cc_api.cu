@@ -109,6 +109,9 @@ CurveLayout curve_layout(const cc_field* f, int64_t m) {
     o += 256;
     L.off_work = o;
     o += L.work_stride * (size_t)L.S;
+    L.fmm = !fp64 && f->opt.far_field && f->opt.hp_arith == CC_HP_DFLOAT && f->dev.n >= FMM_MIN_STARS;
+    L.off_fmm = o;
+    if (L.fmm) o += align256(fmm_workspace_bytes((m + 1) * nr));
     L.total = o;
     return L;
 }
@@ -159,6 +162,7 @@ int cc_options_default(cc_options* opt) {
     opt->subchains = 0;
     opt->predictor = 1;
     opt->block_threads = 0;
+    opt->far_field = 1;
     return CC_OK;
 }
 
@@ -181,6 +185,7 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
     if (!(o.tol_abs > 0) || !(o.tol_cert > 0) || o.max_iter_cold < 1 || o.max_iter_warm < 1 || o.max_polish < 1 ||
         o.mu_max < 0 || o.subchains < 0)
         return fail(CC_EINVAL, "cc_field_create: bad options");
+    if (o.far_field != 0 && o.far_field != 1) return fail(CC_EINVAL, "cc_field_create: far_field must be 0 or 1");
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 512 || (o.block_threads & 31)))
         return fail(CC_EINVAL, "cc_field_create: block_threads must be 0 or a multiple of 32 in [32, 512]");
 
@@ -211,8 +216,22 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
         sdp[i] = make_float4(a, b, c, d);
         sdm[i] = make_float2(e, g);
     }
+    // far-field cell: about 6 stars in a 5x5 block of cells at the mean star density of the
+    // field's bounding disc
+    double mx = 0.0, my = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        mx += hx[i];
+        my += hy[i];
+    }
+    mx /= (double)n;
+    my /= (double)n;
+    double r2max = 0.0;
+    for (int64_t i = 0; i < n; i++) r2max = std::max(r2max, (hx[i] - mx) * (hx[i] - mx) + (hy[i] - my) * (hy[i] - my));
+    const double density = r2max > 0.0 ? (double)n / (3.14159265358979323846 * r2max) : 0.0;
+    const float fmm_cell = density > 0.0 ? (float)std::sqrt(6.0 / (25.0 * density)) : 1.0f;
     cc_field* f = new cc_field();
     f->opt = o;
+    f->dev.fmm_cell = fmm_cell;
     f->dev.n = n;
     f->dev.kappa_s = kappa_s;
     f->dev.gamma = gamma;
@@ -358,8 +377,12 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
         pa.rescue_list = (int4*)(ws + L.off_list);
         pa.rescue_count = (int*)(ws + L.off_nlist);
         pa.field_id = 0;
+        pa.skip_if = nullptr;
         CC_CUDA(cudaMemsetAsync(pa.rescue_count, 0, sizeof(int), st), "clear rescue count");
-        CC_CUDA(launch_polish(pa, st), "polish");
+        if (L.fmm)
+            CC_CUDA(launch_polish_fmm(pa, ws + L.off_fmm, st), "far-field polish");
+        else
+            CC_CUDA(launch_polish(pa, st), "polish");
         RescueTask rt;
         rt.stars = f->dev.star64;
         rt.n = (int)f->dev.n;

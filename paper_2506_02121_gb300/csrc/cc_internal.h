@@ -19,6 +19,7 @@ struct FieldDev {
     int64_t n;
     double kappa_s, gamma;
     bool unit_mass;
+    float fmm_cell;   // far-field cell size aimed at ~6 stars in a 5x5 block of cells
     float4* star32;   // (x, y, m, 0) rounded to FP32
     StarD* star64;    // FP64
     float4* star_dfp; // (x_hi, x_lo, y_hi, y_lo) double-float positions
@@ -96,7 +97,8 @@ struct CurveLayout {
     int threads;
     size_t elem;           // bytes per tracer complex (8 FP32, 16 FP64)
     size_t off_phase, off_zrows, off_seam, off_iters, off_match, off_hits, off_perm, off_work,
-        off_report, off_list, off_nlist, total;
+        off_report, off_list, off_nlist, off_fmm, total;
+    bool fmm;
     size_t work_stride;
 };
 
@@ -131,8 +133,14 @@ struct PolishArgs {
     int4* rescue_list;      // uncertified points go here (field_id, row, column, 0)
     int* rescue_count;
     int field_id;
+    const int* skip_if;     // direct polish does nothing when *skip_if != 0 (may be null)
 };
+constexpr int FMM_MIN_STARS = 128;
 cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st);
+// Far-field (local-expansion) polish: scratch of fmm_workspace_bytes(points) bytes; falls back
+// to the direct polish on the device when its tables do not fit.
+size_t fmm_workspace_bytes(int64_t points);
+cudaError_t launch_polish_fmm(const PolishArgs& a, void* ws, cudaStream_t st);
 // Batched polish: a device table of per-field task records (polish_task_bytes() each,
 // filled on the host by polish_task_fill), blocks of all fields in one launch.
 int64_t polish_blocks(int64_t points);

@@ -46,6 +46,7 @@ struct PolishK {
     int4* rescue_list;    // uncertified points, for the FP64 rescue
     int* rescue_count;
     int field_id;
+    const int* skip_if;   // direct polish: return at once when *skip_if != 0 (far-field path took over)
 };
 
 struct Sums {
@@ -122,7 +123,7 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
                                                 double S1x, double S1y, double S2x, double S2y,
                                                 float s3x, float s3y, float s4x, float s4y, float a3,
                                                 double& zx, double& zy, float z0x, float z0y,
-                                                int pass, int32_t it_in) {
+                                                int pass, int32_t it_in, double& est_out, double s2_err = 0.0) {
     const double oms = 1.0 - K.kappa_s;
     const double2 ph = K.phase[row];
     const double Fx = K.gamma + S2x - oms * ph.x;
@@ -140,7 +141,7 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
     const double s4a = sqrt((double)s4x * s4x + (double)s4y * s4y);
     double est;
     if (s3a > 0.0)
-        est = 1.5 * ad * ad * s4a / s3a + ad * 4.0 * (double)FLT_EPSILON * (double)a3 / s3a;
+        est = 1.5 * ad * ad * s4a / s3a + ad * 4.0 * (double)FLT_EPSILON * (double)a3 / s3a + 0.5 * s2_err / s3a;
     else
         est = (ad == 0.0) ? 0.0 : DBL_MAX;
     const double nzx = zx + dx, nzy = zy + dy;
@@ -175,7 +176,7 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
     const double jx = nzx - (double)z0x, jy = nzy - (double)z0y;
     const double zs = 1.0 + sqrt(nzx * nzx + nzy * nzy);
     if (jx * jx + jy * jy > 1e-6 * zs * zs) atomicAdd(&K.rep->jumped, 1ull);
-    if (est < K.tol_cert) atomic_max_double_nonneg(&K.rep->max_err_est, est);
+    est_out = est < K.tol_cert ? est : 0.0;  // certified points only; the caller reduces
     return true;
 }
 
@@ -187,6 +188,7 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
     StarD* sd = (StarD*)smem;
     unsigned long long& s_passes = *s_passes_p;
     const int tid = threadIdx.x;
+    if (K.skip_if && *K.skip_if) return;  // uniform across the grid
     const int64_t point = blk * (int64_t)PB_THREADS + tid;
     const bool valid = point < K.points;
     int64_t row = 0;
@@ -204,6 +206,7 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
     }
     double zx = z0x, zy = z0y;
     bool need = valid;
+    double est_max = 0.0;
     if (tid == 0) s_passes = 0;
     const bool resident = K.n <= TSB;
     if (resident) {
@@ -231,9 +234,12 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
                 if (need)
                     for (int j = 0; j < tn; j++) star_fp64(zx, zy, sd[j], s);
             }
+            double est = 0.0;
             if (need && polish_epilogue(K, point, row, s.S1x, s.S1y, s.S2x, s.S2y, s.s3x, s.s3y, s.s4x,
-                                        s.s4y, s.a3, zx, zy, z0x, z0y, pass, it_in))
+                                        s.s4y, s.a3, zx, zy, z0x, z0y, pass, it_in, est)) {
                 need = false;
+                est_max = fmax(est_max, est);
+            }
         } else {
             Sums s;
             s.S1x = s.S1y = s.S2x = s.S2y = df{0.f, 0.f};
@@ -254,12 +260,17 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
                     for (int j = 0; j < tn; j++) star_df<UNIT>(zxd, zyd, sp[j], sm[j], s);
                 }
             }
+            double est = 0.0;
             if (need && polish_epilogue(K, point, row, df_to_double(s.S1x), df_to_double(s.S1y),
                                         df_to_double(s.S2x), df_to_double(s.S2y), s.s3x, s.s3y, s.s4x,
-                                        s.s4y, s.a3, zx, zy, z0x, z0y, pass, it_in))
+                                        s.s4y, s.a3, zx, zy, z0x, z0y, pass, it_in, est)) {
                 need = false;
+                est_max = fmax(est_max, est);
+            }
         }
     }
+    for (int off = 16; off > 0; off >>= 1) est_max = fmax(est_max, __shfl_xor_sync(0xffffffffu, est_max, off));
+    if ((tid & 31) == 0 && est_max > 0.0) atomic_max_double_nonneg(&K.rep->max_err_est, est_max);
     __syncthreads();
     if (tid == 0 && s_passes) atomicAdd(&K.rep->polish_passes, s_passes);
 }
@@ -315,6 +326,7 @@ static PolishK make_polish_k(const PolishArgs& a) {
     K.rescue_list = a.rescue_list;
     K.rescue_count = a.rescue_count;
     K.field_id = a.field_id;
+    K.skip_if = a.skip_if;
     return K;
 }
 
@@ -358,6 +370,445 @@ cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st) {
         CC_LAUNCH_POLISH(false, false, smem_df);
 #undef CC_LAUNCH_POLISH
     return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Far-field polish (the star-sum splitting of Sec. 4.1, fast multipole method): the plane
+// of the traced points is cut into square cells of side b.  For a point in cell B the
+// stars of the 5x5 block of cells around B are summed directly in double-float, as in the
+// direct polish; the other stars ("far": at least 2.5 b from B's centre c, while the point
+// is within 0.72 b of c) enter through the local expansion of B,
+//   S1_far(z) = sum_far m_i / (z - z_i) = sum_k L_k (z - c)^k,  L_k = -sum_far m_i / (z_i - c)^(k+1),
+// truncated at FMM_P terms.  With D1, D2, D3 the first three derivatives of S1_far:
+// S2 = -D1, S3 = D2 / 2, S4 = -D3 / 6, all from the same coefficients (Horner with
+// derivatives: double-float for S1, S2, FP32 for S3, S4).  The truncation bound (ratio
+// rho <= 0.29, rho^31 ~ 1e-17) joins the polish error estimate.  Cells, expansions and
+// near lists are built on the device from the traced points, so the whole path stays
+// asynchronous.
+// ----------------------------------------------------------------------------------
+constexpr int FMM_P = 32;
+constexpr int FMM_K = 2;
+constexpr int FMM_G = 2048;
+
+struct FmmParams {
+    float x0, y0, b, inv_b;  // cell (0, 0) lower-left corner, cell side and its inverse (FP32)
+    int nbx, nby;
+    int ok;                   // 1 while every table is complete (else the direct polish runs)
+    int nocc;                 // occupied cells
+    int pool_used;            // near-list entries handed out
+    int cap, pool_cap;
+};
+
+struct BoxInfo {
+    float4 c;      // centre as double-float (x_hi, x_lo, y_hi, y_lo)
+    int near_off, near_cnt;
+    float s2_err;  // truncation bound of S2_far (theta_*^-2)
+    float pad;
+};
+
+__device__ __forceinline__ int fmm_cell(float v, float v0, float inv_b) {
+    const float t = floorf(__fmul_rn(__fsub_rn(v, v0), inv_b));
+    return (int)fminf(fmaxf(t, -1.0e6f), 1.0e6f);
+}
+
+__global__ void fmm_extent_kernel(const float2* z, int64_t npts, float4* part) {
+    float mnx = 3.0e38f, mny = 3.0e38f, mxx = -3.0e38f, mxy = -3.0e38f;
+    bool bad = false;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npts; p += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = z[p];
+        if (!(isfinite(v.x) && isfinite(v.y))) {
+            bad = true;
+            continue;
+        }
+        mnx = fminf(mnx, v.x);
+        mny = fminf(mny, v.y);
+        mxx = fmaxf(mxx, v.x);
+        mxy = fmaxf(mxy, v.y);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, off));
+        mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, off));
+        mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, off));
+        mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, off));
+    }
+    __shared__ float4 sh[32];
+    __shared__ int sbad;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    if (bad) sbad = 1;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = make_float4(mnx, mny, mxx, mxy);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float4 r = sh[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            r.x = fminf(r.x, sh[w].x);
+            r.y = fminf(r.y, sh[w].y);
+            r.z = fmaxf(r.z, sh[w].z);
+            r.w = fmaxf(r.w, sh[w].w);
+        }
+        if (sbad) r.x = __int_as_float(0x7fc00000);  // NaN marks a block that saw a bad point
+        part[blockIdx.x] = r;
+    }
+}
+
+__global__ void fmm_setup_kernel(const float4* part, int nparts, float b_target, int cap, int pool_cap,
+                                 FmmParams* P) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    float mnx = 3.0e38f, mny = 3.0e38f, mxx = -3.0e38f, mxy = -3.0e38f;
+    bool ok = true;
+    for (int i = 0; i < nparts; i++) {
+        const float4 r = part[i];
+        if (r.x != r.x) {
+            ok = false;
+            continue;
+        }
+        mnx = fminf(mnx, r.x);
+        mny = fminf(mny, r.y);
+        mxx = fmaxf(mxx, r.z);
+        mxy = fmaxf(mxy, r.w);
+    }
+    float b = b_target > 0.f ? b_target : 1.0f;
+    const float span = fmaxf(mxx - mnx, mxy - mny);
+    const int margin = 2 * (FMM_K + 1) + 2;
+    if (span / b + margin > (float)FMM_G) b = span / (float)(FMM_G - margin - 1);
+    if (!(b > 0.f) || !isfinite(b) || !(span >= 0.f)) {
+        b = 1.0f;
+        ok = false;
+        mnx = mny = mxx = mxy = 0.f;
+    }
+    const float inv_b = __fdiv_rn(1.0f, b);
+    const float x0 = mnx - (FMM_K + 1) * b, y0 = mny - (FMM_K + 1) * b;
+    const int nbx = fmm_cell(mxx, x0, inv_b) + FMM_K + 2;
+    const int nby = fmm_cell(mxy, y0, inv_b) + FMM_K + 2;
+    if (nbx > FMM_G || nby > FMM_G || nbx < 1 || nby < 1) ok = false;
+    P->x0 = x0;
+    P->y0 = y0;
+    P->b = b;
+    P->inv_b = inv_b;
+    P->nbx = min(max(nbx, 1), FMM_G);
+    P->nby = min(max(nby, 1), FMM_G);
+    P->ok = ok ? 1 : 0;
+    P->nocc = 0;
+    P->pool_used = 0;
+    P->cap = cap;
+    P->pool_cap = pool_cap;
+}
+
+__global__ void fmm_occupy_kernel(const float2* z, int64_t npts, FmmParams* P, uint8_t* occ) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= npts || !P->ok) return;
+    const float2 v = z[p];
+    const int cx = fmm_cell(v.x, P->x0, P->inv_b), cy = fmm_cell(v.y, P->y0, P->inv_b);
+    if (cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby)
+        occ[(int64_t)cy * P->nbx + cx] = 1;
+    else
+        P->ok = 0;
+}
+
+__global__ void fmm_slot_kernel(FmmParams* P, const uint8_t* occ, int* slot, int2* boxlist) {
+    const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t ncell = (int64_t)P->nbx * P->nby;
+    if (cell >= ncell) return;
+    int v = -1;
+    if (occ[cell]) {
+        const int idx = atomicAdd(&P->nocc, 1);
+        if (idx < P->cap) {
+            v = idx;
+            boxlist[idx] = make_int2((int)(cell % P->nbx), (int)(cell / P->nbx));
+        } else {
+            P->ok = 0;
+        }
+    }
+    slot[cell] = v;
+}
+
+// One CTA (FMM_WARPS warps) per occupied cell: near list in star order, local expansion
+// of the far stars (lane-private accumulators in shared memory, then a fixed-order sum),
+// truncation bound.
+constexpr int FMM_WARPS = 4;
+constexpr int FMM_CT = FMM_WARPS * 32;
+constexpr int FMM_ACC = FMM_WARPS * FMM_P * 32;  // floats per accumulator component
+__global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const int2* boxlist, const float4* dfp,
+                                                           const float2* dfm, const float4* s32, int n,
+                                                           BoxInfo* info, float4* coeff, int* pool) {
+    extern __shared__ __align__(16) float acc[];  // [4 components][warp][k][lane]
+    __shared__ int s_wcnt[FMM_WARPS];
+    __shared__ int s_off, s_cnt;
+    __shared__ float s_r2[FMM_CT], s_dmin[FMM_CT];
+    __shared__ int s_ok, s_nocc;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_ok = P->ok;
+        s_nocc = min(P->nocc, P->cap);
+    }
+    __syncthreads();
+    if (!s_ok) return;  // block-uniform
+    const int nocc = s_nocc;
+    for (int box = blockIdx.x; box < nocc; box += gridDim.x) {
+        const int2 bc = boxlist[box];
+        const double cxd = (double)P->x0 + ((double)bc.x + 0.5) * (double)P->b;
+        const double cyd = (double)P->y0 + ((double)bc.y + 0.5) * (double)P->b;
+        const df cx = df_from_double(cxd), cy = df_from_double(cyd);
+        // near list: count, reserve, ordered write
+        int cnt = 0;
+        for (int j = tid; j < n; j += FMM_CT) {
+            const float4 sp = s32[j];
+            const int sx = fmm_cell(sp.x, P->x0, P->inv_b), sy = fmm_cell(sp.y, P->y0, P->inv_b);
+            cnt += (abs(sx - bc.x) <= FMM_K && abs(sy - bc.y) <= FMM_K);
+        }
+        for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+        if (lane == 0) s_wcnt[warp] = cnt;
+        __syncthreads();
+        if (tid == 0) {
+            int tot = 0;
+            for (int w = 0; w < FMM_WARPS; w++) tot += s_wcnt[w];
+            const int off = atomicAdd(&P->pool_used, tot);
+            if (off + tot > P->pool_cap) P->ok = 0;
+            s_off = off;
+            s_cnt = tot;
+        }
+        __syncthreads();
+        const bool room = s_off + s_cnt <= P->pool_cap;
+        int base = 0;
+        for (int j0 = 0; j0 < n; j0 += FMM_CT) {
+            const int j = j0 + tid;
+            bool nr_ = false;
+            if (j < n) {
+                const float4 sp = s32[j];
+                const int sx = fmm_cell(sp.x, P->x0, P->inv_b), sy = fmm_cell(sp.y, P->y0, P->inv_b);
+                nr_ = abs(sx - bc.x) <= FMM_K && abs(sy - bc.y) <= FMM_K;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, nr_);
+            if (lane == 0) s_wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w = 0; w < FMM_WARPS; w++) {
+                if (w < warp) before += s_wcnt[w];
+                total += s_wcnt[w];
+            }
+            if (nr_ && room) pool[s_off + base + before + __popc(bal & ((1u << lane) - 1u))] = j;
+            base += total;
+            __syncthreads();
+        }
+        // far stars: lane-private accumulation of L_k = -sum m u^(k+1), u = 1/(z_i - c)
+        for (int q = tid; q < 4 * FMM_ACC; q += FMM_CT) acc[q] = 0.f;
+        float r2 = 0.f, dmin = 3.0e38f;
+        __syncthreads();
+        for (int j = tid; j < n; j += FMM_CT) {
+            const float4 sp = s32[j];
+            const int sx = fmm_cell(sp.x, P->x0, P->inv_b), sy = fmm_cell(sp.y, P->y0, P->inv_b);
+            if (abs(sx - bc.x) <= FMM_K && abs(sy - bc.y) <= FMM_K) continue;
+            const float4 pd = dfp[j];
+            const float2 md = dfm[j];
+            const df dx = df_sub(df{pd.x, pd.y}, cx), dy = df_sub(df{pd.z, pd.w}, cy);
+            const df inv = df_rcp(df_add(df_sqr(dx), df_sqr(dy)));
+            const df ux = df_mul(dx, inv), uy = df_neg(df_mul(dy, inv));  // u = 1/(z_i - c)
+            df wx = df_mul(df{md.x, md.y}, ux), wy = df_mul(df{md.x, md.y}, uy);
+            const float dd = sqrtf(dx.hi * dx.hi + dy.hi * dy.hi);
+            r2 += md.x / (dd * dd);
+            dmin = fminf(dmin, dd);
+            for (int k = 0; k < FMM_P; k++) {
+                const int a = ((warp * FMM_P + k) << 5) + lane;
+                df ax = df{acc[a], acc[a + FMM_ACC]}, ay = df{acc[a + 2 * FMM_ACC], acc[a + 3 * FMM_ACC]};
+                ax = df_sub(ax, wx);
+                ay = df_sub(ay, wy);
+                acc[a] = ax.hi;
+                acc[a + FMM_ACC] = ax.lo;
+                acc[a + 2 * FMM_ACC] = ay.hi;
+                acc[a + 3 * FMM_ACC] = ay.lo;
+                const df nx = df_sub(df_mul(wx, ux), df_mul(wy, uy));  // w <- w u
+                const df ny = df_add(df_mul(wx, uy), df_mul(wy, ux));
+                wx = nx;
+                wy = ny;
+            }
+        }
+        s_r2[tid] = r2;
+        s_dmin[tid] = dmin;
+        __syncthreads();
+        if (tid < FMM_P) {
+            df sx = df{0.f, 0.f}, sy = df{0.f, 0.f};
+            for (int w = 0; w < FMM_WARPS; w++)
+                for (int l = 0; l < 32; l++) {
+                    const int a = ((w * FMM_P + tid) << 5) + l;
+                    sx = df_add(sx, df{acc[a], acc[a + FMM_ACC]});
+                    sy = df_add(sy, df{acc[a + 2 * FMM_ACC], acc[a + 3 * FMM_ACC]});
+                }
+            coeff[(size_t)box * FMM_P + tid] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
+        }
+        if (tid == 0) {
+            float R2 = 0.f, D = 3.0e38f;
+            for (int t = 0; t < FMM_CT; t++) {
+                R2 += s_r2[t];
+                D = fminf(D, s_dmin[t]);
+            }
+            BoxInfo bi;
+            bi.c = make_float4(cx.hi, cx.lo, cy.hi, cy.lo);
+            bi.near_off = s_off;
+            bi.near_cnt = room ? s_cnt : 0;
+            // |z - c| <= 0.72 b (half-diagonal plus the Newton steps); the tail of -S1_far'
+            // after P terms is at most sum_far m/|d|^2 * P rho^(P-1) / (1 - rho)^2
+            float s2e = 0.f;
+            if (R2 > 0.f) {
+                const float rho = fminf(0.72f * P->b / D, 0.99f);
+                s2e = R2 * (float)FMM_P * powf(rho, (float)(FMM_P - 1)) / ((1.f - rho) * (1.f - rho));
+            }
+            bi.s2_err = s2e;
+            bi.pad = 0.f;
+            info[box] = bi;
+        }
+        __syncthreads();
+    }
+}
+
+// Points: warp = one chain (global column g), 32 consecutive rows, so that a warp's
+// points sit in one or two neighbouring cells.
+template <bool UNIT>
+__global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const FmmParams* Pm, const int* slot,
+                                                                const BoxInfo* info, const float4* coeff,
+                                                                const int* pool) {
+    if (!Pm->ok) return;  // grid-uniform (set before this launch)
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = blockIdx.x * (int64_t)(PB_THREADS / 32) + (threadIdx.x >> 5);
+    const int64_t g = wg % K.nr;
+    const int64_t row0 = (wg / K.nr) * 32 + lane;
+    const bool valid = wg < K.nr * ((K.m + 32) / 32) && row0 <= K.m;
+    int passes = 0;
+    double est_max = 0.0;
+    if (valid) {
+    const int64_t row = row0;
+    const int64_t point = row * K.nr + g;
+    const int s = subchain_of_row(row, K.m, K.S);
+    const int32_t k = K.perm[(size_t)s * K.nr + g];
+    const float2 z0 = K.zrows[(size_t)row * K.nr + k];
+    const int32_t it_in = K.iters_out ? K.iters_in[(size_t)row * K.nr + k] : 0;
+    const int cx = fmm_cell(z0.x, Pm->x0, Pm->inv_b), cy = fmm_cell(z0.y, Pm->y0, Pm->inv_b);
+    const int sl = slot[(int64_t)cy * Pm->nbx + cx];
+    const BoxInfo bi = info[sl];
+    const float4* L = coeff + (size_t)sl * FMM_P;
+    double zx = z0.x, zy = z0.y;
+    for (int pass = 0; pass < K.max_polish; pass++) {
+        passes++;
+        Sums sm;
+        sm.S1x = sm.S1y = sm.S2x = sm.S2y = df{0.f, 0.f};
+        sm.s3x = sm.s3y = sm.s4x = sm.s4y = sm.a3 = 0.f;
+        const df zxd = df_from_double(zx), zyd = df_from_double(zy);
+        for (int q = 0; q < bi.near_cnt; q++) {
+            const int j = pool[bi.near_off + q];
+            star_df<UNIT>(zxd, zyd, K.dfp[j], K.dfm[j], sm);
+        }
+        // far field: Horner with derivatives in t = z - c
+        const df tx = df_sub(zxd, df{bi.c.x, bi.c.y}), ty = df_sub(zyd, df{bi.c.z, bi.c.w});
+        const float4 top = L[FMM_P - 1];
+        df b0x = df{top.x, top.y}, b0y = df{top.z, top.w};
+        df b1x = df{0.f, 0.f}, b1y = df{0.f, 0.f};
+        float b2x = 0.f, b2y = 0.f, b3x = 0.f, b3y = 0.f;
+        const float tfx = tx.hi, tfy = ty.hi;
+        for (int kk = FMM_P - 2; kk >= 0; kk--) {
+            // b3 <- b3 t + b2 ; b2 <- b2 t + b1 ; b1 <- b1 t + b0 ; b0 <- b0 t + L_k
+            const float n3x = fmaf(b3x, tfx, fmaf(-b3y, tfy, b2x)), n3y = fmaf(b3x, tfy, fmaf(b3y, tfx, b2y));
+            const float n2x = fmaf(b2x, tfx, fmaf(-b2y, tfy, b1x.hi)), n2y = fmaf(b2x, tfy, fmaf(b2y, tfx, b1y.hi));
+            b3x = n3x;
+            b3y = n3y;
+            b2x = n2x;
+            b2y = n2y;
+            const df m1x = df_add(df_sub(df_mul(b1x, tx), df_mul(b1y, ty)), b0x);
+            const df m1y = df_add(df_add(df_mul(b1x, ty), df_mul(b1y, tx)), b0y);
+            const float4 Lk = L[kk];
+            const df m0x = df_add(df_sub(df_mul(b0x, tx), df_mul(b0y, ty)), df{Lk.x, Lk.y});
+            const df m0y = df_add(df_add(df_mul(b0x, ty), df_mul(b0y, tx)), df{Lk.z, Lk.w});
+            b1x = m1x;
+            b1y = m1y;
+            b0x = m0x;
+            b0y = m0y;
+        }
+        // S1 += b0, S2 += -b1, S3 += b2, S4 += -b3
+        sm.S1x = df_add(sm.S1x, b0x);
+        sm.S1y = df_add(sm.S1y, b0y);
+        sm.S2x = df_sub(sm.S2x, b1x);
+        sm.S2y = df_sub(sm.S2y, b1y);
+        sm.s3x += b2x;
+        sm.s3y += b2y;
+        sm.s4x -= b3x;
+        sm.s4y -= b3y;
+        sm.a3 += 4.0f * (fabsf(b2x) + fabsf(b2y));
+        double est = 0.0;
+        if (polish_epilogue(K, point, row, df_to_double(sm.S1x), df_to_double(sm.S1y), df_to_double(sm.S2x),
+                            df_to_double(sm.S2y), sm.s3x, sm.s3y, sm.s4x, sm.s4y, sm.a3, zx, zy, z0.x, z0.y, pass,
+                            it_in, est, (double)bi.s2_err)) {
+            est_max = est;
+            break;
+        }
+    }
+    }  // valid
+    for (int off = 16; off > 0; off >>= 1) {
+        passes += __shfl_xor_sync(0xffffffffu, passes, off);
+        est_max = fmax(est_max, __shfl_xor_sync(0xffffffffu, est_max, off));
+    }
+    if (lane == 0) {
+        if (passes) atomicAdd(&K.rep->polish_passes, (unsigned long long)passes);
+        if (est_max > 0.0) atomic_max_double_nonneg(&K.rep->max_err_est, est_max);
+    }
+}
+
+size_t fmm_workspace_bytes(int64_t points) {
+    const int64_t cap = points < (1 << 18) ? points : (1 << 18);
+    const int64_t pool = cap * 64 < (1 << 24) ? cap * 64 : (1 << 24);
+    size_t b = 0;
+    auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
+    add(sizeof(FmmParams));
+    add(sizeof(float4) * 512);
+    add((size_t)FMM_G * FMM_G);                 // occupancy
+    add(sizeof(int) * (size_t)FMM_G * FMM_G);   // slots
+    add(sizeof(int2) * cap);
+    add(sizeof(BoxInfo) * cap);
+    add(sizeof(float4) * FMM_P * cap);
+    add(sizeof(int) * pool);
+    return b;
+}
+
+cudaError_t launch_polish_fmm(const PolishArgs& a, void* ws, cudaStream_t st) {
+    const int64_t points = (a.m + 1) * a.nr;
+    const int cap = (int)(points < (1 << 18) ? points : (1 << 18));
+    const int pool_cap = (int)((int64_t)cap * 64 < (1 << 24) ? (int64_t)cap * 64 : (1 << 24));
+    char* p = (char*)ws;
+    auto take = [&](size_t x) {
+        char* r = p;
+        p += (x + 255) / 256 * 256;
+        return r;
+    };
+    FmmParams* P = (FmmParams*)take(sizeof(FmmParams));
+    float4* part = (float4*)take(sizeof(float4) * 512);
+    uint8_t* occ = (uint8_t*)take((size_t)FMM_G * FMM_G);
+    int* slot = (int*)take(sizeof(int) * (size_t)FMM_G * FMM_G);
+    int2* boxlist = (int2*)take(sizeof(int2) * cap);
+    BoxInfo* info = (BoxInfo*)take(sizeof(BoxInfo) * cap);
+    float4* coeff = (float4*)take(sizeof(float4) * FMM_P * (size_t)cap);
+    int* pool = (int*)take(sizeof(int) * (size_t)pool_cap);
+    cudaError_t e;
+    fmm_extent_kernel<<<512, 256, 0, st>>>(a.zrows, points, part);
+    fmm_setup_kernel<<<1, 32, 0, st>>>(part, 512, a.f->fmm_cell, cap, pool_cap, P);
+    if ((e = cudaMemsetAsync(occ, 0, (size_t)FMM_G * FMM_G, st)) != cudaSuccess) return e;
+    fmm_occupy_kernel<<<(unsigned)((points + 255) / 256), 256, 0, st>>>(a.zrows, points, P, occ);
+    fmm_slot_kernel<<<(unsigned)(((int64_t)FMM_G * FMM_G + 255) / 256), 256, 0, st>>>(P, occ, slot, boxlist);
+    const size_t csmem = sizeof(float) * 4 * FMM_ACC;
+    if ((e = cudaFuncSetAttribute(fmm_coeff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem)) !=
+        cudaSuccess)
+        return e;
+    fmm_coeff_kernel<<<1216, FMM_CT, csmem, st>>>(P, boxlist, a.f->star_dfp, a.f->star_dfm, a.f->star32,
+                                                  (int)a.f->n, info, coeff, pool);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    PolishK K = make_polish_k(a);
+    const int64_t warps = ((a.m + 1 + 31) / 32) * a.nr;
+    const unsigned blocks = (unsigned)((warps + (PB_THREADS / 32) - 1) / (PB_THREADS / 32));
+    if (a.f->unit_mass)
+        fmm_polish_kernel<true><<<blocks, PB_THREADS, 0, st>>>(K, P, slot, info, coeff, pool);
+    else
+        fmm_polish_kernel<false><<<blocks, PB_THREADS, 0, st>>>(K, P, slot, info, coeff, pool);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the direct polish runs (and does the whole job) only when the tables did not fit
+    PolishArgs b = a;
+    b.skip_if = &P->ok;
+    return launch_polish(b, st);
 }
 
 // ----------------------------------------------------------------------------------

@@ -215,3 +215,23 @@ def test_moving_distance_map_on_real_caustics():
         got = cc.moving_distance_map(torch.from_numpy(ncc).cuda(), 6 / 128, angle).cpu().numpy()
         assert np.array_equal(got, ref)
         assert np.isfinite(ref).any() and np.isinf(ref).any()
+
+
+@pytest.mark.parametrize("n,msteps,ks,g", [(400, 300, 0.0, 0.35), (1500, 40, 0.2, 0.55)])
+def test_far_field_polish_matches_oracle_and_direct(n, msteps, ks, g):
+    """The local-expansion polish (stars beyond a 5x5 block of cells through 32-term local
+    expansions) agrees with the oracle and with the all-direct polish within 1e-9."""
+    f = synth.disc_field(n, 0.45, ks, g, synth.stream_seed(12, n), "loguniform", normalise=True)
+    zf, wf, _, st, rep = _solve(f.x, f.y, f.m, ks, g, msteps)
+    assert st == cc.CC_OK and rep["uncertified"] == 0, rep
+    zd, wd, _, st2, rep2 = _solve(f.x, f.y, f.m, ks, g, msteps, far_field=0)
+    assert st2 == cc.CC_OK
+    # each side is certified to 1e-10 (tol_cert), so they agree to twice that plus rounding
+    assert np.abs(zf - zd).max() < 3e-10 and np.abs(wf - wd).max() < 3e-10
+    rows = [0, msteps // 3, msteps // 2, msteps]
+    for j in rows:
+        zo, left = oracle.solve_row(f.x, f.y, f.m, ks, g, oracle.phi(j, msteps))
+        idx, dist, sep = match_row(zf[j], zo)
+        assert dist < TOL and len(set(idx.tolist())) == len(idx)
+        wo = oracle.map_caustics(f.x, f.y, f.m, ks, g, zo[idx])
+        assert np.abs(wf[j] - wo).max() < TOL
