@@ -32,11 +32,14 @@ if ROOT not in sys.path:
 METRIC = "critical-curve roots/s at 1e-9 theta_E (batched/served vs plain FP64); p99 latency"
 UNIT = "roots/s"
 
-# FP32 pipe operations (FADD, FMUL, FFMA each counted once) per star / per root
-# interaction of the FP32 tracer (acc_star / acc_root in csrc/aberth.cu): the tracer is the
-# dominant kernel once the polish uses local expansions.
+# FP32 pipe operations (FADD, FMUL, FFMA each counted once) of the FP32 tracer (the dominant
+# kernel once the polish uses local expansions), csrc/aberth.cu: per star term summed
+# directly (acc_star), per root-root term (acc_root), and per evaluation of a cell's two
+# 14-term local expansions with the first two derivatives (13 Horner steps of 4 complex
+# multiply-adds, 16 FP32 ops each).
 TRACE_OPS_PER_STAR = 21
 TRACE_OPS_PER_ROOT = 6
+TRACE_OPS_PER_FAR_EVAL = 13 * 16
 
 
 def parse():
@@ -279,7 +282,8 @@ def run_ours(args):
     peaks, peak_src = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak_tops = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lane-ops per second at max clock
-    trace_ops = rep["root_iterations"] * (f.n * TRACE_OPS_PER_STAR + nr * TRACE_OPS_PER_ROOT)
+    trace_ops = (rep["star_terms"] * TRACE_OPS_PER_STAR + rep["root_iterations"] * nr * TRACE_OPS_PER_ROOT
+                 + rep["far_evals"] * TRACE_OPS_PER_FAR_EVAL)
     stage = {"trace_ms": trace_ms, "join_ms": join_ms, "polish_caustic_ms": polish_ms,
              "crossing_ms": cross_ms, "distance_ms": dist_ms}
     achieved = trace_ops / (trace_ms / 1e3) / 1e12
@@ -287,9 +291,10 @@ def run_ours(args):
                 "achieved": round(achieved, 3), "peak": round(fp32_peak_tops, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak_tops, 4), "traffic": None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (FP32 pipe ops, FADD/FMUL/FFMA = 1)",
-                "ops_per_interaction": {"star": TRACE_OPS_PER_STAR, "root": TRACE_OPS_PER_ROOT},
-                "units": f"{rep['root_iterations']} root-iterations x (N x {TRACE_OPS_PER_STAR} + n_r x "
-                         f"{TRACE_OPS_PER_ROOT}) FP32 ops"}
+                "ops_per_unit": {"star_term": TRACE_OPS_PER_STAR, "root_term": TRACE_OPS_PER_ROOT,
+                                 "far_eval": TRACE_OPS_PER_FAR_EVAL},
+                "units": f"{rep['star_terms']} star terms, {rep['root_iterations']} root-iterations x {nr} root "
+                         f"terms, {rep['far_evals']} expansion evaluations"}
     # crossing map: algorithmic bytes = vertex reads + one int32 read+write per pixel for
     # the scan + the clearing store
     cross_bytes = rows * nr * 16 + 3 * px * px * 4

@@ -104,6 +104,8 @@ typedef struct cc_report {
                                   rest of its row fixed) and now converged */
     int64_t jumped;            /* points the polish moved > 1e-3 (1 + |z|) from the tracer's
                                   root (a sign of a root swap; diagnostic) */
+    int64_t star_terms;        /* tracer: star terms summed directly (all roots, iterations) */
+    int64_t far_evals;         /* tracer: root updates that used a cell's local expansions */
 } cc_report;
 
 /* Fill *opt with the defaults listed above. */

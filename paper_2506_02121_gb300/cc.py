@@ -47,7 +47,8 @@ class Report(ctypes.Structure):
                 ("uncertified", ctypes.c_int64), ("seam_ambiguous", ctypes.c_int64),
                 ("max_iter_row", ctypes.c_int32), ("timeout", ctypes.c_int32), ("max_err_est", ctypes.c_double),
                 ("trace_ms", ctypes.c_float), ("join_ms", ctypes.c_float), ("polish_ms", ctypes.c_float),
-                ("rescued_points", ctypes.c_int64), ("jumped", ctypes.c_int64)]
+                ("rescued_points", ctypes.c_int64), ("jumped", ctypes.c_int64),
+                ("star_terms", ctypes.c_int64), ("far_evals", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

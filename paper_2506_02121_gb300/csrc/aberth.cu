@@ -107,6 +107,11 @@ struct TK {
     DevReport* rep;
     double tol_abs, mu_max;
     int max_iter_cold, max_iter_warm, predictor;
+    // FP32 far-field tables (tfmm.ok == 0: every star summed directly)
+    TfmmParams tfmm;
+    const TCell* tcells;
+    const int* tnear;
+    const float4* tcoeff;
 };
 
 template <typename T>
@@ -120,10 +125,239 @@ struct Ctx {
     float* dprev;
     int *conv, *it, *act;
     bool resident;
+    unsigned long long* n_terms;  // this thread's work counters (registers of the caller)
+    unsigned long long* n_far;
 };
 
+// One other root in FP32, without a branch: D += 1/(z_k - z_r).  The tiny constant added
+// to |d|^2 turns the root's own term into 0 * 1e30 = 0 and leaves every other term as it
+// was (two roots that FP32 can tell apart at |z| >= 1e-3 have |d|^2 >= 1e-20).
+__device__ __forceinline__ void acc_root_f(float zx, float zy, float rx, float ry, float& Dx, float& Dy) {
+    const float dx = zx - rx, dy = zy - ry;
+    const float inv = rcp_approx(fmaf(dx, dx, fmaf(dy, dy, 1e-30f)));
+    Dx = fmaf(dx, inv, Dx);
+    Dy = fmaf(-dy, inv, Dy);
+}
+
+// 16-byte load from shared memory (two FP32 roots); a warp that reads one address gets it
+// by broadcast.
+__device__ __forceinline__ float4 lds_f4(unsigned addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+// Cell of z in the FP32 far-field grid, or -1 when every star is summed directly (FP64
+// tracer, no grid, z outside it, or a cell with too many near stars).
+template <typename T>
+__device__ __forceinline__ int far_cell(const TK& K, T zx, T zy) {
+    if (sizeof(T) != 4 || !K.tfmm.ok) return -1;
+    const float fx = floorf(((float)zx - K.tfmm.x0) * K.tfmm.inv_b);
+    const float fy = floorf(((float)zy - K.tfmm.y0) * K.tfmm.inv_b);
+    if (!(fx >= 0.f && fy >= 0.f && fx < (float)K.tfmm.nbx && fy < (float)K.tfmm.nby)) return -1;
+    const int c = (int)fy * K.tfmm.nbx + (int)fx;
+    return K.tcells[c].near_cnt >= 0 ? c : -1;
+}
+
+// Star terms of a root in a far-field cell: its near stars (lanes lane, lane + g, ...) and,
+// on lane 0, the cell's two local expansions by Horner, U(t) = sum U_k t^k -> C and
+// S1(t) = sum L_k t^k with its first and half second derivative -> A = -S1', B = S1''/2.
+template <typename T>
+__device__ __forceinline__ void cell_part(const Ctx<T>& x, int cell, T zx, T zy, int lane, int g, Acc<T>& acc) {
+    const TK& K = *x.k;
+    const TCell tc = K.tcells[cell];
+    const int* nl = K.tnear + (size_t)cell * TFMM_NEAR_MAX;
+    const typename CT<T>::Star* gs = (const typename CT<T>::Star*)K.stars;
+    for (int q = lane; q < tc.near_cnt; q += g) {
+        const int j = nl[q];
+        acc_star(zx, zy, x.resident ? x.s_star[j] : gs[j], acc);
+    }
+    if (lane != 0) return;
+    const float tx = (float)zx - tc.cx, ty = (float)zy - tc.cy;
+    const float4* L = K.tcoeff + (size_t)cell * TFMM_P;
+    const float4 top = L[TFMM_P - 1];
+    float ux = top.x, uy = top.y, b0x = top.z, b0y = top.w;
+    float b1x = 0.f, b1y = 0.f, b2x = 0.f, b2y = 0.f;
+#pragma unroll
+    for (int kk = TFMM_P - 2; kk >= 0; kk--) {
+        const float4 c4 = L[kk];
+        const float n2x = fmaf(b2x, tx, fmaf(-b2y, ty, b1x)), n2y = fmaf(b2x, ty, fmaf(b2y, tx, b1y));
+        const float n1x = fmaf(b1x, tx, fmaf(-b1y, ty, b0x)), n1y = fmaf(b1x, ty, fmaf(b1y, tx, b0y));
+        const float n0x = fmaf(b0x, tx, fmaf(-b0y, ty, c4.z)), n0y = fmaf(b0x, ty, fmaf(b0y, tx, c4.w));
+        const float nux = fmaf(ux, tx, fmaf(-uy, ty, c4.x)), nuy = fmaf(ux, ty, fmaf(uy, tx, c4.y));
+        b2x = n2x;
+        b2y = n2y;
+        b1x = n1x;
+        b1y = n1y;
+        b0x = n0x;
+        b0y = n0y;
+        ux = nux;
+        uy = nuy;
+    }
+    acc.Cx += (T)ux;
+    acc.Cy += (T)uy;
+    acc.Ax -= (T)b1x;
+    acc.Ay -= (T)b1y;
+    acc.Bx += (T)b2x;
+    acc.By += (T)b2y;
+    acc.Am += (T)tc.far_m_d2;
+}
+
+// Aberth update of one root from its sums (Eq. 9 with F, F' of Eqs. 6-7), and the stop rule.
+template <typename T>
+__device__ __forceinline__ void finish_root(const Ctx<T>& x, int key, typename CT<T>::C z, const Acc<T>& acc, T cph,
+                                            T sph, int* s_maxit) {
+    using C = typename CT<T>::C;
+    const TK& K = *x.k;
+    const T oms = (T)(1.0 - K.kappa_s);
+    const T gam = (T)K.gamma;
+    // F = gamma + A - (1 - kappa_s) e^{-i phi}
+    const T Fx = gam + acc.Ax - oms * cph;
+    const T Fy = acc.Ay + oms * sph;
+    C zn = z;
+    T ad = 0;
+    if (Fx != (T)0 || Fy != (T)0) {
+        const T dFx = (T)-2 * acc.Bx, dFy = (T)-2 * acc.By;
+        const T fden = Fx * Fx + Fy * Fy;
+        const T qx = qdiv(dFx * Fx + dFy * Fy, fden);
+        const T qy = qdiv(dFy * Fx - dFx * Fy, fden);
+        const T px = qx + (T)2 * acc.Cx - acc.Dx;
+        const T py = qy + (T)2 * acc.Cy - acc.Dy;
+        const T pden = px * px + py * py;
+        const T delx = qdiv(px, pden), dely = qdiv(-py, pden);
+        zn.x = z.x - delx;
+        zn.y = z.y - dely;
+        ad = qsqrt(delx * delx + dely * dely);
+    }
+    const int its = x.it[key] + 1;
+    x.it[key] = its;
+    atomicMax(s_maxit, its);
+    bool done;
+    if (sizeof(T) == 4) {
+        // FP32: freeze at the absolute tolerance or at the rounding floor of this root: a
+        // few ulp of |z|, or the FP32 noise of F (~eps sum |m/d^2|) divided by |F'|; or when
+        // the corrections stop shrinking within a few times that floor.
+        const T sc = (T)1 + qsqrt(z.x * z.x + z.y * z.y);
+        const T fpa = (T)2 * qsqrt(acc.Bx * acc.Bx + acc.By * acc.By);
+        const T noise = (T)(4.0 * FLT_EPSILON) * (acc.Am + fabs(gam) + oms);
+        T tolz = fmax((T)K.tol_abs, (T)(8.0 * FLT_EPSILON) * sc);
+        if (fpa > (T)0) tolz = fmax(tolz, (T)4 * noise * qdiv((T)1, fpa));
+        // never looser than 64x the ulp floor: an iterate that runs away where F' vanishes
+        // must not count as converged
+        tolz = fmin(tolz, (T)(512.0 * FLT_EPSILON) * sc);
+        done = !(ad >= tolz) || (its >= 3 && ad > (T)0.25 * (T)x.dprev[key] && ad < (T)4 * tolz);
+    } else {
+        done = !(ad >= (T)K.tol_abs);
+        if (!done && K.mu_max > 0) {
+            const T gx = gam + acc.Ax, gy = acc.Ay;
+            const T detj = oms * oms - (gx * gx + gy * gy);
+            done = fabs((double)detj) * K.mu_max < 1.0;
+        }
+    }
+    x.dprev[key] = (float)ad;
+    if (done) x.conv[key] = 1;
+    x.nxt[key] = zn;
+}
+
+// One sweep over the active FP32 roots with R roots per thread.  Slots [0, A0) hold the
+// direction-0 roots, [A0p, A0p + A1) the direction-1 roots, A0p = A0 rounded up to 32 R so
+// that a warp never mixes the directions and every root-tile load is a broadcast.
+template <int R>
+__device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool a1, int A0, int A1, float cph0,
+                                              float sph0, float cph1, float sph1, int* s_maxit) {
+    using C = float2;
+    constexpr int TS = CT<float>::TS;
+    const TK& K = *x.k;
+    const int tid = threadIdx.x, P = blockDim.x;
+    const int nr = K.nr, n = K.n;
+    const int A0p = (A0 + 32 * R - 1) / (32 * R) * (32 * R);
+    const int nq = A0p / R + (A1 + R - 1) / R;  // thread items
+    for (int qb = 0; qb < nq; qb += P) {
+        const int q = qb + tid;
+        const int s0 = q * R;
+        const int d = s0 >= A0p ? 1 : 0;
+        int key[R];
+        bool valid[R];
+        C z[R];
+        int cell[R];
+        Acc<float> acc[R];
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int s = s0 + r;
+            valid[r] = q < nq && (d ? s - A0p < A1 : s < A0);
+            key[r] = valid[r] ? (d ? x.act[nr + s - A0p] : x.act[s]) : -1;
+            any |= valid[r];
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int kk = valid[r] ? key[r] : (valid[0] ? key[0] : 0);
+            z[r] = x.cur[kk];
+            acc[r] = Acc<float>{0, 0, 0, 0, 0, 0, 0, 0, 0};
+            cell[r] = valid[r] ? far_cell<float>(K, z[r].x, z[r].y) : -1;
+            if (valid[r]) {
+                *x.n_terms += (unsigned long long)(cell[r] >= 0 ? K.tcells[cell[r]].near_cnt : n);
+                *x.n_far += cell[r] >= 0 ? 1ull : 0ull;
+                if (cell[r] >= 0) cell_part<float>(x, cell[r], z[r].x, z[r].y, 0, 1, acc[r]);
+            }
+        }
+        for (int t0 = 0; t0 < n; t0 += TS) {
+            const int tn = min(TS, n - t0);
+            if (!x.resident) {
+                __syncthreads();
+                const float4* gs = (const float4*)K.stars;
+                for (int j = tid; j < tn; j += P) x.s_star[j] = gs[t0 + j];
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                if (valid[r] && cell[r] < 0) {
+#pragma unroll 4
+                    for (int j = 0; j < tn; j++) acc_star(z[r].x, z[r].y, x.s_star[j], acc[r]);
+                }
+            }
+        }
+        for (int t0 = 0; t0 < nr; t0 += TR) {
+            const int tn = min(TR, nr - t0);
+            __syncthreads();
+            for (int j = tid; j < tn; j += P) {
+                if (a0) x.s_root[j] = x.cur[t0 + j];
+                if (a1) x.s_root[TR + j] = x.cur[nr + t0 + j];
+            }
+            __syncthreads();
+            if (any) {
+                const unsigned base = (unsigned)__cvta_generic_to_shared(x.s_root + d * TR);
+                const int tn2 = tn >> 1;
+#pragma unroll 2
+                for (int j2 = 0; j2 < tn2; j2++) {
+                    const float4 p = lds_f4(base + 16u * (unsigned)j2);
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        acc_root_f(z[r].x, z[r].y, p.x, p.y, acc[r].Dx, acc[r].Dy);
+                        acc_root_f(z[r].x, z[r].y, p.z, p.w, acc[r].Dx, acc[r].Dy);
+                    }
+                }
+                if (tn & 1) {
+                    const C p = x.s_root[d * TR + tn - 1];
+#pragma unroll
+                    for (int r = 0; r < R; r++) acc_root_f(z[r].x, z[r].y, p.x, p.y, acc[r].Dx, acc[r].Dy);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            if (valid[r]) finish_root<float>(x, key[r], z[r], acc[r], d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
+    }
+}
+
 // Run Jacobi Aberth sweeps on the active rows (dir 0: row0, dir 1: row1) until every root
-// is frozen or max_iter sweeps were made.  Called by all threads of the CTA.
+// is frozen or max_iter sweeps were made.  Called by all threads of the CTA.  The unfrozen
+// roots of direction d are listed in act[d nr, d nr + A_d).  With many of them the FP32
+// tracer gives each thread several roots of one direction (sweep_blocked); otherwise g
+// lanes share a root and reduce their partial sums with shuffles.
 template <typename T>
 __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int64_t row0, int64_t row1,
                                           int max_iter, bool cold, bool report, int* s_count, int* s_maxit) {
@@ -132,8 +366,6 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
     const TK& K = *x.k;
     const int tid = threadIdx.x, P = blockDim.x;
     const int nr = K.nr, n = K.n;
-    const T oms = (T)(1.0 - K.kappa_s);
-    const T gam = (T)K.gamma;
     T cph0 = 0, sph0 = 0, cph1 = 0, sph1 = 0;
     if (a0) {
         double2 ph = K.phase[row0];
@@ -147,14 +379,16 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
     }
     for (int iter = 0;; iter++) {
         __syncthreads();
-        if (tid == 0) *s_count = 0;
+        if (tid < 2) s_count[tid] = 0;
         __syncthreads();
         for (int key = tid; key < 2 * nr; key += P) {
-            bool on = key < nr ? a0 : a1;
-            if (on && !x.conv[key]) x.act[atomicAdd(s_count, 1)] = key;
+            const int d = key >= nr;
+            const bool on = d ? a1 : a0;
+            if (on && !x.conv[key]) x.act[d * nr + atomicAdd(&s_count[d], 1)] = key;
         }
         __syncthreads();
-        const int A = *s_count;
+        const int A0 = s_count[0], A1 = s_count[1];
+        const int A = A0 + A1;
         if (A == 0) break;
         if (iter >= max_iter) {
             if (tid == 0 && report) atomicAdd(&K.rep->unconverged, (unsigned long long)A);
@@ -164,112 +398,85 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             atomicAdd(&K.rep->root_iterations, (unsigned long long)A);
             if (cold) atomicAdd(&K.rep->cold_root_iterations, (unsigned long long)A);
         }
-        int g = P / A;
-        g = g < 1 ? 1 : (g > 32 ? 32 : g);
-        g = 1 << (31 - __clz(g));  // power of two
-        const int groups = P / g;
-        const int lane = tid & (g - 1);
-        const int gid = tid / g;
-        for (int base = 0; base < A; base += groups) {
-            const int slot = base + gid;
-            const bool valid = slot < A;
-            const int key = valid ? x.act[slot] : 0;
-            const int d = key >= nr;
-            const C z = x.cur[key];
-            Acc<T> acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-            for (int t0 = 0; t0 < n; t0 += TS) {
-                const int tn = min(TS, n - t0);
-                if (!x.resident) {
-                    __syncthreads();
-                    const typename CT<T>::Star* gs = (const typename CT<T>::Star*)K.stars;
-                    for (int j = tid; j < tn; j += P) x.s_star[j] = gs[t0 + j];
-                    __syncthreads();
+        bool blocked = false;
+        if constexpr (sizeof(T) == 4) {
+            if (A >= 2 * P) {
+                sweep_blocked<4>(x, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                blocked = true;
+            } else if (A >= P) {
+                sweep_blocked<2>(x, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                blocked = true;
+            }
+        }
+        if (!blocked) {
+            int g = P / A;
+            g = g < 1 ? 1 : (g > 32 ? 32 : g);
+            g = 1 << (31 - __clz(g));  // power of two
+            const int groups = P / g;
+            const int lane = tid & (g - 1);
+            const int gid = tid / g;
+            for (int base = 0; base < A; base += groups) {
+                const int slot = base + gid;
+                const bool valid = slot < A;
+                const int key = valid ? (slot < A0 ? x.act[slot] : x.act[nr + slot - A0]) : 0;
+                const int d = key >= nr;
+                const C z = x.cur[key];
+                Acc<T> acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                const int cell = valid ? far_cell<T>(K, z.x, z.y) : -1;
+                if (valid && lane == 0) {
+                    *x.n_terms += (unsigned long long)(cell >= 0 ? K.tcells[cell].near_cnt : n);
+                    *x.n_far += cell >= 0 ? 1ull : 0ull;
                 }
-                if (valid) {
+                if (cell >= 0) cell_part<T>(x, cell, z.x, z.y, lane, g, acc);
+                for (int t0 = 0; t0 < n; t0 += TS) {
+                    const int tn = min(TS, n - t0);
+                    if (!x.resident) {
+                        __syncthreads();
+                        const typename CT<T>::Star* gs = (const typename CT<T>::Star*)K.stars;
+                        for (int j = tid; j < tn; j += P) x.s_star[j] = gs[t0 + j];
+                        __syncthreads();
+                    }
+                    if (valid && cell < 0) {
 #pragma unroll 4
-                    for (int j = lane; j < tn; j += g) acc_star(z.x, z.y, x.s_star[j], acc);
-                }
-            }
-            for (int t0 = 0; t0 < nr; t0 += TR) {
-                const int tn = min(TR, nr - t0);
-                __syncthreads();
-                for (int j = tid; j < tn; j += P) {
-                    if (a0) x.s_root[j] = x.cur[t0 + j];
-                    if (a1) x.s_root[TR + j] = x.cur[nr + t0 + j];
-                }
-                __syncthreads();
-                if (valid) {
-                    const C* rr = x.s_root + d * TR;
-#pragma unroll 4
-                    for (int j = lane; j < tn; j += g) acc_root(z.x, z.y, rr[j], acc);
-                }
-            }
-            for (int off = g >> 1; off > 0; off >>= 1) {
-                acc.Cx += shfl_x(acc.Cx, off);
-                acc.Cy += shfl_x(acc.Cy, off);
-                acc.Ax += shfl_x(acc.Ax, off);
-                acc.Ay += shfl_x(acc.Ay, off);
-                acc.Bx += shfl_x(acc.Bx, off);
-                acc.By += shfl_x(acc.By, off);
-                acc.Dx += shfl_x(acc.Dx, off);
-                acc.Dy += shfl_x(acc.Dy, off);
-                acc.Am += shfl_x(acc.Am, off);
-            }
-            if (valid && lane == 0) {
-                const T cph = d ? cph1 : cph0, sph = d ? sph1 : sph0;
-                // F = gamma + A - (1 - kappa_s) e^{-i phi}
-                const T Fx = gam + acc.Ax - oms * cph;
-                const T Fy = acc.Ay + oms * sph;
-                C zn = z;
-                T ad = 0;
-                if (Fx != (T)0 || Fy != (T)0) {
-                    const T dFx = (T)-2 * acc.Bx, dFy = (T)-2 * acc.By;
-                    const T fden = Fx * Fx + Fy * Fy;
-                    const T qx = qdiv(dFx * Fx + dFy * Fy, fden);
-                    const T qy = qdiv(dFy * Fx - dFx * Fy, fden);
-                    const T px = qx + (T)2 * acc.Cx - acc.Dx;
-                    const T py = qy + (T)2 * acc.Cy - acc.Dy;
-                    const T pden = px * px + py * py;
-                    const T delx = qdiv(px, pden), dely = qdiv(-py, pden);
-                    zn.x = z.x - delx;
-                    zn.y = z.y - dely;
-                    ad = qsqrt(delx * delx + dely * dely);
-                }
-                const int its = x.it[key] + 1;
-                x.it[key] = its;
-                atomicMax(s_maxit, its);
-                bool done;
-                if (sizeof(T) == 4) {
-                    // FP32: freeze at the absolute tolerance or at the rounding floor of this
-                    // root: a few ulp of |z|, or the FP32 noise of F (~eps sum |m/d^2|)
-                    // divided by |F'|; or when the corrections stop shrinking within a few
-                    // times that floor.
-                    const T sc = (T)1 + qsqrt(z.x * z.x + z.y * z.y);
-                    const T fpa = (T)2 * qsqrt(acc.Bx * acc.Bx + acc.By * acc.By);
-                    const T noise = (T)(4.0 * FLT_EPSILON) * (acc.Am + fabs(gam) + oms);
-                    T tolz = fmax((T)K.tol_abs, (T)(8.0 * FLT_EPSILON) * sc);
-                    if (fpa > (T)0) tolz = fmax(tolz, (T)4 * noise * qdiv((T)1, fpa));
-                    // never looser than 64x the ulp floor: an iterate that runs away where F'
-                    // vanishes must not count as converged
-                    tolz = fmin(tolz, (T)(512.0 * FLT_EPSILON) * sc);
-                    done = !(ad >= tolz) ||
-                           (its >= 3 && ad > (T)0.25 * (T)x.dprev[key] && ad < (T)4 * tolz);
-                } else {
-                    done = !(ad >= (T)K.tol_abs);
-                    if (!done && K.mu_max > 0) {
-                        const T gx = gam + acc.Ax, gy = acc.Ay;
-                        const T detj = oms * oms - (gx * gx + gy * gy);
-                        done = fabs((double)detj) * K.mu_max < 1.0;
+                        for (int j = lane; j < tn; j += g) acc_star(z.x, z.y, x.s_star[j], acc);
                     }
                 }
-                x.dprev[key] = (float)ad;
-                if (done) x.conv[key] = 1;
-                x.nxt[key] = zn;
+                for (int t0 = 0; t0 < nr; t0 += TR) {
+                    const int tn = min(TR, nr - t0);
+                    __syncthreads();
+                    for (int j = tid; j < tn; j += P) {
+                        if (a0) x.s_root[j] = x.cur[t0 + j];
+                        if (a1) x.s_root[TR + j] = x.cur[nr + t0 + j];
+                    }
+                    __syncthreads();
+                    if (valid) {
+                        const C* rr = x.s_root + d * TR;
+                        if constexpr (sizeof(T) == 4) {
+#pragma unroll 4
+                            for (int j = lane; j < tn; j += g) acc_root_f(z.x, z.y, rr[j].x, rr[j].y, acc.Dx, acc.Dy);
+                        } else {
+#pragma unroll 4
+                            for (int j = lane; j < tn; j += g) acc_root(z.x, z.y, rr[j], acc);
+                        }
+                    }
+                }
+                for (int off = g >> 1; off > 0; off >>= 1) {
+                    acc.Cx += shfl_x(acc.Cx, off);
+                    acc.Cy += shfl_x(acc.Cy, off);
+                    acc.Ax += shfl_x(acc.Ax, off);
+                    acc.Ay += shfl_x(acc.Ay, off);
+                    acc.Bx += shfl_x(acc.Bx, off);
+                    acc.By += shfl_x(acc.By, off);
+                    acc.Dx += shfl_x(acc.Dx, off);
+                    acc.Dy += shfl_x(acc.Dy, off);
+                    acc.Am += shfl_x(acc.Am, off);
+                }
+                if (valid && lane == 0) finish_root<T>(x, key, z, acc, d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
             }
         }
         __syncthreads();
         for (int i = tid; i < A; i += P) {
-            const int key = x.act[i];
+            const int key = i < A0 ? x.act[i] : x.act[nr + i - A0];
             x.cur[key] = x.nxt[key];
         }
     }
@@ -322,11 +529,12 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
 // row, then both directions row by row.  w: this CTA's Jacobi scratch.
 template <typename T>
 __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, unsigned char* smem,
-                                             int* s_count_p, int* s_maxit_p) {
+                                             int* s_count_p, int* s_maxit_p, unsigned long long* n_terms_p,
+                                             unsigned long long* n_far_p) {
     using C = typename CT<T>::C;
     using Star = typename CT<T>::Star;
     constexpr int TS = CT<T>::TS;
-    int& s_count = *s_count_p;
+    int* s_count = s_count_p;  // [2]: active roots per direction
     int& s_maxit = *s_maxit_p;
     const int tid = threadIdx.x, P = blockDim.x;
     const int nr = K.nr, n = K.n;
@@ -345,13 +553,15 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     x.it = x.conv + 2 * nr;
     x.act = x.it + 2 * nr;
     x.resident = n <= TS;
+    x.n_terms = n_terms_p;
+    x.n_far = n_far_p;
     const Star* gs = (const Star*)K.stars;
     if (x.resident)
         for (int j = tid; j < n; j += P) x.s_star[j] = gs[j];
 
     seed_guesses<T>(x, 0);
     for (int k = tid; k < nr; k += P) x.conv[nr + k] = 1;
-    solve_rows<T>(x, true, false, c, -1, K.max_iter_cold, true, true, &s_count, &s_maxit);
+    solve_rows<T>(x, true, false, c, -1, K.max_iter_cold, true, true, s_count, &s_maxit);
 
     C* zrows = (C*)K.zrows;
     C* seam = (C*)K.seam;
@@ -390,7 +600,7 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             x.it[k] = 0;
             x.dprev[k] = FLT_MAX;
         }
-        const int bad = solve_rows<T>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, &s_count, &s_maxit);
+        const int bad = solve_rows<T>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit);
         if (bad) {
             // A warm start that does not settle (e.g. a phase step so large that the previous
             // row sits on a symmetric, non-converging configuration) restarts that row from
@@ -398,7 +608,7 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             __syncthreads();
             if (bad & 1) seed_guesses<T>(x, 0);
             if (bad & 2) seed_guesses<T>(x, 1);
-            solve_rows<T>(x, bad & 1, (bad & 2) != 0, r0, r1, K.max_iter_cold, true, true, &s_count, &s_maxit);
+            solve_rows<T>(x, bad & 1, (bad & 2) != 0, r0, r1, K.max_iter_cold, true, true, s_count, &s_maxit);
         }
         if (a0) {
             C* o = dst(r0);
@@ -421,9 +631,19 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
 template <typename T>
 __global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_count, s_maxit;
+    __shared__ int s_count[2], s_maxit;
     if (threadIdx.x == 0) s_maxit = 0;
-    run_subchain<T>(K, blockIdx.x, K.work + (size_t)blockIdx.x * K.work_stride, smem, &s_count, &s_maxit);
+    unsigned long long n_terms = 0, n_far = 0;
+    run_subchain<T>(K, blockIdx.x, K.work + (size_t)blockIdx.x * K.work_stride, smem, s_count, &s_maxit, &n_terms,
+                    &n_far);
+    for (int off = 16; off > 0; off >>= 1) {
+        n_terms += __shfl_xor_sync(0xffffffffu, n_terms, off);
+        n_far += __shfl_xor_sync(0xffffffffu, n_far, off);
+    }
+    if ((threadIdx.x & 31) == 0 && (n_terms || n_far)) {
+        atomicAdd(&K.rep->star_terms, n_terms);
+        atomicAdd(&K.rep->far_evals, n_far);
+    }
     if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
 }
 
@@ -432,7 +652,8 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
 template <typename T>
 __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_count, s_maxit, s_item;
+    __shared__ int s_count[2], s_maxit, s_item;
+    unsigned long long n_terms = 0, n_far = 0;
     char* w = (char*)B.work + (size_t)blockIdx.x * B.work_stride;
     for (;;) {
         __syncthreads();
@@ -462,8 +683,22 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
         K.max_iter_cold = B.max_iter_cold;
         K.max_iter_warm = B.max_iter_warm;
         K.predictor = B.predictor;
+        K.tfmm = t.tfmm;
+        K.tcells = t.tcells;
+        K.tnear = t.tnear;
+        K.tcoeff = t.tcoeff;
         if (threadIdx.x == 0) s_maxit = 0;
-        run_subchain<T>(K, fs.y, w, smem, &s_count, &s_maxit);
+        n_terms = 0;
+        n_far = 0;
+        run_subchain<T>(K, fs.y, w, smem, s_count, &s_maxit, &n_terms, &n_far);
+        for (int off = 16; off > 0; off >>= 1) {
+            n_terms += __shfl_xor_sync(0xffffffffu, n_terms, off);
+            n_far += __shfl_xor_sync(0xffffffffu, n_far, off);
+        }
+        if ((threadIdx.x & 31) == 0 && (n_terms || n_far)) {
+            atomicAdd(&K.rep->star_terms, n_terms);
+            atomicAdd(&K.rep->far_evals, n_far);
+        }
         if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
     }
 }
@@ -533,6 +768,11 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
     K.max_iter_cold = a.max_iter_cold;
     K.max_iter_warm = a.max_iter_warm;
     K.predictor = a.predictor;
+    K.tfmm = a.f->tfmm;
+    if (fp64) K.tfmm.ok = 0;
+    K.tcells = a.f->tcells;
+    K.tnear = a.f->tnear;
+    K.tcoeff = a.f->tcoeff;
     const size_t smem = tracer_smem_bytes(fp64);
     cudaError_t e;
     if (fp64) {
@@ -797,6 +1037,95 @@ __global__ void phase_batch_kernel(const TraceTask* tasks, int count) {
 cudaError_t launch_phase_batch(const TraceTask* tasks, int count, int64_t max_m, cudaStream_t st) {
     dim3 grid((unsigned)((max_m + 1 + 255) / 256), (unsigned)count);
     phase_batch_kernel<<<grid, 256, 0, st>>>(tasks, count);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Tracer far-field tables (built once per field): one warp per cell.  Near stars (the 5x5
+// block of cells around it) are listed in star order; every other star (at least 2.5
+// cells from the centre, while a root in the cell is within 0.71 cells) adds to the FP32
+// local expansions U_k = -sum 1/(z_i - c)^(k+1) and L_k = -sum m_i/(z_i - c)^(k+1).
+// ----------------------------------------------------------------------------------
+__global__ void tracer_far_field_kernel(const float4* s32, int n, TfmmParams P, TCell* cells, int* near,
+                                        float4* coeff) {
+    const int lane = threadIdx.x & 31;
+    const int cell = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (cell >= P.nbx * P.nby) return;  // whole warp
+    const int bx = cell % P.nbx, by = cell / P.nbx;
+    const float cx = P.x0 + ((float)bx + 0.5f) * P.b, cy = P.y0 + ((float)by + 0.5f) * P.b;
+    float ux[TFMM_P], uy[TFMM_P], lx[TFMM_P], ly[TFMM_P];
+#pragma unroll
+    for (int k = 0; k < TFMM_P; k++) ux[k] = uy[k] = lx[k] = ly[k] = 0.f;
+    float r2 = 0.f;
+    int cnt = 0;
+    bool over = false;
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        const int j = j0 + lane;
+        bool nr_ = false;
+        float4 sp = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (j < n) {
+            sp = s32[j];
+            const int sx = (int)fminf(fmaxf(floorf((sp.x - P.x0) * P.inv_b), -1e6f), 1e6f);
+            const int sy = (int)fminf(fmaxf(floorf((sp.y - P.y0) * P.inv_b), -1e6f), 1e6f);
+            nr_ = abs(sx - bx) <= 2 && abs(sy - by) <= 2;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, nr_);
+        if (nr_) {
+            const int q = cnt + __popc(bal & ((1u << lane) - 1u));
+            if (q < TFMM_NEAR_MAX) near[(size_t)cell * TFMM_NEAR_MAX + q] = j;
+        }
+        cnt += __popc(bal);
+        if (j < n && !nr_) {
+            const float dx = sp.x - cx, dy = sp.y - cy;
+            const float d2 = dx * dx + dy * dy;
+            const float inv = 1.0f / d2;
+            const float vx = dx * inv, vy = -dy * inv;  // 1/(z_i - c)
+            float wx = vx, wy = vy;
+            r2 += sp.z * inv;
+#pragma unroll
+            for (int k = 0; k < TFMM_P; k++) {
+                ux[k] -= wx;
+                uy[k] -= wy;
+                lx[k] = fmaf(-sp.z, wx, lx[k]);
+                ly[k] = fmaf(-sp.z, wy, ly[k]);
+                const float nx = wx * vx - wy * vy, ny = wx * vy + wy * vx;
+                wx = nx;
+                wy = ny;
+            }
+        }
+    }
+    over = cnt > TFMM_NEAR_MAX;
+#pragma unroll
+    for (int k = 0; k < TFMM_P; k++) {
+        for (int off = 16; off > 0; off >>= 1) {
+            ux[k] += __shfl_xor_sync(0xffffffffu, ux[k], off);
+            uy[k] += __shfl_xor_sync(0xffffffffu, uy[k], off);
+            lx[k] += __shfl_xor_sync(0xffffffffu, lx[k], off);
+            ly[k] += __shfl_xor_sync(0xffffffffu, ly[k], off);
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, off);
+    if (lane < TFMM_P) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < TFMM_P; k++)
+            if (k == lane) v = make_float4(ux[k], uy[k], lx[k], ly[k]);
+        coeff[(size_t)cell * TFMM_P + lane] = v;
+    }
+    if (lane == 0) {
+        TCell c;
+        c.cx = cx;
+        c.cy = cy;
+        c.near_cnt = over ? -1 : cnt;
+        c.far_m_d2 = r2;
+        cells[cell] = c;
+    }
+}
+
+cudaError_t launch_tracer_far_field(const float4* s32, int n, const TfmmParams& P, TCell* cells, int* near,
+                                    float4* coeff, cudaStream_t st) {
+    const int64_t threads = (int64_t)P.nbx * P.nby * 32;
+    tracer_far_field_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(s32, n, P, cells, near, coeff);
     return cudaGetLastError();
 }
 

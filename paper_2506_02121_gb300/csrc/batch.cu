@@ -262,6 +262,10 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         const FieldDev& fd = b->dev[f];
         TraceTask& t = tasks[f];
         t.stars = fd.star32;
+        t.tfmm = fd.tfmm;
+        t.tcells = fd.tcells;
+        t.tnear = fd.tnear;
+        t.tcoeff = fd.tcoeff;
         t.n = (int)fd.n;
         t.nr = (int)b->nr[f];
         t.kappa_s = fd.kappa_s;
@@ -410,6 +414,8 @@ int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
         q.max_err_est = r[f].max_err_est;
         q.rescued_points = (int64_t)r[f].rescued_points;
         q.jumped = (int64_t)r[f].jumped;
+        q.star_terms = (int64_t)r[f].star_terms;
+        q.far_evals = (int64_t)r[f].far_evals;
         if (per_field) per_field[f] = q;
         tot.rows += q.rows;
         tot.n_roots += q.n_roots;
@@ -425,6 +431,8 @@ int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
         tot.max_err_est = std::max(tot.max_err_est, q.max_err_est);
         tot.rescued_points += q.rescued_points;
         tot.jumped += q.jumped;
+        tot.star_terms += q.star_terms;
+        tot.far_evals += q.far_evals;
         bad = bad || q.unconverged || q.uncertified;
     }
     tot.trace_ms = t01;

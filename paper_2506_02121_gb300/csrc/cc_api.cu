@@ -200,7 +200,7 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
         unit = unit && hm[i] == 1.0;
     }
     std::vector<float4> s32(n), sdp(n);
-    std::vector<float2> sdm(n);
+    std::vector<float2> sdm(n), stf(n);
     std::vector<StarD> s64(n);
     auto split = [](double v, float& hi, float& lo) {
         hi = (float)v;
@@ -215,6 +215,7 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
         split(hm[i], e, g);
         sdp[i] = make_float4(a, b, c, d);
         sdm[i] = make_float2(e, g);
+        stf[i] = make_float2((float)(hx[i] - (double)a - (double)b), (float)(hy[i] - (double)c - (double)d));
     }
     // far-field cell: about 6 stars in a 5x5 block of cells at the mean star density of the
     // field's bounding disc
@@ -243,6 +244,7 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
     e = e ? e : cudaMalloc(&f->dev.star64, sizeof(StarD) * n);
     e = e ? e : cudaMalloc(&f->dev.star_dfp, sizeof(float4) * n);
     e = e ? e : cudaMalloc(&f->dev.star_dfm, sizeof(float2) * n);
+    e = e ? e : cudaMalloc(&f->dev.star_tf, sizeof(float2) * n);
     e = e ? e : cudaMalloc(&f->d_rep, sizeof(DevReport));
     e = e ? e : cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming);
     for (int i = 0; i < 4; i++) e = e ? e : cudaEventCreate(&f->ev[i]);
@@ -254,10 +256,45 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
     e = e ? e : cudaMemcpy(f->dev.star64, s64.data(), sizeof(StarD) * n, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(f->dev.star_dfp, sdp.data(), sizeof(float4) * n, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(f->dev.star_dfm, sdm.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
+    e = e ? e : cudaMemcpy(f->dev.star_tf, stf.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemset(f->d_rep, 0, sizeof(DevReport));
     if (e != cudaSuccess) {
         cc_field_destroy(f);
         return cuda_fail(e, "cc_field_create upload");
+    }
+    // tracer far-field tables: cells of the polish cell size over the stars' bounding box
+    // plus three cells on every side (roots outside sum every star directly)
+    f->dev.tfmm.ok = 0;
+    if (o.far_field && n >= FMM_MIN_STARS) {
+        float xmn = s32[0].x, xmx = s32[0].x, ymn = s32[0].y, ymx = s32[0].y;
+        for (int64_t i = 1; i < n; i++) {
+            xmn = std::min(xmn, s32[i].x);
+            xmx = std::max(xmx, s32[i].x);
+            ymn = std::min(ymn, s32[i].y);
+            ymx = std::max(ymx, s32[i].y);
+        }
+        float b = fmm_cell > 0.f ? fmm_cell : 1.0f;
+        const float span = std::max(xmx - xmn, ymx - ymn);
+        if (span / b + 8.0f > 512.0f) b = span / 504.0f;
+        TfmmParams P;
+        P.b = b;
+        P.inv_b = 1.0f / b;
+        P.x0 = xmn - 3.0f * b;
+        P.y0 = ymn - 3.0f * b;
+        P.nbx = (int)std::ceil((xmx - P.x0) * P.inv_b) + 4;
+        P.nby = (int)std::ceil((ymx - P.y0) * P.inv_b) + 4;
+        P.ok = 1;
+        const size_t cells = (size_t)P.nbx * P.nby;
+        e = cudaMalloc(&f->dev.tcells, sizeof(TCell) * cells);
+        e = e ? e : cudaMalloc(&f->dev.tnear, sizeof(int) * cells * TFMM_NEAR_MAX);
+        e = e ? e : cudaMalloc(&f->dev.tcoeff, sizeof(float4) * cells * TFMM_P);
+        e = e ? e : launch_tracer_far_field(f->dev.star32, (int)n, P, f->dev.tcells, f->dev.tnear, f->dev.tcoeff, 0);
+        e = e ? e : cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            cc_field_destroy(f);
+            return cuda_fail(e, "cc_field_create far-field tables");
+        }
+        f->dev.tfmm = P;
     }
     *out = f;
     return CC_OK;
@@ -270,7 +307,11 @@ int cc_field_destroy(cc_field* f) {
     cudaFree(f->dev.star64);
     cudaFree(f->dev.star_dfp);
     cudaFree(f->dev.star_dfm);
+    cudaFree(f->dev.star_tf);
     cudaFree(f->d_rep);
+    cudaFree(f->dev.tcells);
+    cudaFree(f->dev.tnear);
+    cudaFree(f->dev.tcoeff);
     if (f->done) cudaEventDestroy(f->done);
     for (int i = 0; i < 4; i++)
         if (f->ev[i]) cudaEventDestroy(f->ev[i]);
@@ -427,6 +468,8 @@ int cc_field_report(cc_field* f, cc_report* out) {
     out->max_err_est = r.max_err_est;
     out->rescued_points = (int64_t)r.rescued_points;
     out->jumped = (int64_t)r.jumped;
+    out->star_terms = (int64_t)r.star_terms;
+    out->far_evals = (int64_t)r.far_evals;
     CC_CUDA(cudaEventElapsedTime(&out->trace_ms, f->ev[0], f->ev[1]), "stage time");
     CC_CUDA(cudaEventElapsedTime(&out->join_ms, f->ev[1], f->ev[2]), "stage time");
     CC_CUDA(cudaEventElapsedTime(&out->polish_ms, f->ev[2], f->ev[3]), "stage time");

@@ -101,6 +101,30 @@ __device__ __forceinline__ df df_rcp(df a) {
 
 __device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
 
+// A coordinate as three floats h + m + l (~72-bit significand) and the difference of two
+// such coordinates as a double-float: the pieces are subtracted with error-free sums, so
+// the difference of two close points keeps its full relative precision (the caustic
+// point of a root next to a star depends on that difference at 1 / |d|^2).
+struct tf {
+    float h, m, l;
+};
+
+__device__ __forceinline__ tf tf_from_double(double x) {
+    const float h = __double2float_rn(x);
+    const double r = x - (double)h;
+    const float m = __double2float_rn(r);
+    const float l = __double2float_rn(r - (double)m);
+    return tf{h, m, l};
+}
+
+__device__ __forceinline__ df tf_sub(const tf& a, float bh, float bm, float bl) {
+    const df s = two_sum(a.h, -bh);
+    const df t = two_sum(a.m, -bm);
+    const df u = two_sum(s.hi, t.hi);
+    const float lo = __fadd_rn(__fadd_rn(s.lo, t.lo), __fadd_rn(u.lo, __fsub_rn(a.l, bl)));
+    return fast_two_sum(u.hi, lo);
+}
+
 __device__ __forceinline__ df df_from_double(double x) {
     float h = __double2float_rn(x);
     float l = __double2float_rn(x - (double)h);
@@ -119,6 +143,8 @@ struct DevReport {
     unsigned long long seam_ambiguous;
     unsigned long long jumped;   // polish moved a root further than the tracer's scale
     unsigned long long rescued_points;  // uncertified points re-solved in FP64 (converged)
+    unsigned long long star_terms;      // tracer: star terms summed directly
+    unsigned long long far_evals;       // tracer: root updates that used a cell expansion
     int max_iter_row;
     int timeout;
     double max_err_est;          // stored as the bit pattern of a non-negative double

@@ -14,6 +14,22 @@ struct __align__(32) StarD {
     double x, y, z, w;  // position (x, y), mass z, padding w
 };
 
+// Tracer far-field tables of a field (built once in cc_field_create): a grid of cells
+// over the stars (plus a margin); per cell the stars of its 5x5 block ("near") and FP32
+// local expansions of the other stars' sums sum 1/(z - z_i) and sum m_i/(z - z_i).
+constexpr int TFMM_P = 14;        // expansion terms (rho <= 0.29: rho^14 ~ 3e-8)
+constexpr int TFMM_NEAR_MAX = 48;  // near stars stored per cell (more: the cell sums directly)
+struct TfmmParams {
+    float x0, y0, b, inv_b;
+    int nbx, nby;
+    int ok;
+};
+struct TCell {
+    float cx, cy;     // centre
+    int near_cnt;     // -1: sum every star directly
+    float far_m_d2;   // sum_far m/|z_i - c|^2 (scale of the far-field rounding noise)
+};
+
 // Device-side copy of a field's stars in the layouts the kernels read.
 struct FieldDev {
     int64_t n;
@@ -24,7 +40,15 @@ struct FieldDev {
     StarD* star64;    // FP64
     float4* star_dfp; // (x_hi, x_lo, y_hi, y_lo) double-float positions
     float2* star_dfm; // (m_hi, m_lo)
+    float2* star_tf;  // (x_l, y_l): third float of the positions (x = x_hi + x_lo + x_l)
+    // tracer far field (tfmm.ok == 0: none)
+    TfmmParams tfmm;
+    TCell* tcells;    // nbx * nby
+    int* tnear;       // nbx * nby * TFMM_NEAR_MAX star indices
+    float4* tcoeff;   // nbx * nby * TFMM_P: (U_k re, U_k im, L_k re, L_k im)
 };
+cudaError_t launch_tracer_far_field(const float4* s32, int n, const TfmmParams& P, TCell* cells, int* near,
+                                    float4* coeff, cudaStream_t st);
 
 // Tracing (Aberth) launch arguments shared by the FP32 and FP64 tracers.
 struct TraceArgs {
@@ -46,6 +70,10 @@ struct TraceArgs {
 // One field of a batched launch (device table entry).
 struct TraceTask {
     const void* stars;     // FP32 star records
+    TfmmParams tfmm;
+    const TCell* tcells;
+    const int* tnear;
+    const float4* tcoeff;
     int n, nr;
     double kappa_s, gamma;
     int64_t m;

@@ -26,6 +26,7 @@ constexpr int TSB = 2048;  // stars per shared-memory tile
 struct PolishK {
     const float4* dfp;
     const float2* dfm;
+    const float2* dtf;
     const StarD* s64;
     int n;
     int64_t nr, m, points;
@@ -57,10 +58,10 @@ struct Sums {
 // One star in double-float.  d = z - z_i; r2 = |d|^2; inv = 1/r2; q = m inv;
 // m/d = q conj(d); m/d^2 = q inv conj(d)^2 with conj(d)^2 = (dx^2 - dy^2, -2 dx dy).
 template <bool UNIT>
-__device__ __forceinline__ void star_df(const df& zx, const df& zy, const float4 p, const float2 mm,
+__device__ __forceinline__ void star_df(const tf& zx, const tf& zy, const float4 p, const float2 p3, const float2 mm,
                                         Sums& s) {
-    const df dx = df_sub(zx, df{p.x, p.y});
-    const df dy = df_sub(zy, df{p.z, p.w});
+    const df dx = tf_sub(zx, p.x, p.y, p3.x);
+    const df dy = tf_sub(zy, p.z, p.w, p3.y);
     const df dx2 = df_sqr(dx), dy2 = df_sqr(dy);
     const df r2 = df_add(dx2, dy2);
     const df inv = df_rcp(r2);
@@ -185,6 +186,7 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
                                             unsigned long long* s_passes_p) {
     float4* sp = (float4*)smem;
     float2* sm = (float2*)(smem + TSB * sizeof(float4));
+    float2* st3 = (float2*)(smem + TSB * (sizeof(float4) + sizeof(float2)));
     StarD* sd = (StarD*)smem;
     unsigned long long& s_passes = *s_passes_p;
     const int tid = threadIdx.x;
@@ -216,6 +218,7 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
             for (int j = tid; j < K.n; j += PB_THREADS) {
                 sp[j] = K.dfp[j];
                 sm[j] = K.dfm[j];
+                st3[j] = K.dtf[j];
             }
         }
     }
@@ -244,7 +247,7 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
             Sums s;
             s.S1x = s.S1y = s.S2x = s.S2y = df{0.f, 0.f};
             s.s3x = s.s3y = s.s4x = s.s4y = s.a3 = 0.f;
-            const df zxd = df_from_double(zx), zyd = df_from_double(zy);
+            const tf zxd = tf_from_double(zx), zyd = tf_from_double(zy);
             for (int t0 = 0; t0 < K.n; t0 += TSB) {
                 const int tn = min(TSB, K.n - t0);
                 if (!resident) {
@@ -252,12 +255,13 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
                     for (int j = tid; j < tn; j += PB_THREADS) {
                         sp[j] = K.dfp[t0 + j];
                         sm[j] = K.dfm[t0 + j];
+                        st3[j] = K.dtf[t0 + j];
                     }
                     __syncthreads();
                 }
                 if (need) {
 #pragma unroll 2
-                    for (int j = 0; j < tn; j++) star_df<UNIT>(zxd, zyd, sp[j], sm[j], s);
+                    for (int j = 0; j < tn; j++) star_df<UNIT>(zxd, zyd, sp[j], st3[j], sm[j], s);
                 }
             }
             double est = 0.0;
@@ -303,6 +307,7 @@ static PolishK make_polish_k(const PolishArgs& a) {
     PolishK K;
     K.dfp = a.f->star_dfp;
     K.dfm = a.f->star_dfm;
+    K.dtf = a.f->star_tf;
     K.s64 = a.f->star64;
     K.n = (int)a.f->n;
     K.nr = a.nr;
@@ -342,7 +347,7 @@ void polish_task_fill(const PolishArgs& a, int64_t first_block, void* out) {
 
 cudaError_t launch_polish_batch(const void* tasks, int count, int64_t total_blocks, cudaStream_t st) {
     if (total_blocks <= 0) return cudaSuccess;
-    const size_t smem = TSB * (sizeof(float4) + sizeof(float2));
+    const size_t smem = TSB * (sizeof(float4) + 2 * sizeof(float2));
     cudaError_t e = cudaFuncSetAttribute(polish_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     polish_batch_kernel<<<(unsigned)total_blocks, PB_THREADS, smem, st>>>((const PolishK*)tasks, count);
@@ -352,7 +357,7 @@ cudaError_t launch_polish_batch(const void* tasks, int count, int64_t total_bloc
 cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st) {
     PolishK K = make_polish_k(a);
     const unsigned blocks = (unsigned)((K.points + PB_THREADS - 1) / PB_THREADS);
-    const size_t smem_df = TSB * (sizeof(float4) + sizeof(float2));
+    const size_t smem_df = TSB * (sizeof(float4) + 2 * sizeof(float2));
     const size_t smem_d = TSB * sizeof(StarD);
     cudaError_t e;
 #define CC_LAUNCH_POLISH(U, D, SM)                                                                     \
@@ -691,13 +696,13 @@ __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const
         Sums sm;
         sm.S1x = sm.S1y = sm.S2x = sm.S2y = df{0.f, 0.f};
         sm.s3x = sm.s3y = sm.s4x = sm.s4y = sm.a3 = 0.f;
-        const df zxd = df_from_double(zx), zyd = df_from_double(zy);
+        const tf zxt = tf_from_double(zx), zyt = tf_from_double(zy);
         for (int q = 0; q < bi.near_cnt; q++) {
             const int j = pool[bi.near_off + q];
-            star_df<UNIT>(zxd, zyd, K.dfp[j], K.dfm[j], sm);
+            star_df<UNIT>(zxt, zyt, K.dfp[j], K.dtf[j], K.dfm[j], sm);
         }
         // far field: Horner with derivatives in t = z - c
-        const df tx = df_sub(zxd, df{bi.c.x, bi.c.y}), ty = df_sub(zyd, df{bi.c.z, bi.c.w});
+        const df tx = tf_sub(zxt, bi.c.x, bi.c.y, 0.f), ty = tf_sub(zyt, bi.c.z, bi.c.w, 0.f);
         const float4 top = L[FMM_P - 1];
         df b0x = df{top.x, top.y}, b0y = df{top.z, top.w};
         df b1x = df{0.f, 0.f}, b1y = df{0.f, 0.f};
@@ -837,6 +842,7 @@ cudaError_t launch_finalize_fp64(const FinalizeArgs& a, cudaStream_t st) {
 struct MapK {
     const float4* dfp;
     const float2* dfm;
+    const float2* dtf;
     const StarD* s64;
     int n;
     int64_t count;
@@ -850,6 +856,7 @@ __global__ void __launch_bounds__(PB_THREADS) map_kernel(MapK K) {
     extern __shared__ __align__(16) unsigned char smem[];
     float4* sp = (float4*)smem;
     float2* sm = (float2*)(smem + TSB * sizeof(float4));
+    float2* st3 = (float2*)(smem + TSB * (sizeof(float4) + sizeof(float2)));
     StarD* sd = (StarD*)smem;
     const int tid = threadIdx.x;
     const int64_t p = blockIdx.x * (int64_t)PB_THREADS + tid;
@@ -857,7 +864,7 @@ __global__ void __launch_bounds__(PB_THREADS) map_kernel(MapK K) {
     const double2 z = valid ? K.z[p] : make_double2(0.0, 0.0);
     double S1x = 0.0, S1y = 0.0;
     df ax = df{0.f, 0.f}, ay = df{0.f, 0.f};
-    const df zx = df_from_double(z.x), zy = df_from_double(z.y);
+    const tf zx = tf_from_double(z.x), zy = tf_from_double(z.y);
     for (int t0 = 0; t0 < K.n; t0 += TSB) {
         const int tn = min(TSB, K.n - t0);
         __syncthreads();
@@ -867,6 +874,7 @@ __global__ void __launch_bounds__(PB_THREADS) map_kernel(MapK K) {
             } else {
                 sp[j] = K.dfp[t0 + j];
                 sm[j] = K.dfm[t0 + j];
+                st3[j] = K.dtf[t0 + j];
             }
         }
         __syncthreads();
@@ -880,8 +888,9 @@ __global__ void __launch_bounds__(PB_THREADS) map_kernel(MapK K) {
                 S1y = fma(-q, dy, S1y);
             } else {
                 const float4 pp = sp[j];
-                const df dx = df_sub(zx, df{pp.x, pp.y});
-                const df dy = df_sub(zy, df{pp.z, pp.w});
+                const float2 p3 = st3[j];
+                const df dx = tf_sub(zx, pp.x, pp.y, p3.x);
+                const df dy = tf_sub(zy, pp.z, pp.w, p3.y);
                 const df inv = df_rcp(df_add(df_sqr(dx), df_sqr(dy)));
                 const df q = UNIT ? inv : df_mul(df{sm[j].x, sm[j].y}, inv);
                 ax = df_add(ax, df_mul(q, dx));
@@ -904,6 +913,7 @@ cudaError_t launch_map_caustics(const FieldDev& f, const double2* z, int64_t cou
     MapK K;
     K.dfp = f.star_dfp;
     K.dfm = f.star_dfm;
+    K.dtf = f.star_tf;
     K.s64 = f.star64;
     K.n = (int)f.n;
     K.count = count;
@@ -912,7 +922,7 @@ cudaError_t launch_map_caustics(const FieldDev& f, const double2* z, int64_t cou
     K.z = z;
     K.w = w;
     const unsigned blocks = (unsigned)((count + PB_THREADS - 1) / PB_THREADS);
-    const size_t smem_df = TSB * (sizeof(float4) + sizeof(float2));
+    const size_t smem_df = TSB * (sizeof(float4) + 2 * sizeof(float2));
     const size_t smem_d = TSB * sizeof(StarD);
     cudaError_t e;
 #define CC_LAUNCH_MAP(U, D, SM)                                                                       \

@@ -348,8 +348,38 @@ __global__ void __launch_bounds__(32) edt_row_smem_kernel(const int32_t* g, int 
     const int r = blockIdx.x;
     const int lane = threadIdx.x;
     const int32_t* gr = g + (int64_t)r * W;
-    for (int q = lane; q < W; q += 32) f[q] = gr[q];
+    long long extent = 0;  // sum over pixels of the window a search would scan
+    for (int q = lane; q < W; q += 32) {
+        const int32_t v = gr[q];
+        f[q] = v;
+        extent += v < W ? v : W;
+    }
+    for (int off = 16; off > 0; off >>= 1) extent += __shfl_xor_sync(0xffffffffu, extent, off);
     __syncwarp();
+    double* out_row = d_out + (int64_t)r * W;
+    if (extent <= 200LL * W) {
+        // Windowed search, all lanes: the nearest feature of pixel i lies in a column q with
+        // |i - q| <= g(i) (q = i itself gives g(i)^2), so scan outwards until d^2 >= best.
+        for (int i = lane; i < W; i += 32) {
+            const long long fi = f[i];
+            long long best = fi < DIST_INF ? fi * fi : -1;
+            for (int d = 1;; d++) {
+                const long long dd = (long long)d * d;
+                if (best >= 0 && dd >= best) break;
+                if (i - d < 0 && i + d >= W) break;
+                if (i - d >= 0) {
+                    const long long v = f[i - d];
+                    if (v < DIST_INF && (best < 0 || dd + v * v < best)) best = dd + v * v;
+                }
+                if (i + d < W) {
+                    const long long v = f[i + d];
+                    if (v < DIST_INF && (best < 0 || dd + v * v < best)) best = dd + v * v;
+                }
+            }
+            out_row[i] = best < 0 ? __longlong_as_double(0x7ff0000000000000LL) : pixel * sqrt((double)best);
+        }
+        return;
+    }
     if (lane == 0) {
         int k = -1;
         for (int q = 0; q < W; q++) {

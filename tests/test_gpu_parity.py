@@ -226,8 +226,11 @@ def test_far_field_polish_matches_oracle_and_direct(n, msteps, ks, g):
     assert st == cc.CC_OK and rep["uncertified"] == 0, rep
     zd, wd, _, st2, rep2 = _solve(f.x, f.y, f.m, ks, g, msteps, far_field=0)
     assert st2 == cc.CC_OK
-    # each side is certified to 1e-10 (tol_cert), so they agree to twice that plus rounding
-    assert np.abs(zf - zd).max() < 3e-10 and np.abs(wf - wd).max() < 3e-10
+    # each side is certified to 1e-10 (tol_cert), so the root sets agree to twice that plus
+    # rounding (the column labelling may differ: chains follow the tracer's own trajectory)
+    worst, pairs = compare_chain(zf, zd, 3e-10)
+    for j, idx in enumerate(pairs):
+        assert np.abs(wf[j] - wd[j][idx]).max() < 3e-10
     rows = [0, msteps // 3, msteps // 2, msteps]
     for j in rows:
         zo, left = oracle.solve_row(f.x, f.y, f.m, ks, g, oracle.phi(j, msteps))
