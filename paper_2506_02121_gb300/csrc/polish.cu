@@ -504,10 +504,14 @@ __global__ void fmm_occupy_kernel(const float2* z, int64_t npts, FmmParams* P, u
     if (p >= npts || !P->ok) return;
     const float2 v = z[p];
     const int cx = fmm_cell(v.x, P->x0, P->inv_b), cy = fmm_cell(v.y, P->y0, P->inv_b);
-    if (cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby)
-        occ[(int64_t)cy * P->nbx + cx] = 1;
-    else
+    if (cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby) {
+        // most points fall in cells already marked: test first, so that each cell takes a
+        // handful of stores instead of one per point (a stale 0 only repeats a store)
+        uint8_t* o = occ + (int64_t)cy * P->nbx + cx;
+        if (*o == 0) *o = 1;
+    } else {
         P->ok = 0;
+    }
 }
 
 __global__ void fmm_slot_kernel(FmmParams* P, const uint8_t* occ, int* slot, int2* boxlist) {

@@ -334,88 +334,176 @@ __device__ __forceinline__ long long edt_key(const int32_t* f, int q) {
     return (long long)f[q] * f[q] + (long long)q * q;
 }
 
-// Row pass, one warp per row: the row's g values and the envelope stack live in shared
-// memory; lane 0 builds the lower envelope of the parabolas (i - q)^2 + g[q]^2 (exact
-// integer comparisons of the intersection abscissae), then every lane finds the owning
-// parabola of its pixels by binary search over the envelope and writes the distance.
-constexpr int EDT_ROW_SMEM_MAX_W = 12288;
-__global__ void __launch_bounds__(32) edt_row_smem_kernel(const int32_t* g, int W, int H, double pixel,
-                                                          double* d_out) {
-    extern __shared__ int32_t sh[];
-    int32_t* f = sh;       // [W]
-    int32_t* v = sh + W;   // [W]
-    __shared__ int s_k;
-    const int r = blockIdx.x;
-    const int lane = threadIdx.x;
+// Row pass, one warp per row, exact integer arithmetic.  D(i) = min_q (i - q)^2 + g[q]^2 is
+// the lower envelope of the parabolas of the columns with a feature; its owners are the
+// vertices of the lower convex hull of the lifted points (q, q^2 + g[q]^2).  Lane l takes
+// the band of columns [l Bw, (l + 1) Bw) and builds the hull of its band with a stack; five
+// rounds of bridge merges join neighbouring bands (the hull of two column-separated sets
+// keeps a prefix of the left hull and a suffix of the right one, found by walking both
+// ends until neither end point can be dropped); then the warp fills the row 32 pixels at
+// a time, each lane walking the hull forward from the owner of the tile's first pixel.
+// Band position k of lane l is stored at [k * EDT_LS + l] (16-bit entries), so the lanes
+// of a warp stepping through their bands together never share a shared-memory bank word
+// they do not also share an address in.
+constexpr int EDT_BAND_MAX_W = 32768;
+constexpr int EDT_BAND_MAX_H = 65535;  // g < H fits 16 bits, 0xFFFF marks "no feature"
+constexpr int EDT_LS = 33;
+
+size_t edt_band_smem(int W) { return 2 * sizeof(uint16_t) * (size_t)((W + 31) / 32) * EDT_LS; }
+
+__device__ __forceinline__ long long edt_lift(int q, int gq) { return (long long)q * q + (long long)gq * gq; }
+
+// Site v (u < v < w in column order) is strictly below the chord u-w of the lifted points,
+// i.e. intersection(u, v) < intersection(v, w): its parabola alone is lowest somewhere.
+__device__ __forceinline__ bool edt_keep(int u, long long cu, int v, long long cv, int w, long long cw) {
+    return (cw - cv) * (long long)(v - u) > (cv - cu) * (long long)(w - v);
+}
+
+__global__ void __launch_bounds__(32) edt_row_band_kernel(const int32_t* g, int W, double pixel, double* d_out) {
+    extern __shared__ uint16_t edt_sh[];
+    __shared__ int s_lo[32], s_hi[32];
+    const int r = blockIdx.x, lane = threadIdx.x;
+    const int Bw = (W + 31) / 32;
+    uint16_t* gs = edt_sh;                          // g by (band position, lane)
+    uint16_t* st = edt_sh + (size_t)Bw * EDT_LS;    // hull stacks: band positions
     const int32_t* gr = g + (int64_t)r * W;
-    long long extent = 0;  // sum over pixels of the window a search would scan
-    for (int q = lane; q < W; q += 32) {
-        const int32_t v = gr[q];
-        f[q] = v;
-        extent += v < W ? v : W;
-    }
-    for (int off = 16; off > 0; off >>= 1) extent += __shfl_xor_sync(0xffffffffu, extent, off);
-    __syncwarp();
-    double* out_row = d_out + (int64_t)r * W;
-    if (extent <= 200LL * W) {
-        // Windowed search, all lanes: the nearest feature of pixel i lies in a column q with
-        // |i - q| <= g(i) (q = i itself gives g(i)^2), so scan outwards until d^2 >= best.
-        for (int i = lane; i < W; i += 32) {
-            const long long fi = f[i];
-            long long best = fi < DIST_INF ? fi * fi : -1;
-            for (int d = 1;; d++) {
-                const long long dd = (long long)d * d;
-                if (best >= 0 && dd >= best) break;
-                if (i - d < 0 && i + d >= W) break;
-                if (i - d >= 0) {
-                    const long long v = f[i - d];
-                    if (v < DIST_INF && (best < 0 || dd + v * v < best)) best = dd + v * v;
-                }
-                if (i + d < W) {
-                    const long long v = f[i + d];
-                    if (v < DIST_INF && (best < 0 || dd + v * v < best)) best = dd + v * v;
-                }
+    {
+        int l = lane / Bw, k = lane - l * Bw;  // column q = lane
+        for (int q = lane; q < W; q += 32) {
+            const int32_t v = gr[q];
+            gs[k * EDT_LS + l] = v >= 0xFFFF ? (uint16_t)0xFFFF : (uint16_t)v;
+            k += 32;
+            while (k >= Bw) {
+                k -= Bw;
+                l++;
             }
-            out_row[i] = best < 0 ? __longlong_as_double(0x7ff0000000000000LL) : pixel * sqrt((double)best);
         }
-        return;
-    }
-    if (lane == 0) {
-        int k = -1;
-        for (int q = 0; q < W; q++) {
-            if (f[q] >= DIST_INF) continue;
-            const long long fq = edt_key(f, q);
-            while (k >= 1) {
-                const int p = v[k], pp = v[k - 1];
-                const long long n1 = fq - edt_key(f, p), d1 = 2LL * (q - p);
-                const long long n2 = edt_key(f, p) - edt_key(f, pp), d2 = 2LL * (p - pp);
-                if (n1 * d2 <= n2 * d1) k--;
-                else break;
-            }
-            v[++k] = q;
-        }
-        s_k = k;
     }
     __syncwarp();
-    const int k = s_k;
+    auto site_g = [&](int l, int k) -> int { return gs[k * EDT_LS + l]; };
+    // 1. hull of the own band
+    const int a = lane * Bw;
+    const int bl = max(0, min(Bw, W - a));
+    int len = 0;
+    int ku = 0, kv = 0;             // band positions of the two top stack entries
+    long long cu = 0, cv = 0;       // and their lifted values
+    for (int k = 0; k < bl; k++) {
+        const int gq = site_g(lane, k);
+        if (gq == 0xFFFF) continue;
+        const long long cq = edt_lift(a + k, gq);
+        while (len >= 2 && !edt_keep(ku, cu, kv, cv, k, cq)) {
+            len--;
+            kv = ku;
+            cv = cu;
+            if (len >= 2) {
+                ku = st[(len - 2) * EDT_LS + lane];
+                cu = edt_lift(a + ku, site_g(lane, ku));
+            }
+        }
+        st[len * EDT_LS + lane] = (uint16_t)k;
+        len++;
+        ku = kv;
+        cu = cv;
+        kv = k;
+        cv = cq;
+    }
+    s_lo[lane] = 0;
+    s_hi[lane] = len;
+    __syncwarp();
+    // 2. bridge merges of the hulls of lane groups [b, b + h) and [b + h, b + 2h)
+    for (int h = 1; h < 32; h <<= 1) {
+        if ((lane & (2 * h - 1)) == 0) {
+            const int b = lane, e = lane + 2 * h;
+            int la = b + h - 1, lb = b + h;
+            while (la >= b && s_lo[la] == s_hi[la]) la--;
+            while (lb < e && s_lo[lb] == s_hi[lb]) lb++;
+            if (la >= b && lb < e) {
+                int pa = s_hi[la] - 1, pb = s_lo[lb];
+                int ka = st[pa * EDT_LS + la], kb = st[pb * EDT_LS + lb];
+                int qa = la * Bw + ka, qb = lb * Bw + kb;
+                long long ca = edt_lift(qa, site_g(la, ka)), cb = edt_lift(qb, site_g(lb, kb));
+                for (bool changed = true; changed;) {
+                    changed = false;
+                    for (;;) {  // drop the left end point while it is not below chord(pred, B)
+                        int lp = la, pp = pa - 1;
+                        if (pp < s_lo[la]) {
+                            lp = la - 1;
+                            while (lp >= b && s_lo[lp] == s_hi[lp]) lp--;
+                            if (lp < b) break;
+                            pp = s_hi[lp] - 1;
+                        }
+                        const int kp = st[pp * EDT_LS + lp], qp = lp * Bw + kp;
+                        const long long cp = edt_lift(qp, site_g(lp, kp));
+                        if (edt_keep(qp, cp, qa, ca, qb, cb)) break;
+                        s_hi[la] = pa;
+                        la = lp;
+                        pa = pp;
+                        qa = qp;
+                        ca = cp;
+                        changed = true;
+                    }
+                    for (;;) {  // drop the right end point while it is not below chord(A, succ)
+                        int ln = lb, pn = pb + 1;
+                        if (pn >= s_hi[lb]) {
+                            ln = lb + 1;
+                            while (ln < e && s_lo[ln] == s_hi[ln]) ln++;
+                            if (ln >= e) break;
+                            pn = s_lo[ln];
+                        }
+                        const int kn = st[pn * EDT_LS + ln], qn = ln * Bw + kn;
+                        const long long cn = edt_lift(qn, site_g(ln, kn));
+                        if (edt_keep(qa, ca, qb, cb, qn, cn)) break;
+                        s_lo[lb] = pb + 1;
+                        lb = ln;
+                        pb = pn;
+                        qb = qn;
+                        cb = cn;
+                        changed = true;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // 3. fill, 32 pixels at a time
     double* out = d_out + (int64_t)r * W;
-    if (k < 0) {
+    const unsigned live = __ballot_sync(0xffffffffu, s_lo[lane] < s_hi[lane]);
+    if (live == 0) {
         for (int i = lane; i < W; i += 32) out[i] = __longlong_as_double(0x7ff0000000000000LL);
         return;
     }
-    for (int i = lane; i < W; i += 32) {
-        // largest j in [0, k] whose left boundary s(v[j-1], v[j]) is <= i (boundary of j = 0 is -inf)
-        int lo = 0, hi = k;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            const int p = v[mid - 1], q = v[mid];
-            const long long n = edt_key(f, q) - edt_key(f, p), d = 2LL * (q - p);
-            if (n <= (long long)i * d) lo = mid;  // s <= i: parabola mid owns i (ties: either is minimal)
-            else hi = mid - 1;
+    int cl = __ffs(live) - 1, cp = s_lo[cl];
+    for (int t0 = 0; t0 < W; t0 += 32) {
+        const int i = t0 + lane;
+        int L = cl, p = cp;
+        int k = st[p * EDT_LS + L];
+        int q = L * Bw + k, gq = site_g(L, k);
+        long long cq = edt_lift(q, gq);
+        if (i < W) {
+            for (;;) {
+                int L2 = L, p2 = p + 1;
+                if (p2 >= s_hi[L]) {
+                    const unsigned rest = live & ~((2u << L) - 1u);
+                    if (rest == 0) break;
+                    L2 = __ffs(rest) - 1;
+                    p2 = s_lo[L2];
+                }
+                const int k2 = st[p2 * EDT_LS + L2];
+                const int q2 = L2 * Bw + k2, g2 = site_g(L2, k2);
+                const long long c2 = edt_lift(q2, g2);
+                if (c2 - cq > 2LL * i * (q2 - q)) break;  // the next owner starts right of i
+                L = L2;
+                p = p2;
+                q = q2;
+                gq = g2;
+                cq = c2;
+            }
+            const long long d2 = (long long)(i - q) * (i - q) + (long long)gq * gq;
+            out[i] = pixel * sqrt((double)d2);
         }
-        const int p = v[lo];
-        const long long d2 = (long long)(i - p) * (i - p) + (long long)f[p] * f[p];
-        out[i] = pixel * sqrt((double)d2);
+        const int last = min(31, W - 1 - t0);
+        cl = __shfl_sync(0xffffffffu, L, last);
+        cp = __shfl_sync(0xffffffffu, p, last);
     }
 }
 
@@ -553,11 +641,11 @@ cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double
     edt_column_kernel<<<cg, 128, 0, st>>>(feat, summ, W, H, nchunk, g);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (W <= EDT_ROW_SMEM_MAX_W) {
-        const size_t smem = 2 * sizeof(int32_t) * (size_t)W;
-        e = cudaFuncSetAttribute(edt_row_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (W <= EDT_BAND_MAX_W && H <= EDT_BAND_MAX_H) {
+        const size_t smem = edt_band_smem(W);
+        e = cudaFuncSetAttribute(edt_row_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        edt_row_smem_kernel<<<(unsigned)H, 32, smem, st>>>(g, W, H, pixel, d_out);
+        edt_row_band_kernel<<<(unsigned)H, 32, smem, st>>>(g, W, pixel, d_out);
     } else {
         edt_row_kernel<<<(unsigned)((H + 63) / 64), 64, 0, st>>>(g, W, H, pixel, v, d_out);
     }
