@@ -125,6 +125,20 @@ __device__ __forceinline__ df tf_sub(const tf& a, float bh, float bm, float bl) 
     return fast_two_sum(u.hi, lo);
 }
 
+// a + b for a triple-float a and a float b: error-free sums throughout, the rounding of
+// the two smallest pieces aside (~2^-70 relative).
+__device__ __forceinline__ tf tf_add_f(const tf& a, float b) {
+    const df s = two_sum(a.h, b);
+    const df t = two_sum(a.m, s.lo);
+    const df u = two_sum(s.hi, t.hi);
+    const df v = two_sum(u.lo, __fadd_rn(t.lo, a.l));
+    return tf{u.hi, v.hi, v.lo};
+}
+
+__device__ __forceinline__ double tf_to_double(const tf& a) {
+    return ((double)a.h + (double)a.m) + (double)a.l;
+}
+
 __device__ __forceinline__ df df_from_double(double x) {
     float h = __double2float_rn(x);
     float l = __double2float_rn(x - (double)h);

@@ -181,6 +181,81 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
     return true;
 }
 
+// Newton step delta = F / (2 S3) (F' = -2 S3, Eq. 7), certificate and, when done, the
+// outputs, from double-float sums and a triple-float z.  The residual F = S2 + c with
+// c = gamma - (1 - kappa_s) e^{-i phi} is a double-float sum: S2 nearly cancels c at a
+// critical point, and the sum keeps the residual's full relative precision.  What only
+// needs the relative precision of the FP32 sums S3 and S4 is FP32: the step, its length,
+// the certificate (which charges the FP32 rounding of the step) and the delta^2, delta^3
+// terms of the Taylor correction of S1.  FP64 is used for the outputs alone.
+__device__ __forceinline__ bool polish_epilogue_df(const PolishK& K, int64_t point, int64_t row, const Sums& s,
+                                                   const df& cx, const df& cy, tf& zx, tf& zy, float z0x, float z0y,
+                                                   int pass, int32_t it_in, double& est_out, float s2_err = 0.f) {
+    const df Fx = df_add(s.S2x, cx), Fy = df_add(s.S2y, cy);
+    const float fx = __fadd_rn(Fx.hi, Fx.lo), fy = __fadd_rn(Fy.hi, Fy.lo);
+    const float tx = 2.f * s.s3x, ty = 2.f * s.s3y;
+    const float den = fmaf(tx, tx, ty * ty);
+    float dx = 0.f, dy = 0.f, est;
+    if (den > 0.f && den < FLT_MAX) {
+        const float rd = __frcp_rn(den);
+        dx = fmaf(fx, tx, fy * ty) * rd;
+        dy = fmaf(fy, tx, -fx * ty) * rd;
+        const float ad = sqrtf(fmaf(dx, dx, dy * dy));
+        const float s3a = 0.5f * sqrtf(den);
+        const float s4a = sqrtf(fmaf(s.s4x, s.s4x, s.s4y * s.s4y));
+        const float r3 = __frcp_rn(s3a);
+        est = 1.5f * ad * ad * s4a * r3 + ad * (4.f * FLT_EPSILON * s.a3 * r3 + 8.f * FLT_EPSILON) + 0.5f * s2_err * r3;
+    } else {
+        // F' vanishes (or the sums overflowed): no step, certified only at an exact zero of F
+        est = (fx == 0.f && fy == 0.f) ? 0.f : FLT_MAX;
+    }
+    const tf nzx = tf_add_f(zx, dx), nzy = tf_add_f(zy, dy);
+    const bool done = est < (float)K.tol_cert || pass + 1 >= K.max_polish;
+    if (!done) {
+        zx = nzx;
+        zy = nzy;
+        return false;
+    }
+    // S1 at the final point by Taylor expansion about the evaluation point:
+    // S1 - S2 delta + S3 delta^2 - S4 delta^3
+    const float d2x = fmaf(dx, dx, -dy * dy), d2y = 2.f * dx * dy;
+    const float d3x = fmaf(d2x, dx, -d2y * dy), d3y = fmaf(d2x, dy, d2y * dx);
+    const float hx = fmaf(s.s3x, d2x, -s.s3y * d2y) - fmaf(s.s4x, d3x, -s.s4y * d3y);
+    const float hy = fmaf(s.s3x, d2y, s.s3y * d2x) - fmaf(s.s4x, d3y, s.s4y * d3x);
+    const df S1nx = df_add(df_sub(s.S1x, df_sub(df_mul_f(s.S2x, dx), df_mul_f(s.S2y, dy))), df{hx, 0.f});
+    const df S1ny = df_add(df_sub(s.S1y, df_add(df_mul_f(s.S2x, dy), df_mul_f(s.S2y, dx))), df{hy, 0.f});
+    const double ozx = tf_to_double(nzx), ozy = tf_to_double(nzy);
+    K.z_out[point] = make_double2(ozx, ozy);
+    if (K.w_out) {
+        const double oms = 1.0 - K.kappa_s;
+        const double wx = fma(oms + K.gamma, ozx, -df_to_double(S1nx));
+        const double wy = fma(oms - K.gamma, ozy, df_to_double(S1ny));
+        K.w_out[point] = make_double2(wx, wy);
+    }
+    if (K.iters_out) K.iters_out[point] = it_in;
+    if (!(est < (float)K.tol_cert)) {
+        atomicAdd(&K.rep->uncertified, 1ull);
+        if (K.rescue_list) {
+            const int idx = atomicAdd(K.rescue_count, 1);
+            if (idx < RESCUE_MAX_POINTS)
+                K.rescue_list[idx] = make_int4(K.field_id, (int)row, (int)(point - row * K.nr), 0);
+        }
+    }
+    const float jx = nzx.h - z0x, jy = nzy.h - z0y;
+    const float zs = 1.f + sqrtf(fmaf(nzx.h, nzx.h, nzy.h * nzy.h));
+    if (fmaf(jx, jx, jy * jy) > 1e-6f * zs * zs) atomicAdd(&K.rep->jumped, 1ull);
+    est_out = est < (float)K.tol_cert ? (double)est : 0.0;  // certified points only; the caller reduces
+    return true;
+}
+
+// c = gamma - (1 - kappa_s) e^{-i phi} of a row as double-float (F = S2 + c)
+__device__ __forceinline__ void row_constant(const PolishK& K, int64_t row, df& cx, df& cy) {
+    const double oms = 1.0 - K.kappa_s;
+    const double2 ph = K.phase[row];
+    cx = df_from_double(fma(-oms, ph.x, K.gamma));
+    cy = df_from_double(oms * ph.y);
+}
+
 template <bool UNIT, bool FP64>
 __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk, unsigned char* smem,
                                             unsigned long long* s_passes_p) {
@@ -207,6 +282,9 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
         if (K.iters_out) it_in = K.iters_in[(size_t)row * K.nr + k];
     }
     double zx = z0x, zy = z0y;
+    tf zxt = tf{z0x, 0.f, 0.f}, zyt = tf{z0y, 0.f, 0.f};
+    df cx = df{0.f, 0.f}, cy = df{0.f, 0.f};
+    if (!FP64 && valid) row_constant(K, row, cx, cy);
     bool need = valid;
     double est_max = 0.0;
     if (tid == 0) s_passes = 0;
@@ -247,7 +325,6 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
             Sums s;
             s.S1x = s.S1y = s.S2x = s.S2y = df{0.f, 0.f};
             s.s3x = s.s3y = s.s4x = s.s4y = s.a3 = 0.f;
-            const tf zxd = tf_from_double(zx), zyd = tf_from_double(zy);
             for (int t0 = 0; t0 < K.n; t0 += TSB) {
                 const int tn = min(TSB, K.n - t0);
                 if (!resident) {
@@ -261,13 +338,11 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
                 }
                 if (need) {
 #pragma unroll 2
-                    for (int j = 0; j < tn; j++) star_df<UNIT>(zxd, zyd, sp[j], st3[j], sm[j], s);
+                    for (int j = 0; j < tn; j++) star_df<UNIT>(zxt, zyt, sp[j], st3[j], sm[j], s);
                 }
             }
             double est = 0.0;
-            if (need && polish_epilogue(K, point, row, df_to_double(s.S1x), df_to_double(s.S1y),
-                                        df_to_double(s.S2x), df_to_double(s.S2y), s.s3x, s.s3y, s.s4x,
-                                        s.s4y, s.a3, zx, zy, z0x, z0y, pass, it_in, est)) {
+            if (need && polish_epilogue_df(K, point, row, s, cx, cy, zxt, zyt, z0x, z0y, pass, it_in, est)) {
                 need = false;
                 est_max = fmax(est_max, est);
             }
@@ -694,13 +769,14 @@ __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const
     const int sl = slot[(int64_t)cy * Pm->nbx + cx];
     const BoxInfo bi = info[sl];
     const float4* L = coeff + (size_t)sl * FMM_P;
-    double zx = z0.x, zy = z0.y;
+    tf zxt = tf{z0.x, 0.f, 0.f}, zyt = tf{z0.y, 0.f, 0.f};
+    df cxr, cyr;
+    row_constant(K, row, cxr, cyr);
     for (int pass = 0; pass < K.max_polish; pass++) {
         passes++;
         Sums sm;
         sm.S1x = sm.S1y = sm.S2x = sm.S2y = df{0.f, 0.f};
         sm.s3x = sm.s3y = sm.s4x = sm.s4y = sm.a3 = 0.f;
-        const tf zxt = tf_from_double(zx), zyt = tf_from_double(zy);
         for (int q = 0; q < bi.near_cnt; q++) {
             const int j = pool[bi.near_off + q];
             star_df<UNIT>(zxt, zyt, K.dfp[j], K.dtf[j], K.dfm[j], sm);
@@ -741,9 +817,7 @@ __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const
         sm.s4y -= b3y;
         sm.a3 += 4.0f * (fabsf(b2x) + fabsf(b2y));
         double est = 0.0;
-        if (polish_epilogue(K, point, row, df_to_double(sm.S1x), df_to_double(sm.S1y), df_to_double(sm.S2x),
-                            df_to_double(sm.S2y), sm.s3x, sm.s3y, sm.s4x, sm.s4y, sm.a3, zx, zy, z0.x, z0.y, pass,
-                            it_in, est, (double)bi.s2_err)) {
+        if (polish_epilogue_df(K, point, row, sm, cxr, cyr, zxt, zyt, z0.x, z0.y, pass, it_in, est, bi.s2_err)) {
             est_max = est;
             break;
         }
