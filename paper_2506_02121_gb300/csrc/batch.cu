@@ -1,5 +1,6 @@
 // Batched critical curves: many fields of uneven N in one persistent tracing launch, one
-// batched seam join and one batched polish, optionally replayed as a CUDA graph.
+// batched seam join, then the polish (far-field polish per field for fields with enough
+// stars, one batched direct polish for the rest), optionally replayed as a CUDA graph.
 //
 // Work items are (field, sub-range) pairs.  Each field gets a number of phi sub-ranges in
 // proportion to its estimated work (rows x n_r x (N + n_r)), so that items are of similar
@@ -33,6 +34,12 @@ struct cc_batch {
     size_t hits_begin = 0, hits_bytes = 0;
     size_t off_rtasks = 0, off_list = 0, off_nlist = 0;
     size_t off_tasks = 0, off_items = 0, off_seams = 0, off_ptasks = 0, off_reps = 0, off_queue = 0, off_work = 0;
+    // far-field polish: fields with enough stars run it one after another in stream order,
+    // sharing one scratch region; the others share one batched direct polish launch
+    std::vector<char> use_fmm;
+    std::vector<PolishArgs> fmm_args;
+    size_t off_fmm = 0;
+    int direct_count = 0;
     size_t work_stride = 0, total = 0;
     // bound buffers
     bool bound = false;
@@ -94,7 +101,11 @@ cudaError_t enqueue(cc_batch* b, cudaStream_t st, bool capturing) {
         cudaSuccess)
         return e;
     if ((e = rec(b->ev[2], st, capturing)) != cudaSuccess) return e;
-    if ((e = launch_polish_batch(ws + b->off_ptasks, b->count, b->total_blocks, st)) != cudaSuccess) return e;
+    if (b->direct_count > 0 &&
+        (e = launch_polish_batch(ws + b->off_ptasks, b->direct_count, b->total_blocks, st)) != cudaSuccess)
+        return e;
+    for (const PolishArgs& pa : b->fmm_args)
+        if ((e = launch_polish_fmm(pa, ws + b->off_fmm, st)) != cudaSuccess) return e;
     if ((e = launch_rescue(nullptr, (const RescueTask*)(ws + b->off_rtasks), (const int4*)(ws + b->off_list),
                            (const int*)(ws + b->off_nlist), RESCUE_MAX_POINTS, b->opt.tol_abs, b->opt.max_iter_warm, st)) !=
         cudaSuccess)
@@ -187,6 +198,14 @@ int cc_batch_create(cc_field* const* fields, int32_t count, const int64_t* m, in
     o += a256(sizeof(int2) * std::max(1, b->nseams));
     b->off_ptasks = o;
     o += a256(polish_task_bytes() * count);
+    int64_t fmm_points = 0;
+    for (int f = 0; f < count; f++) {
+        const bool u = b->opt.far_field && b->dev[f].n >= FMM_MIN_STARS;
+        b->use_fmm.push_back(u ? 1 : 0);
+        if (u) fmm_points = std::max<int64_t>(fmm_points, b->rows[f] * b->nr[f]);
+    }
+    b->off_fmm = o;
+    if (fmm_points > 0) o += a256(fmm_workspace_bytes(fmm_points));
     b->hits_begin = o;
     for (int f = 0; f < count; f++) {
         b->off_hits.push_back(o);
@@ -255,6 +274,8 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
     std::vector<TraceTask> tasks(b->count);
     std::vector<RescueTask> rtasks(b->count);
     std::vector<unsigned char> ptasks(polish_task_bytes() * b->count);
+    b->fmm_args.clear();
+    b->direct_count = 0;
     std::vector<int2> seams;
     std::vector<std::pair<double, int2>> items;
     int64_t block0 = 0;
@@ -304,7 +325,13 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         pa.rescue_count = (int*)(ws + b->off_nlist);
         pa.field_id = f;
         pa.skip_if = nullptr;
-        polish_task_fill(pa, block0, ptasks.data() + polish_task_bytes() * f);
+        if (b->use_fmm[f]) {
+            b->fmm_args.push_back(pa);
+        } else {
+            polish_task_fill(pa, block0, ptasks.data() + polish_task_bytes() * b->direct_count);
+            b->direct_count++;
+            block0 += polish_blocks(b->rows[f] * b->nr[f]);
+        }
         RescueTask& rt = rtasks[f];
         rt.stars = fd.star64;
         rt.n = (int)fd.n;
@@ -316,7 +343,6 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         rt.z = pa.z_out;
         rt.w = pa.w_out;
         rt.rep = t.rep;
-        block0 += polish_blocks(b->rows[f] * b->nr[f]);
     }
     b->total_blocks = block0;
     std::stable_sort(items.begin(), items.end(), [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
