@@ -84,6 +84,25 @@ def _load():
         lib.orc_distance_map_separable.restype = None
         lib.orc_moving_distance_map.argtypes = [_I32P, i32, i32, dbl, dbl, _DP]
         lib.orc_moving_distance_map.restype = None
+        ci = ctypes.c_int
+        lib.orc_rect_F.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, dbl, dbl, dbl, ci, dbl, _DP, _DP]
+        lib.orc_rect_F.restype = dbl
+        lib.orc_rect_dF.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, dbl, ci, _DP, _DP]
+        lib.orc_rect_dF.restype = dbl
+        lib.orc_rect_alpha.argtypes = [dbl, dbl, dbl, ci, _DP, _DP]
+        lib.orc_rect_alpha.restype = None
+        lib.orc_rect_dalpha_dzb.argtypes = [dbl, dbl, dbl, ci, _DP, _DP]
+        lib.orc_rect_dalpha_dzb.restype = None
+        lib.orc_rect_choose_t.argtypes = [dbl, dbl, dbl, dbl, dbl]
+        lib.orc_rect_choose_t.restype = ci
+        lib.orc_rect_solve_row.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, dbl, dbl, dbl, ci, dbl, _DP, _DP, ci,
+                                           dbl, _I32P]
+        lib.orc_rect_solve_row.restype = i64
+        lib.orc_rect_critical_curves.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, dbl, dbl, dbl, ci, i64, dbl, ci,
+                                                 ci, _DP, _I32P]
+        lib.orc_rect_critical_curves.restype = i64
+        lib.orc_rect_map_caustics.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, dbl, dbl, dbl, ci, _DP, i64, _DP]
+        lib.orc_rect_map_caustics.restype = None
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = ctypes.c_int
         _lib = lib
@@ -103,6 +122,44 @@ def _stars(x, y, m):
     return x, y, m
 
 
+class Rect:
+    """Rectangular microlens field (Sec. 4.2, Appendix B): smooth sheet of convergence
+    kappa_star, corner c = c1 + i c2, logarithm series truncated at the odd order t."""
+
+    def __init__(self, kappa_star: float, c1: float, c2: float, t: int):
+        if t < 1 or t % 2 == 0:
+            raise ValueError("t must be odd and >= 1")
+        self.kappa_star, self.c1, self.c2, self.t = float(kappa_star), float(c1), float(c2), int(t)
+
+    def n_roots(self, n: int) -> int:
+        return 2 * n + self.t - 1
+
+    def args(self):
+        return self.kappa_star, self.c1, self.c2, self.t
+
+
+def rect_choose_t(kappa_star, c1, c2, eps=1e-9, s=2.0) -> int:
+    """Odd truncation order from the Appendix B error bound, moved away from orders whose
+    leading coefficient vanishes ((t - 1) Arg c a multiple of pi)."""
+    return int(_load().orc_rect_choose_t(float(kappa_star), float(c1), float(c2), float(eps), float(s)))
+
+
+def rect_alpha(kappa_star, c1, c2, z, t=-1):
+    """alpha_s(z) of the rectangle (Appendix B); t < 0: exact logarithms."""
+    zz = np.array([complex(z).real, complex(z).imag])
+    out = np.zeros(2)
+    _load().orc_rect_alpha(float(kappa_star), float(c1), float(c2), int(t), _d(zz), _d(out))
+    return complex(out[0], out[1])
+
+
+def rect_dalpha_dzb(kappa_star, c1, c2, t, z):
+    """dalpha_s/dconj(z) of the rectangle at z (Appendix B, final form)."""
+    zz = np.array([complex(z).real, complex(z).imag])
+    out = np.zeros(2)
+    _load().orc_rect_dalpha_dzb(float(kappa_star), float(c1), float(c2), int(t), _d(zz), _d(out))
+    return complex(out[0], out[1])
+
+
 def num_threads() -> int:
     """OpenMP threads the oracle uses (1 when built without OpenMP)."""
     return int(_load().orc_num_threads())
@@ -113,21 +170,28 @@ def phi(j: int, msteps: int) -> float:
     return float(_load().orc_phi(int(j), int(msteps)))
 
 
-def F(x, y, m, kappa_s, gamma, phi_, z):
-    """F(z, phi) of the parametric critical-curve equation (Sec. 3.1, Appendix A)."""
+def F(x, y, m, kappa_s, gamma, phi_, z, rect: Rect | None = None):
+    """F(z, phi) of the parametric critical-curve equation (Sec. 3.1, Appendix A; with
+    rect, the rectangular field of Appendix B)."""
     x, y, m = _stars(x, y, m)
     zz = np.array([complex(z).real, complex(z).imag])
     out = np.zeros(2)
-    _load().orc_F(_d(x), _d(y), _d(m), len(x), kappa_s, gamma, phi_, _d(zz), _d(out))
+    if rect is None:
+        _load().orc_F(_d(x), _d(y), _d(m), len(x), kappa_s, gamma, phi_, _d(zz), _d(out))
+    else:
+        _load().orc_rect_F(_d(x), _d(y), _d(m), len(x), kappa_s, gamma, *rect.args(), phi_, _d(zz), _d(out))
     return complex(out[0], out[1])
 
 
-def dF(x, y, m, z):
-    """dF/dz = -2 sum m_i/(z - z_i)^3."""
+def dF(x, y, m, z, rect: Rect | None = None):
+    """dF/dz = -2 sum m_i/(z - z_i)^3 (minus the rectangle's polynomial derivative)."""
     x, y, m = _stars(x, y, m)
     zz = np.array([complex(z).real, complex(z).imag])
     out = np.zeros(2)
-    _load().orc_dF(_d(x), _d(y), _d(m), len(x), _d(zz), _d(out))
+    if rect is None:
+        _load().orc_dF(_d(x), _d(y), _d(m), len(x), _d(zz), _d(out))
+    else:
+        _load().orc_rect_dF(_d(x), _d(y), _d(m), len(x), *rect.args(), _d(zz), _d(out))
     return complex(out[0], out[1])
 
 
@@ -138,50 +202,67 @@ def inv_mu(x, y, m, kappa_s, gamma, z):
     return float(_load().orc_inv_mu(_d(x), _d(y), _d(m), len(x), kappa_s, gamma, _d(zz)))
 
 
-def solve_row(x, y, m, kappa_s, gamma, phi_, z0=None, max_iter=500, tol=1e-9, return_iters=False):
-    """Roots of F(., phi) for one row: Jacobi Aberth (from z0, or from the z_i +- 1 guesses
-    when z0 is None) followed by a Newton polish.  Returns (z[2N] complex128, unfrozen)."""
+def solve_row(x, y, m, kappa_s, gamma, phi_, z0=None, max_iter=500, tol=1e-9, return_iters=False,
+              rect: Rect | None = None):
+    """Roots of F(., phi) for one row: Jacobi Aberth (from z0, or from the initial guesses
+    when z0 is None) followed by a Newton polish.  Returns (z[n_r] complex128, unfrozen);
+    n_r = 2N, or 2N + t - 1 for a rectangular field."""
     x, y, m = _stars(x, y, m)
     n = len(x)
-    out = np.zeros(2 * n, dtype=np.complex128)
+    nr = 2 * n if rect is None else rect.n_roots(n)
+    out = np.zeros(nr, dtype=np.complex128)
     zin = None
     if z0 is not None:
         zin = np.ascontiguousarray(z0, dtype=np.complex128)
-        if zin.shape != (2 * n,):
-            raise ValueError("z0 must have 2N entries")
-    iters = np.zeros(2 * n, dtype=np.int32)
-    left = _load().orc_solve_row(_d(x), _d(y), _d(m), n, kappa_s, gamma, phi_,
-                                 None if zin is None else zin.view(np.float64).ctypes.data_as(_DP),
-                                 out.view(np.float64).ctypes.data_as(_DP), int(max_iter), tol,
-                                 iters.ctypes.data_as(_I32P))
+        if zin.shape != (nr,):
+            raise ValueError("z0 must have n_r entries")
+    iters = np.zeros(nr, dtype=np.int32)
+    zp = None if zin is None else zin.view(np.float64).ctypes.data_as(_DP)
+    if rect is None:
+        left = _load().orc_solve_row(_d(x), _d(y), _d(m), n, kappa_s, gamma, phi_, zp,
+                                     out.view(np.float64).ctypes.data_as(_DP), int(max_iter), tol,
+                                     iters.ctypes.data_as(_I32P))
+    else:
+        left = _load().orc_rect_solve_row(_d(x), _d(y), _d(m), n, kappa_s, gamma, *rect.args(), phi_, zp,
+                                          out.view(np.float64).ctypes.data_as(_DP), int(max_iter), tol,
+                                          iters.ctypes.data_as(_I32P))
     if return_iters:
         return out, int(left), iters
     return out, int(left)
 
 
-def critical_curves(x, y, m, kappa_s, gamma, msteps, tol=1e-9, max_iter_cold=500, max_iter_warm=200):
-    """Chain matrix of Sec. 4.3: (m+1) x 2N complex128 roots, row j at phi_j = 2 pi j/m.
+def critical_curves(x, y, m, kappa_s, gamma, msteps, tol=1e-9, max_iter_cold=500, max_iter_warm=200,
+                    rect: Rect | None = None):
+    """Chain matrix of Sec. 4.3: (m+1) x n_r complex128 roots, row j at phi_j = 2 pi j/m.
     Returns (z, iters, unfrozen_total)."""
     if msteps < 2 or msteps % 2:
         raise ValueError("m must be even and >= 2")
     x, y, m = _stars(x, y, m)
     n = len(x)
-    z = np.zeros((msteps + 1, 2 * n), dtype=np.complex128)
-    it = np.zeros((msteps + 1, 2 * n), dtype=np.int32)
-    bad = _load().orc_critical_curves(_d(x), _d(y), _d(m), n, kappa_s, gamma, int(msteps), tol,
-                                      int(max_iter_cold), int(max_iter_warm),
-                                      z.view(np.float64).ctypes.data_as(_DP), it.ctypes.data_as(_I32P))
+    nr = 2 * n if rect is None else rect.n_roots(n)
+    z = np.zeros((msteps + 1, nr), dtype=np.complex128)
+    it = np.zeros((msteps + 1, nr), dtype=np.int32)
+    zp, ip = z.view(np.float64).ctypes.data_as(_DP), it.ctypes.data_as(_I32P)
+    if rect is None:
+        bad = _load().orc_critical_curves(_d(x), _d(y), _d(m), n, kappa_s, gamma, int(msteps), tol,
+                                          int(max_iter_cold), int(max_iter_warm), zp, ip)
+    else:
+        bad = _load().orc_rect_critical_curves(_d(x), _d(y), _d(m), n, kappa_s, gamma, *rect.args(), int(msteps),
+                                               tol, int(max_iter_cold), int(max_iter_warm), zp, ip)
     return z, it, int(bad)
 
 
-def map_caustics(x, y, m, kappa_s, gamma, z):
-    """Lens map w(z) of every critical point (Sec. 3.1); same shape as z."""
+def map_caustics(x, y, m, kappa_s, gamma, z, rect: Rect | None = None):
+    """Lens map w(z) of every critical point (Sec. 3.1; with rect, alpha_s of Appendix B);
+    same shape as z."""
     x, y, m = _stars(x, y, m)
     zz = np.ascontiguousarray(z, dtype=np.complex128)
     w = np.zeros_like(zz)
-    _load().orc_map_caustics(_d(x), _d(y), _d(m), len(x), kappa_s, gamma,
-                             zz.view(np.float64).ctypes.data_as(_DP), zz.size,
-                             w.view(np.float64).ctypes.data_as(_DP))
+    zp, wp = zz.view(np.float64).ctypes.data_as(_DP), w.view(np.float64).ctypes.data_as(_DP)
+    if rect is None:
+        _load().orc_map_caustics(_d(x), _d(y), _d(m), len(x), kappa_s, gamma, zp, zz.size, wp)
+    else:
+        _load().orc_rect_map_caustics(_d(x), _d(y), _d(m), len(x), kappa_s, gamma, *rect.args(), zp, zz.size, wp)
     return w
 
 

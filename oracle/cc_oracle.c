@@ -14,7 +14,8 @@
  *     (Appendix A), so alpha_s(z) = -kappa_* z everywhere and
  *       w(z)    = (1 - kappa_s) z + gamma conj(z) - sum_i m_i / conj(z - z_i)   (Sec. 3.1)
  *       F(z,phi)= gamma + sum_i m_i / (z - z_i)^2 - (1 - kappa_s) e^{-i phi}     (Eq. parametric cc)
- *     where kappa_s is the smooth convergence (kappa - kappa_*).
+ *     where kappa_s is the smooth convergence (kappa - kappa_*); or the rectangular field
+ *     of Sec. 4.2 with the polynomial alpha_s of Appendix B (the orc_rect_* functions).
  *   - Complex arrays are interleaved (re, im) doubles == C99 double complex.
  *   - Built with -ffp-contract=off and without fast-math: every operation is an IEEE
  *     round-to-nearest FP64 operation in the order written.
@@ -31,48 +32,161 @@ typedef double complex cplx;
 #define ORC_PI 3.14159265358979323846
 
 /* ------------------------------------------------------------------------------------
- * Lens model (Sec. 3.1 and Appendix A)
+ * Lens model (Sec. 3.1, Sec. 4.2 and Appendices A and B)
+ *
+ * Two smooth-matter models:
+ *   disc      the circular field with its compensating sheet extended to infinity
+ *             (Appendix A): alpha_s(z) = -kappa_* z, so dalpha_s/dz = -kappa_* and
+ *             dalpha_s/dconj(z) = 0.
+ *   rectangle the rectangular field of corner c = c1 + i c2 (Sec. 4.2) with the complex
+ *             logarithms of alpha_s replaced by their Taylor series truncated at an odd
+ *             order t and the sheet extended to infinity (Appendix B).  Then
+ *             dalpha_s/dz = -kappa_* and dalpha_s/dconj(z) is a polynomial in conj(z).
+ * In both, 1 - kappa - dalpha_s/dz = 1 - kappa_s (kappa = kappa_s + kappa_*).
  * ------------------------------------------------------------------------------------ */
+typedef struct {
+    const double *x, *y, *m;
+    int64_t n;
+    double kappa_s, gamma;
+    int rect;          /* 0: disc; 1: rectangle */
+    double kappa_star; /* rectangle: convergence of the smooth sheet */
+    cplx c;            /* rectangle: corner c1 + i c2 */
+    int t;             /* rectangle: odd truncation order of the logarithm series */
+    int64_t nr;        /* roots per row: 2n (disc), 2n + t - 1 (rectangle) */
+} lens_t;
 
-/* F(z, phi) of the parametric critical-curve equation (Sec. 3.1) with the infinite
- * compensating sheet (Appendix A): dalpha_s/dz = -kappa_*, dalpha_s/dconj(z) = 0, so
- * 1 - kappa - dalpha_s/dz = 1 - kappa_s. */
-static cplx lens_F(const double* x, const double* y, const double* m, int64_t n,
-                   double kappa_s, double gamma, cplx e_mphi, cplx z) {
-    cplx s = 0.0;
-    for (int64_t i = 0; i < n; i++) {
-        cplx d = z - (x[i] + I * y[i]);
-        s += m[i] / (d * d);
-    }
-    return gamma + s - (1.0 - kappa_s) * e_mphi;
+static lens_t disc_lens(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
+                        double gamma) {
+    lens_t L;
+    memset(&L, 0, sizeof L);
+    L.x = x;
+    L.y = y;
+    L.m = m;
+    L.n = n;
+    L.kappa_s = kappa_s;
+    L.gamma = gamma;
+    L.nr = 2 * n;
+    return L;
 }
 
-/* dF/dz = -2 sum_i m_i / (z - z_i)^3 (derivative of F, needed by P'/P in Sec. 3.2). */
-static cplx lens_dF(const double* x, const double* y, const double* m, int64_t n, cplx z) {
-    cplx s = 0.0;
-    for (int64_t i = 0; i < n; i++) {
-        cplx d = z - (x[i] + I * y[i]);
-        s += m[i] / (d * d * d);
-    }
-    return -2.0 * s;
+static lens_t rect_lens(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
+                        double gamma, double kappa_star, double c1, double c2, int t) {
+    lens_t L = disc_lens(x, y, m, n, kappa_s, gamma);
+    L.rect = 1;
+    L.kappa_star = kappa_star;
+    L.c = c1 + I * c2;
+    L.t = t;
+    L.nr = 2 * n + (t - 1);
+    return L;
 }
 
-/* Complex lens equation (Sec. 3.1) with alpha_s = -kappa_* z (Appendix A):
- * w = (1 - kappa_s) z + gamma conj(z) - sum_i m_i / (conj(z) - conj(z_i)). */
-static cplx lens_w(const double* x, const double* y, const double* m, int64_t n,
-                   double kappa_s, double gamma, cplx z) {
-    cplx s = 0.0;
-    for (int64_t i = 0; i < n; i++) {
-        cplx d = conj(z) - (x[i] - I * y[i]);
-        s += m[i] / d;
+/* Rectangle: dalpha_s/dconj(z) as a function of zb = conj(z), the final form of
+ * Appendix B:
+ *   (-kappa_* i / pi) [ (zb/c)^t (1 + (-1)^t)(1 - e^{2 i Arg(c) t})
+ *                       + sum_{j=1}^{t} (1/j) (zb/c)^j (1 + (-1)^j)(1 - e^{2 i Arg(c) j}) ]
+ *   + kappa_* - 4 kappa_* Arg(c) / pi. */
+static cplx rect_dalpha_dzb(const lens_t* L, cplx zb) {
+    const double th = carg(L->c);
+    const cplx u = zb / L->c;
+    cplx s = 0.0, p = 1.0;
+    for (int j = 1; j <= L->t; j++) {
+        p *= u; /* (zb/c)^j */
+        const double ev = (j % 2 == 0) ? 2.0 : 0.0; /* 1 + (-1)^j */
+        s += (1.0 / j) * p * ev * (1.0 - cexp(I * 2.0 * th * j));
     }
-    return (1.0 - kappa_s) * z + gamma * conj(z) - s;
+    const double evt = (L->t % 2 == 0) ? 2.0 : 0.0;
+    s += p * evt * (1.0 - cexp(I * 2.0 * th * L->t));
+    return (-L->kappa_star * I / ORC_PI) * s + L->kappa_star - 4.0 * L->kappa_star * th / ORC_PI;
+}
+
+/* Rectangle: d^2 alpha_s / dconj(z)^2 (Appendix B), with (zb/c)^j / zb written as
+ * zb^(j-1) / c^j so that zb = 0 needs no division:
+ *   (-kappa_* i / pi) [ t zb^(t-1)/c^t (1 + (-1)^t)(1 - e^{2 i Arg(c) t})
+ *                       + sum_{j=1}^{t} zb^(j-1)/c^j (1 + (-1)^j)(1 - e^{2 i Arg(c) j}) ]. */
+static cplx rect_d2alpha_dzb2(const lens_t* L, cplx zb) {
+    const double th = carg(L->c);
+    cplx s = 0.0, p = 1.0 / L->c; /* zb^(j-1) / c^j at j = 1 */
+    cplx last = p;
+    for (int j = 1; j <= L->t; j++) {
+        const double ev = (j % 2 == 0) ? 2.0 : 0.0;
+        s += p * ev * (1.0 - cexp(I * 2.0 * th * j));
+        last = p;
+        p *= zb / L->c;
+    }
+    const double evt = (L->t % 2 == 0) ? 2.0 : 0.0;
+    s += (double)L->t * last * evt * (1.0 - cexp(I * 2.0 * th * L->t));
+    return (-L->kappa_star * I / ORC_PI) * s;
+}
+
+/* Rectangle: alpha_s(z) (Appendix B) with every log(a - zb), a in {c, conj c, -c, -conj c},
+ * replaced by log(a) - sum_{j=1}^{t} (1/j) (zb/a)^j.  t < 0 evaluates the series' limit
+ * log(a) + log(1 - zb/a): the logarithm continued from zb = 0 without crossing a branch cut
+ * for |z| < |c| (the principal log(a - zb) jumps outside the rectangle, Appendix A); inside
+ * the rectangle the two are equal.
+ *   alpha_s = (-kappa_* i / pi) [ (c - zb) L(c) - (conj c - zb) L(conj c)
+ *                                 + (-c - zb) L(-c) - (-conj c - zb) L(-conj c) ]
+ *             - kappa_* (c + conj c + zb + z). */
+static cplx rect_log_term(cplx a, cplx zb, int t) {
+    if (t < 0) return clog(a) + clog(1.0 - zb / a);
+    cplx s = clog(a), p = 1.0;
+    for (int j = 1; j <= t; j++) {
+        p *= zb / a;
+        s -= p / (double)j;
+    }
+    return s;
+}
+
+static cplx rect_alpha(const lens_t* L, cplx z, int t) {
+    const cplx zb = conj(z), c = L->c, cb = conj(L->c);
+    const cplx A = (c - zb) * rect_log_term(c, zb, t) - (cb - zb) * rect_log_term(cb, zb, t) +
+                   (-c - zb) * rect_log_term(-c, zb, t) - (-cb - zb) * rect_log_term(-cb, zb, t);
+    return (-L->kappa_star * I / ORC_PI) * A - L->kappa_star * (c + cb + zb + z);
+}
+
+/* F(z, phi) of the parametric critical-curve equation (Sec. 3.1):
+ *   F = gamma + sum_i m_i/(z - z_i)^2 - conj(dalpha_s/dconj z) - (1 - kappa_s) e^{-i phi}. */
+static cplx lens_F(const lens_t* L, cplx e_mphi, cplx z) {
+    cplx s = 0.0;
+    for (int64_t i = 0; i < L->n; i++) {
+        cplx d = z - (L->x[i] + I * L->y[i]);
+        s += L->m[i] / (d * d);
+    }
+    cplx f = L->gamma + s - (1.0 - L->kappa_s) * e_mphi;
+    if (L->rect) f -= conj(rect_dalpha_dzb(L, conj(z)));
+    return f;
+}
+
+/* dF/dz = -2 sum_i m_i / (z - z_i)^3 - d/dz conj(dalpha_s/dconj z)
+ * (derivative of F, needed by P'/P in Sec. 3.2); d/dz conj(g(conj z)) = conj(g'(conj z)). */
+static cplx lens_dF(const lens_t* L, cplx z) {
+    cplx s = 0.0;
+    for (int64_t i = 0; i < L->n; i++) {
+        cplx d = z - (L->x[i] + I * L->y[i]);
+        s += L->m[i] / (d * d * d);
+    }
+    cplx f = -2.0 * s;
+    if (L->rect) f -= conj(rect_d2alpha_dzb2(L, conj(z)));
+    return f;
+}
+
+/* Complex lens equation (Sec. 3.1): w = (1 - kappa) z + gamma conj(z)
+ *   - sum_i m_i / (conj(z) - conj(z_i)) - alpha_s(z), kappa = kappa_s + kappa_*;
+ * for the disc alpha_s = -kappa_* z, which leaves (1 - kappa_s) z. */
+static cplx lens_w(const lens_t* L, cplx z) {
+    cplx s = 0.0;
+    for (int64_t i = 0; i < L->n; i++) {
+        cplx d = conj(z) - (L->x[i] - I * L->y[i]);
+        s += L->m[i] / d;
+    }
+    if (!L->rect) return (1.0 - L->kappa_s) * z + L->gamma * conj(z) - s;
+    return (1.0 - L->kappa_s - L->kappa_star) * z + L->gamma * conj(z) - s - rect_alpha(L, z, L->t);
 }
 
 double orc_F(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
              double gamma, double phi, const double* z, double* out) {
+    lens_t L = disc_lens(x, y, m, n, kappa_s, gamma);
     cplx e = cos(phi) - I * sin(phi);
-    cplx f = lens_F(x, y, m, n, kappa_s, gamma, e, z[0] + I * z[1]);
+    cplx f = lens_F(&L, e, z[0] + I * z[1]);
     out[0] = creal(f);
     out[1] = cimag(f);
     return cabs(f);
@@ -80,7 +194,8 @@ double orc_F(const double* x, const double* y, const double* m, int64_t n, doubl
 
 double orc_dF(const double* x, const double* y, const double* m, int64_t n, const double* z,
               double* out) {
-    cplx f = lens_dF(x, y, m, n, z[0] + I * z[1]);
+    lens_t L = disc_lens(x, y, m, n, 0.0, 0.0);
+    cplx f = lens_dF(&L, z[0] + I * z[1]);
     out[0] = creal(f);
     out[1] = cimag(f);
     return cabs(f);
@@ -101,6 +216,62 @@ double orc_inv_mu(const double* x, const double* y, const double* m, int64_t n, 
     return a * a - g * g;
 }
 
+/* Rectangle versions of F, F', alpha_s and w (Sec. 4.2, Appendix B).  t_alpha < 0 in
+ * orc_rect_alpha evaluates the exact logarithms. */
+double orc_rect_F(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
+                  double gamma, double kappa_star, double c1, double c2, int t, double phi,
+                  const double* z, double* out) {
+    lens_t L = rect_lens(x, y, m, n, kappa_s, gamma, kappa_star, c1, c2, t);
+    cplx e = cos(phi) - I * sin(phi);
+    cplx f = lens_F(&L, e, z[0] + I * z[1]);
+    out[0] = creal(f);
+    out[1] = cimag(f);
+    return cabs(f);
+}
+
+double orc_rect_dF(const double* x, const double* y, const double* m, int64_t n, double kappa_star,
+                   double c1, double c2, int t, const double* z, double* out) {
+    lens_t L = rect_lens(x, y, m, n, 0.0, 0.0, kappa_star, c1, c2, t);
+    cplx f = lens_dF(&L, z[0] + I * z[1]);
+    out[0] = creal(f);
+    out[1] = cimag(f);
+    return cabs(f);
+}
+
+void orc_rect_alpha(double kappa_star, double c1, double c2, int t_alpha, const double* z, double* out) {
+    lens_t L = rect_lens(NULL, NULL, NULL, 0, 0.0, 0.0, kappa_star, c1, c2, t_alpha < 0 ? 1 : t_alpha);
+    cplx a = rect_alpha(&L, z[0] + I * z[1], t_alpha);
+    out[0] = creal(a);
+    out[1] = cimag(a);
+}
+
+void orc_rect_dalpha_dzb(double kappa_star, double c1, double c2, int t, const double* z, double* out) {
+    lens_t L = rect_lens(NULL, NULL, NULL, 0, 0.0, 0.0, kappa_star, c1, c2, t);
+    cplx a = rect_dalpha_dzb(&L, conj(z[0] + I * z[1]));
+    out[0] = creal(a);
+    out[1] = cimag(a);
+}
+
+/* Truncation order t for the rectangle (Appendix B): the smallest odd t >= 3 whose bound
+ *   (kappa_* / pi) (4 / (t + 1)) s^-(t+1) |c| (s + 1)/(s - 1)
+ * on the alpha_s error for |z| s < |c| is <= eps; then t grows by 2 while (t - 1) Arg(c)
+ * lies within 10% of pi of a multiple of pi (where the leading coefficient vanishes or
+ * nearly so). */
+int orc_rect_choose_t(double kappa_star, double c1, double c2, double eps, double s) {
+    const double ac = sqrt(c1 * c1 + c2 * c2), th = atan2(c2, c1);
+    int t = 3;
+    for (; t < 1000; t += 2) {
+        double b = (kappa_star / ORC_PI) * (4.0 / (t + 1)) * pow(1.0 / s, t + 1) * ac * (s + 1.0) / (s - 1.0);
+        if (b <= eps) break;
+    }
+    for (int guard = 0; guard < 1000; guard++) {
+        double r = fmod((t - 1) * th, ORC_PI);
+        if (r > 0.1 * ORC_PI && r < 0.9 * ORC_PI) break;
+        t += 2;
+    }
+    return t;
+}
+
 /* ------------------------------------------------------------------------------------
  * Aberth-Ehrlich iteration on P(z) = F(z) prod (z - z_i)^2 (Sec. 3.2)
  * ------------------------------------------------------------------------------------ */
@@ -108,15 +279,13 @@ double orc_inv_mu(const double* x, const double* y, const double* m, int64_t n, 
 /* One root's Aberth correction (Sec. 3.2):
  *   P'/P = F'/F + 2 sum_i 1/(z_k - z_i)
  *   Delta = 1 / (P'/P - sum_{r != k} 1/(z_k - z_r)),   z_k <- z_k - Delta. */
-static cplx aberth_delta(const double* x, const double* y, const double* m, int64_t n,
-                         double kappa_s, double gamma, cplx e_mphi, const cplx* z, int64_t nr,
-                         int64_t k) {
+static cplx aberth_delta(const lens_t* L, cplx e_mphi, const cplx* z, int64_t nr, int64_t k) {
     cplx zk = z[k];
-    cplx F = lens_F(x, y, m, n, kappa_s, gamma, e_mphi, zk);
+    cplx F = lens_F(L, e_mphi, zk);
     if (F == 0.0) return 0.0; /* z_k is an exact root */
-    cplx dF = lens_dF(x, y, m, n, zk);
+    cplx dF = lens_dF(L, zk);
     cplx s1 = 0.0;
-    for (int64_t i = 0; i < n; i++) s1 += 1.0 / (zk - (x[i] + I * y[i]));
+    for (int64_t i = 0; i < L->n; i++) s1 += 1.0 / (zk - (L->x[i] + I * L->y[i]));
     cplx pp = dF / F + 2.0 * s1;
     cplx ab = 0.0;
     for (int64_t r = 0; r < nr; r++)
@@ -124,14 +293,12 @@ static cplx aberth_delta(const double* x, const double* y, const double* m, int6
     return 1.0 / (pp - ab);
 }
 
-/* Jacobi Aberth over the n_r = 2n roots of one phi row (Sec. 3.2): every iteration
- * updates all unfrozen roots from the previous iterate; frozen roots still enter the
- * root sum.  A root is frozen once |z^{a+1} - z^a| < tol (Sec. 3.2 footnote).
+/* Jacobi Aberth over the n_r roots of one phi row (Sec. 3.2): every iteration updates
+ * all unfrozen roots from the previous iterate; frozen roots still enter the root sum.
+ * A root is frozen once |z^{a+1} - z^a| < tol (Sec. 3.2 footnote).
  * Returns the number of roots still unfrozen after max_iter iterations. */
-static int64_t aberth_jacobi(const double* x, const double* y, const double* m, int64_t n,
-                             double kappa_s, double gamma, double phi, cplx* z, int max_iter,
-                             double tol, int32_t* iters) {
-    int64_t nr = 2 * n;
+static int64_t aberth_jacobi(const lens_t* L, double phi, cplx* z, int max_iter, double tol, int32_t* iters) {
+    int64_t nr = L->nr;
     cplx e = cos(phi) - I * sin(phi);
     cplx* nxt = (cplx*)malloc(sizeof(cplx) * (size_t)nr);
     unsigned char* frozen = (unsigned char*)calloc((size_t)nr, 1);
@@ -148,7 +315,7 @@ static int64_t aberth_jacobi(const double* x, const double* y, const double* m, 
                 frozen_nxt[k] = 1;
                 continue;
             }
-            cplx d = aberth_delta(x, y, m, n, kappa_s, gamma, e, z, nr, k);
+            cplx d = aberth_delta(L, e, z, nr, k);
             nxt[k] = z[k] - d;
             if (iters) iters[k] = a + 1;
             if (cabs(d) < tol) {
@@ -171,15 +338,14 @@ static int64_t aberth_jacobi(const double* x, const double* y, const double* m, 
 /* Newton refinement of each root on F alone, to |dz| < 1e-13 max(1,|z|) (at most 8
  * steps).  This takes the Aberth result (accurate to ~1e-9) to the FP64 limit, so the
  * oracle's roots stand for the exact roots of F(., phi). */
-static void newton_polish(const double* x, const double* y, const double* m, int64_t n,
-                          double kappa_s, double gamma, double phi, cplx* z, int64_t nr) {
+static void newton_polish(const lens_t* L, double phi, cplx* z) {
     cplx e = cos(phi) - I * sin(phi);
 #pragma omp parallel for schedule(dynamic, 16)
-    for (int64_t k = 0; k < nr; k++) {
+    for (int64_t k = 0; k < L->nr; k++) {
         cplx zk = z[k];
         for (int s = 0; s < 8; s++) {
-            cplx F = lens_F(x, y, m, n, kappa_s, gamma, e, zk);
-            cplx dF = lens_dF(x, y, m, n, zk);
+            cplx F = lens_F(L, e, zk);
+            cplx dF = lens_dF(L, zk);
             if (F == 0.0 || dF == 0.0) break;
             cplx d = F / dF;
             zk -= d;
@@ -191,13 +357,19 @@ static void newton_polish(const double* x, const double* y, const double* m, int
 }
 
 /* Initial guesses z_i + 1 and z_i - 1 for every star (Sec. 3.2), stored as
- * [2i] = z_i + 1, [2i+1] = z_i - 1.  A guess that coincides (within 1e-12) with an
- * earlier one is moved by 1e-6 (1 + i) so that the Aberth root sum stays finite. */
-static void initial_guesses(const double* x, const double* y, int64_t n, cplx* z) {
-    int64_t nr = 2 * n;
+ * [2i] = z_i + 1, [2i+1] = z_i - 1; for the rectangle, the t - 1 further roots start
+ * evenly spread on the circle of radius |c| around the field (Sec. 3.2), at angles
+ * 2 pi (k + 1/2) / (t - 1).  A guess that coincides (within 1e-12) with an earlier one is
+ * moved by 1e-6 (1 + i) so that the Aberth root sum stays finite. */
+static void initial_guesses(const lens_t* L, cplx* z) {
+    int64_t nr = L->nr, n = L->n;
     for (int64_t i = 0; i < n; i++) {
-        z[2 * i] = (x[i] + 1.0) + I * y[i];
-        z[2 * i + 1] = (x[i] - 1.0) + I * y[i];
+        z[2 * i] = (L->x[i] + 1.0) + I * L->y[i];
+        z[2 * i + 1] = (L->x[i] - 1.0) + I * L->y[i];
+    }
+    for (int64_t k = 2 * n; k < nr; k++) {
+        double a = 2.0 * ORC_PI * ((double)(k - 2 * n) + 0.5) / (double)(nr - 2 * n);
+        z[k] = cabs(L->c) * (cos(a) + I * sin(a));
     }
     for (int64_t b = 1; b < nr; b++) {
         int moved = 1;
@@ -213,69 +385,105 @@ static void initial_guesses(const double* x, const double* y, int64_t n, cplx* z
     }
 }
 
-/* Solve one phi row from a given start (warm) or from the star guesses (z_in == NULL),
- * then Newton-polish.  Output: z_out[2n] complex.  Returns the unfrozen count.
+/* Solve one phi row from a given start (warm) or from the initial guesses (z_in == NULL),
+ * then Newton-polish.  Output: z_out[n_r] complex.  Returns the unfrozen count.
  * A warm start assumes a small phase step (Sec. 3.2); when it does not converge within
  * max_iter (e.g. a phase step of pi for an isolated star, whose warm start then lies on a
- * line the iteration never leaves), the row is solved again from the star guesses. */
+ * line the iteration never leaves), the row is solved again from the initial guesses. */
+static int64_t solve_row(const lens_t* L, double phi, const double* z_in, double* z_out, int max_iter, double tol,
+                         int32_t* iters) {
+    cplx* z = (cplx*)z_out;
+    if (z_in)
+        memcpy(z, z_in, sizeof(cplx) * (size_t)L->nr);
+    else
+        initial_guesses(L, z);
+    int64_t left = aberth_jacobi(L, phi, z, max_iter, tol, iters);
+    if (left > 0 && z_in) {
+        initial_guesses(L, z);
+        left = aberth_jacobi(L, phi, z, max_iter, tol, iters);
+    }
+    newton_polish(L, phi, z);
+    return left;
+}
+
 int64_t orc_solve_row(const double* x, const double* y, const double* m, int64_t n,
                       double kappa_s, double gamma, double phi, const double* z_in,
                       double* z_out, int max_iter, double tol, int32_t* iters) {
-    int64_t nr = 2 * n;
-    cplx* z = (cplx*)z_out;
-    if (z_in)
-        memcpy(z, z_in, sizeof(cplx) * (size_t)nr);
-    else
-        initial_guesses(x, y, n, z);
-    int64_t left = aberth_jacobi(x, y, m, n, kappa_s, gamma, phi, z, max_iter, tol, iters);
-    if (left > 0 && z_in) {
-        initial_guesses(x, y, n, z);
-        left = aberth_jacobi(x, y, m, n, kappa_s, gamma, phi, z, max_iter, tol, iters);
-    }
-    newton_polish(x, y, m, n, kappa_s, gamma, phi, z, nr);
-    return left;
+    lens_t L = disc_lens(x, y, m, n, kappa_s, gamma);
+    return solve_row(&L, phi, z_in, z_out, max_iter, tol, iters);
+}
+
+int64_t orc_rect_solve_row(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
+                           double gamma, double kappa_star, double c1, double c2, int t, double phi,
+                           const double* z_in, double* z_out, int max_iter, double tol, int32_t* iters) {
+    lens_t L = rect_lens(x, y, m, n, kappa_s, gamma, kappa_star, c1, c2, t);
+    return solve_row(&L, phi, z_in, z_out, max_iter, tol, iters);
 }
 
 /* phi_j = 2 pi j / m for the (m+1)-row chain matrix (Sec. 4.3). */
 double orc_phi(int64_t j, int64_t msteps) { return 2.0 * ORC_PI * (double)j / (double)msteps; }
 
 /* Chain matrix of Sec. 4.3: rows j = 0..m (m even) hold the n_r roots at phi_j.  The
- * central row m/2 (phi = pi) starts from the star guesses (cap max_iter_cold); the
+ * central row m/2 (phi = pi) starts from the initial guesses (cap max_iter_cold); the
  * matrix then grows toward rows 0 and m, each row warm-started from its neighbour
  * nearer the centre (Sec. 3.2 last paragraph), cap max_iter_warm.
- * z_out: (m+1) x 2n complex; iters_out (optional): (m+1) x 2n.
+ * z_out: (m+1) x n_r complex; iters_out (optional): (m+1) x n_r.
  * Returns the total number of unfrozen roots over all rows (0 = all converged). */
+static int64_t critical_curves(const lens_t* L, int64_t msteps, double tol, int max_iter_cold, int max_iter_warm,
+                               double* z_out, int32_t* iters_out) {
+    int64_t nr = L->nr;
+    int64_t c = msteps / 2;
+    int64_t bad = 0;
+    double* zr = z_out;
+    bad += solve_row(L, orc_phi(c, msteps), NULL, zr + 2 * nr * c, max_iter_cold, tol,
+                     iters_out ? iters_out + nr * c : NULL);
+    for (int64_t j = c - 1; j >= 0; j--)
+        bad += solve_row(L, orc_phi(j, msteps), zr + 2 * nr * (j + 1), zr + 2 * nr * j, max_iter_warm, tol,
+                         iters_out ? iters_out + nr * j : NULL);
+    for (int64_t j = c + 1; j <= msteps; j++)
+        bad += solve_row(L, orc_phi(j, msteps), zr + 2 * nr * (j - 1), zr + 2 * nr * j, max_iter_warm, tol,
+                         iters_out ? iters_out + nr * j : NULL);
+    return bad;
+}
+
 int64_t orc_critical_curves(const double* x, const double* y, const double* m, int64_t n,
                             double kappa_s, double gamma, int64_t msteps, double tol,
                             int max_iter_cold, int max_iter_warm, double* z_out,
                             int32_t* iters_out) {
-    int64_t nr = 2 * n;
-    int64_t c = msteps / 2;
-    int64_t bad = 0;
-    double* zr = z_out;
-    bad += orc_solve_row(x, y, m, n, kappa_s, gamma, orc_phi(c, msteps), NULL, zr + 2 * nr * c,
-                         max_iter_cold, tol, iters_out ? iters_out + nr * c : NULL);
-    for (int64_t j = c - 1; j >= 0; j--)
-        bad += orc_solve_row(x, y, m, n, kappa_s, gamma, orc_phi(j, msteps),
-                             zr + 2 * nr * (j + 1), zr + 2 * nr * j, max_iter_warm, tol,
-                             iters_out ? iters_out + nr * j : NULL);
-    for (int64_t j = c + 1; j <= msteps; j++)
-        bad += orc_solve_row(x, y, m, n, kappa_s, gamma, orc_phi(j, msteps),
-                             zr + 2 * nr * (j - 1), zr + 2 * nr * j, max_iter_warm, tol,
-                             iters_out ? iters_out + nr * j : NULL);
-    return bad;
+    lens_t L = disc_lens(x, y, m, n, kappa_s, gamma);
+    return critical_curves(&L, msteps, tol, max_iter_cold, max_iter_warm, z_out, iters_out);
+}
+
+int64_t orc_rect_critical_curves(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
+                                 double gamma, double kappa_star, double c1, double c2, int t, int64_t msteps,
+                                 double tol, int max_iter_cold, int max_iter_warm, double* z_out,
+                                 int32_t* iters_out) {
+    lens_t L = rect_lens(x, y, m, n, kappa_s, gamma, kappa_star, c1, c2, t);
+    return critical_curves(&L, msteps, tol, max_iter_cold, max_iter_warm, z_out, iters_out);
 }
 
 /* Caustic mapping (Sec. 3.1, Sec. 5.1): w = lens map of each critical point. */
-void orc_map_caustics(const double* x, const double* y, const double* m, int64_t n,
-                      double kappa_s, double gamma, const double* z, int64_t count,
-                      double* w_out) {
+static void map_caustics(const lens_t* L, const double* z, int64_t count, double* w_out) {
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < count; p++) {
-        cplx w = lens_w(x, y, m, n, kappa_s, gamma, z[2 * p] + I * z[2 * p + 1]);
+        cplx w = lens_w(L, z[2 * p] + I * z[2 * p + 1]);
         w_out[2 * p] = creal(w);
         w_out[2 * p + 1] = cimag(w);
     }
+}
+
+void orc_map_caustics(const double* x, const double* y, const double* m, int64_t n,
+                      double kappa_s, double gamma, const double* z, int64_t count,
+                      double* w_out) {
+    lens_t L = disc_lens(x, y, m, n, kappa_s, gamma);
+    map_caustics(&L, z, count, w_out);
+}
+
+void orc_rect_map_caustics(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
+                           double gamma, double kappa_star, double c1, double c2, int t, const double* z,
+                           int64_t count, double* w_out) {
+    lens_t L = rect_lens(x, y, m, n, kappa_s, gamma, kappa_star, c1, c2, t);
+    map_caustics(&L, z, count, w_out);
 }
 
 /* Smallest pairwise distance among the n_r roots of one row (distinctness check). */
