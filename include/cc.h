@@ -62,6 +62,17 @@ typedef enum cc_hp_arith {
     CC_HP_FP64 = 1    /* native FP64 */
 } cc_hp_arith;
 
+/* Shape of the microlens field (Sec. 4.2, Appendices A and B).
+ *   CC_FIELD_DISC  circular field; its smooth sheet is extended to infinity (Appendix A):
+ *                  alpha_s = -kappa_* z, n_r = 2N roots per phi.
+ *   CC_FIELD_RECT  rectangular field |Re z| <= c1, |Im z| <= c2 (the stars should lie in it)
+ *                  with the logarithms of alpha_s replaced by their series truncated at the
+ *                  odd order t and the sheet extended to infinity (Appendix B): F gains
+ *                  -conj(dalpha_s/dconj z), a polynomial of degree t - 1 in z, and the
+ *                  lens map gains the matching odd polynomial in conj(z); n_r = 2N + t - 1. */
+typedef enum cc_field_shape { CC_FIELD_DISC = 0, CC_FIELD_RECT = 1 } cc_field_shape;
+#define CC_RECT_MAX_T 129
+
 typedef struct cc_options {
     double tol_abs;      /* freeze a root when |z^{a+1} - z^a| < tol_abs (Sec. 3.2 footnote: 1e-9) */
     double mu_max;       /* also freeze when |mu| > mu_max (Sec. 3.2 footnote: 1e9); 0 = off.
@@ -74,18 +85,29 @@ typedef struct cc_options {
     int32_t precision;     /* cc_precision */
     int32_t hp_arith;      /* cc_hp_arith (polish and cc_map_caustics) */
     int32_t subchains;     /* phi sub-ranges grown in parallel (Sec. 4.3); 0 = automatic */
-    int32_t predictor;     /* 1: warm start by linear extrapolation of the last two rows; 0: copy
-                              the previous row (Sec. 3.2 last paragraph) */
+    int32_t predictor;     /* warm start of a row (Sec. 3.2 last paragraph) from the rows before it
+                              on its chain: 0 copies the previous row, 1 extrapolates linearly
+                              through the last two, 2 quadratically through the last three */
     int32_t block_threads; /* threads per tracing CTA (0 = automatic) */
     int32_t far_field;     /* 1: polish stars beyond a 5x5 block of cells through local expansions
                               (Sec. 4.1, fast multipole method; used when N >= 128 and hp_arith is
                               CC_HP_DFLOAT); 0: every star summed directly */
+    /* Shape of the microlens field and its smooth sheet (Sec. 4.2, Appendices A and B). */
+    int32_t field_shape;   /* cc_field_shape: CC_FIELD_DISC (default) or CC_FIELD_RECT */
+    int32_t rect_t;        /* CC_FIELD_RECT: odd truncation order t >= 3 of the logarithm series of
+                              alpha_s, at most CC_RECT_MAX_T; 0 = the Appendix B rule (the smallest
+                              odd t whose error bound is <= rect_eps for |z| rect_s < |c|, then
+                              t + 2 while (t - 1) Arg(c) lies within 0.1 pi of a multiple of pi) */
+    double kappa_star;     /* CC_FIELD_RECT: convergence of the stars' smooth sheet, kappa_* > 0 */
+    double rect_c1, rect_c2; /* CC_FIELD_RECT: corner c = c1 + i c2 of the field (half-width,
+                              half-height, both > 0) */
+    double rect_eps, rect_s; /* CC_FIELD_RECT, rect_t == 0: error target (1e-9) and ratio s > 1 (2) */
 } cc_options;
 
 /* Solve statistics of the last cc_critical_curves on a field (host copy). */
 typedef struct cc_report {
     int64_t rows;              /* m + 1 */
-    int64_t n_roots;           /* n_r = 2N */
+    int64_t n_roots;           /* n_r = 2N (disc) or 2N + t - 1 (rectangle) */
     int64_t subchains;         /* sub-ranges used */
     int64_t root_iterations;   /* Aberth updates executed (all rows, all roots) */
     int64_t cold_root_iterations; /* of which at the subchain centre rows */

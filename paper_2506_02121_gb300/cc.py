@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_HERE, "libccgpu.so")
 CC_OK, CC_EINVAL, CC_ENOMEM, CC_ENOCONV, CC_EDEGENERATE, CC_ECUDA, CC_ETIMEOUT = range(7)
 CC_MIXED, CC_FP64 = 0, 1
 CC_HP_DFLOAT, CC_HP_FP64 = 0, 1
+CC_FIELD_DISC, CC_FIELD_RECT = 0, 1
+CC_RECT_MAX_T = 129
 _NAMES = {0: "CC_OK", 1: "CC_EINVAL", 2: "CC_ENOMEM", 3: "CC_ENOCONV", 4: "CC_EDEGENERATE", 5: "CC_ECUDA",
           6: "CC_ETIMEOUT"}
 
@@ -37,7 +39,9 @@ class Options(ctypes.Structure):
                 ("max_iter_cold", ctypes.c_int32), ("max_iter_warm", ctypes.c_int32),
                 ("max_polish", ctypes.c_int32), ("precision", ctypes.c_int32), ("hp_arith", ctypes.c_int32),
                 ("subchains", ctypes.c_int32), ("predictor", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("far_field", ctypes.c_int32)]
+                ("far_field", ctypes.c_int32), ("field_shape", ctypes.c_int32), ("rect_t", ctypes.c_int32),
+                ("kappa_star", ctypes.c_double), ("rect_c1", ctypes.c_double), ("rect_c2", ctypes.c_double),
+                ("rect_eps", ctypes.c_double), ("rect_s", ctypes.c_double)]
 
 
 class Report(ctypes.Structure):
@@ -133,13 +137,26 @@ def cc_options_default() -> Options:
     return o
 
 
+def rect_options(kappa_star: float, c1: float, c2: float, t: int = 0, base: Options | None = None) -> Options:
+    """Options for a rectangular microlens field |Re z| <= c1, |Im z| <= c2 (Sec. 4.2) whose
+    smooth sheet has convergence kappa_star; t = 0 picks the truncation order by the
+    Appendix B rule."""
+    o = cc_options_default() if base is None else base
+    o.field_shape = CC_FIELD_RECT
+    o.kappa_star = float(kappa_star)
+    o.rect_c1 = float(c1)
+    o.rect_c2 = float(c2)
+    o.rect_t = int(t)
+    return o
+
+
 class Field:
     """Owner of a cc_field handle (stars resident on the device)."""
 
-    def __init__(self, handle, n):
+    def __init__(self, handle, n, n_roots):
         self._h = handle
         self.n = n
-        self.n_roots = 2 * n
+        self.n_roots = n_roots  # 2N (disc) or 2N + t - 1 (rectangular field)
 
     @property
     def handle(self):
@@ -170,7 +187,9 @@ def cc_field_create(x, y, mass, kappa_s: float, gamma: float, opt: Options | Non
     h = ctypes.c_void_p()
     _check(_lib.cc_field_create(_ptr(tx), _ptr(ty), _ptr(tm), n, float(kappa_s), float(gamma),
                                 ctypes.byref(opt) if opt is not None else None, ctypes.byref(h)))
-    return Field(h, n)
+    ns, nr = _i64(), _i64()
+    _check(_lib.cc_field_size(h, ctypes.byref(ns), ctypes.byref(nr)))
+    return Field(h, n, nr.value)
 
 
 def cc_field_destroy(field: Field):

@@ -94,6 +94,7 @@ __device__ __forceinline__ T shfl_x(T v, int off) {
 
 struct TK {
     const void* stars;
+    const SmoothPoly* poly;  // rectangular field: smooth-sheet polynomial; nullptr for the disc
     int n, nr;
     double kappa_s, gamma;
     int64_t m;
@@ -121,7 +122,7 @@ struct Ctx {
     const TK* k;
     Star* s_star;
     C* s_root;  // [2][TR]
-    C *cur, *nxt, *prev;
+    C *cur, *nxt, *prev, *prev2;  // prev, prev2: the two rows before cur on this direction
     float* dprev;
     int *conv, *it, *act;
     bool resident;
@@ -214,13 +215,34 @@ __device__ __forceinline__ void finish_root(const Ctx<T>& x, int key, typename C
     const TK& K = *x.k;
     const T oms = (T)(1.0 - K.kappa_s);
     const T gam = (T)K.gamma;
-    // F = gamma + A - (1 - kappa_s) e^{-i phi}
-    const T Fx = gam + acc.Ax - oms * cph;
-    const T Fy = acc.Ay + oms * sph;
+    // F = gamma + A - Q(z) - (1 - kappa_s) e^{-i phi},  F' = -2 B - Q'(z)  (Q = 0 for the disc)
+    T Fx = gam + acc.Ax - oms * cph;
+    T Fy = acc.Ay + oms * sph;
+    T dFx = (T)-2 * acc.Bx, dFy = (T)-2 * acc.By;
+    T qa = 0, sca = 1;  // |common scale| of F, F' (FP32 rectangle far out: see poly_eval_scaled)
+    if (K.poly) {
+        if constexpr (sizeof(T) == 4) {
+            float Qx, Qy, Q1x, Q1y, scx, scy;
+            poly_eval_scaled(K.poly, z.x, z.y, Qx, Qy, Q1x, Q1y, scx, scy, qa);
+            const T fx = Fx * scx - Fy * scy, fy = Fx * scy + Fy * scx;
+            const T gx = dFx * scx - dFy * scy, gy = dFx * scy + dFy * scx;
+            Fx = fx - Qx;
+            Fy = fy - Qy;
+            dFx = gx - Q1x;
+            dFy = gy - Q1y;
+            sca = sqrtf(scx * scx + scy * scy);
+        } else {
+            T Qx, Qy, Q1x, Q1y, Q2x, Q2y;
+            poly_eval<T>(K.poly, z.x, z.y, Qx, Qy, Q1x, Q1y, Q2x, Q2y, qa);
+            Fx -= Qx;
+            Fy -= Qy;
+            dFx -= Q1x;
+            dFy -= Q1y;
+        }
+    }
     C zn = z;
     T ad = 0;
     if (Fx != (T)0 || Fy != (T)0) {
-        const T dFx = (T)-2 * acc.Bx, dFy = (T)-2 * acc.By;
         const T fden = Fx * Fx + Fy * Fy;
         const T qx = qdiv(dFx * Fx + dFy * Fy, fden);
         const T qy = qdiv(dFy * Fx - dFx * Fy, fden);
@@ -241,17 +263,20 @@ __device__ __forceinline__ void finish_root(const Ctx<T>& x, int key, typename C
         // few ulp of |z|, or the FP32 noise of F (~eps sum |m/d^2|) divided by |F'|; or when
         // the corrections stop shrinking within a few times that floor.
         const T sc = (T)1 + qsqrt(z.x * z.x + z.y * z.y);
-        const T fpa = (T)2 * qsqrt(acc.Bx * acc.Bx + acc.By * acc.By);
-        const T noise = (T)(4.0 * FLT_EPSILON) * (acc.Am + fabs(gam) + oms);
+        const T fpa = qsqrt(dFx * dFx + dFy * dFy);
+        const T noise = (T)(4.0 * FLT_EPSILON) * (sca * (acc.Am + fabs(gam) + oms) + qa);
         T tolz = fmax((T)K.tol_abs, (T)(8.0 * FLT_EPSILON) * sc);
         if (fpa > (T)0) tolz = fmax(tolz, (T)4 * noise * qdiv((T)1, fpa));
         // never looser than 64x the ulp floor: an iterate that runs away where F' vanishes
         // must not count as converged
         tolz = fmin(tolz, (T)(512.0 * FLT_EPSILON) * sc);
-        done = !(ad >= tolz) || (its >= 3 && ad > (T)0.25 * (T)x.dprev[key] && ad < (T)4 * tolz);
+        // a non-finite step (ad NaN) never freezes a root: it would poison every root sum
+        done = ad < tolz || (its >= 3 && ad > (T)0.25 * (T)x.dprev[key] && ad < (T)4 * tolz);
+        if (!(ad == ad)) zn = z;
     } else {
-        done = !(ad >= (T)K.tol_abs);
-        if (!done && K.mu_max > 0) {
+        done = ad < (T)K.tol_abs;
+        if (!(ad == ad)) zn = z;
+        if (!done && K.mu_max > 0 && !K.poly) {
             const T gx = gam + acc.Ax, gy = acc.Ay;
             const T detj = oms * oms - (gx * gx + gy * gy);
             done = fabs((double)detj) * K.mu_max < 1.0;
@@ -503,7 +528,24 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
     const TK& K = *x.k;
     const int nr = K.nr;
     const Star* gs = (const Star*)K.stars;
+    const int n2 = 2 * K.n;
     for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+        const int key = d * nr + k;
+        if (k >= n2) {
+            // rectangular field: the t - 1 further roots start evenly spread on the circle of
+            // radius |c| around the field (Sec. 3.2), at angles 2 pi (k - 2N + 1/2) / (t - 1)
+            const float a = 6.2831853f * ((float)(k - n2) + 0.5f) / (float)(nr - n2);
+            float sa, ca;
+            __sincosf(a, &sa, &ca);  // a starting guess: the fast intrinsic is accurate enough
+            C z;
+            z.x = (T)(K.poly->rg * (double)ca);
+            z.y = (T)(K.poly->rg * (double)sa);
+            x.cur[key] = z;
+            x.conv[key] = 0;
+            x.it[key] = 0;
+            x.dprev[key] = FLT_MAX;
+            continue;
+        }
         const Star si = gs[k >> 1];
         const T sg = (k & 1) ? (T)-1 : (T)1;
         const T gx = (T)si.x + sg, gy = (T)si.y + sg * (T)0.015625;
@@ -517,7 +559,6 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
         C z;
         z.x = gx + (T)1e-3 * (T)dup;
         z.y = gy + (T)1e-3 * (T)dup;
-        const int key = d * nr + k;
         x.cur[key] = z;
         x.conv[key] = 0;
         x.it[key] = 0;
@@ -548,7 +589,8 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     x.cur = (C*)w;
     x.nxt = x.cur + 2 * nr;
     x.prev = x.nxt + 2 * nr;
-    x.dprev = (float*)(x.prev + 2 * nr);
+    x.prev2 = x.prev + 2 * nr;
+    x.dprev = (float*)(x.prev2 + 2 * nr);
     x.conv = (int*)(x.dprev + 2 * nr);
     x.it = x.conv + 2 * nr;
     x.act = x.it + 2 * nr;
@@ -576,6 +618,9 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             K.iters[(size_t)c * nr + k] = x.it[k];
         }
     }
+    // hist[d]: rows of direction d already behind the current one that belong to the same
+    // chains (a row re-solved from the star guesses has new column labels: history restarts)
+    int hist[2] = {0, 0};
     for (int64_t t = 1;; t++) {
         const bool a0 = c - t >= b0, a1 = c + t <= b1;
         if (!a0 && !a1) break;
@@ -587,13 +632,20 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
                 x.conv[k] = 1;
                 continue;
             }
+            const int h = hist[k < nr ? 0 : 1];
             const C zc = x.cur[k];
             C g = zc;
-            if (t >= 2 && K.predictor) {
+            if (K.predictor >= 2 && h >= 2) {
+                // quadratic extrapolation through the last three rows: 3 z_c - 3 z_p + z_pp
+                const C zp = x.prev[k], zpp = x.prev2[k];
+                g.x = zpp.x + (T)3 * (zc.x - zp.x);
+                g.y = zpp.y + (T)3 * (zc.y - zp.y);
+            } else if (K.predictor >= 1 && h >= 1) {
                 const C zp = x.prev[k];
                 g.x = zc.x + (zc.x - zp.x);
                 g.y = zc.y + (zc.y - zp.y);
             }
+            if (h >= 1) x.prev2[k] = x.prev[k];
             x.prev[k] = zc;
             x.cur[k] = g;
             x.conv[k] = 0;
@@ -601,6 +653,10 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             x.dprev[k] = FLT_MAX;
         }
         const int bad = solve_rows<T>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit);
+        if (a0) hist[0] = min(hist[0] + 1, 2);
+        if (a1) hist[1] = min(hist[1] + 1, 2);
+        if (bad & 1) hist[0] = 0;
+        if (bad & 2) hist[1] = 0;
         if (bad) {
             // A warm start that does not settle (e.g. a phase step so large that the previous
             // row sits on a symmetric, non-converging configuration) restarts that row from
@@ -665,6 +721,7 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
         const TraceTask& t = B.tasks[fs.x];
         TK K;
         K.stars = t.stars;
+        K.poly = t.poly;
         K.n = t.n;
         K.nr = t.nr;
         K.kappa_s = t.kappa_s;
@@ -709,7 +766,7 @@ size_t tracer_smem_bytes(bool fp64) {
 }
 
 size_t tracer_work_stride(int64_t nr, size_t elem) {
-    size_t b = (size_t)(2 * nr) * (3 * elem + 4 * 4);
+    size_t b = (size_t)(2 * nr) * (4 * elem + 4 * 4);
     return (b + 255) / 256 * 256;
 }
 
@@ -750,7 +807,8 @@ int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms, int bloc
 cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
     TK K;
     K.n = (int)a.f->n;
-    K.nr = (int)(2 * a.f->n);
+    K.nr = (int)a.f->nr;
+    K.poly = a.f->poly;
     K.stars = fp64 ? (const void*)a.f->star64 : (const void*)a.f->star32;
     K.kappa_s = a.f->kappa_s;
     K.gamma = a.f->gamma;
@@ -946,12 +1004,20 @@ __global__ void __launch_bounds__(256) rescue_kernel(RescueTask t0, const Rescue
             By = warp_sum_d(By);
             Dx = warp_sum_d(Dx);
             Dy = warp_sum_d(Dy);
-            const double Fx = t.gamma + Ax - oms * ph.x, Fy = Ay + oms * ph.y;
+            double Fx = t.gamma + Ax - oms * ph.x, Fy = Ay + oms * ph.y;
+            double dFx = -2.0 * Bx, dFy = -2.0 * By;
+            if (t.poly) {
+                double Qx, Qy, Q1x, Q1y, Q2x, Q2y, qa;
+                poly_eval<double>(t.poly, zx, zy, Qx, Qy, Q1x, Q1y, Q2x, Q2y, qa);
+                Fx -= Qx;
+                Fy -= Qy;
+                dFx -= Q1x;
+                dFy -= Q1y;
+            }
             if (Fx == 0.0 && Fy == 0.0) {
                 conv = true;
                 break;
             }
-            const double dFx = -2.0 * Bx, dFy = -2.0 * By;
             const double fd = Fx * Fx + Fy * Fy;
             const double px = (dFx * Fx + dFy * Fy) / fd + 2.0 * Cx - Dx;
             const double py = (dFy * Fx - dFx * Fy) / fd + 2.0 * Cy - Dy;
@@ -974,7 +1040,15 @@ __global__ void __launch_bounds__(256) rescue_kernel(RescueTask t0, const Rescue
         Sy = warp_sum_d(Sy);
         if (lane == 0) {
             t.z[(size_t)row * nr + col] = make_double2(zx, zy);
-            if (t.w) t.w[(size_t)row * nr + col] = make_double2(oms * zx + t.gamma * zx - Sx, oms * zy - t.gamma * zy + Sy);
+            double Vx = 0.0, Vy = 0.0;
+            if (t.poly) {
+                const double2 V = poly_V(t.poly, zx, zy);
+                Vx = V.x;
+                Vy = V.y;
+            }
+            if (t.w)
+                t.w[(size_t)row * nr + col] =
+                    make_double2(oms * zx + t.gamma * zx - Sx + Vx, oms * zy - t.gamma * zy + Sy + Vy);
             if (conv) {
                 atomicAdd(&t.rep->uncertified, (unsigned long long)(-1LL));
                 atomicAdd(&t.rep->rescued_points, 1ull);

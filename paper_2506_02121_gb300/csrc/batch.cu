@@ -155,11 +155,11 @@ int cc_batch_create(cc_field* const* fields, int32_t count, const int64_t* m, in
         b->fields.push_back(fields[f]);
         b->dev.push_back(*fd);
         b->m.push_back(m[f]);
-        b->nr.push_back(2 * fd->n);
+        b->nr.push_back(fd->nr);
         b->rows.push_back(m[f] + 1);
-        cost[f] = (double)(m[f] + 1) * (double)(2 * fd->n) * (double)(3 * fd->n);
+        cost[f] = (double)(m[f] + 1) * (double)fd->nr * (double)(fd->n + fd->nr);
         total_cost += cost[f];
-        b->max_nr = std::max<int>(b->max_nr, (int)(2 * fd->n));
+        b->max_nr = std::max<int>(b->max_nr, (int)fd->nr);
         b->max_m = std::max<int64_t>(b->max_m, m[f]);
     }
     cudaError_t e = cudaSetDevice(b->device);
@@ -283,6 +283,7 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         const FieldDev& fd = b->dev[f];
         TraceTask& t = tasks[f];
         t.stars = fd.star32;
+        t.poly = fd.poly;
         t.tfmm = fd.tfmm;
         t.tcells = fd.tcells;
         t.tnear = fd.tnear;
@@ -302,8 +303,8 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         t.perm = (int32_t*)(ws + b->off_perm[f]);
         t.rep = (DevReport*)(ws + b->off_reps) + f;
         for (int s = 0; s + 1 < b->S[f]; s++) seams.push_back(make_int2(f, s));
-        const double cost = (double)b->rows[f] * (double)b->nr[f] * (double)(3 * fd.n);
-        const double per = cost / (double)b->S[f] + 20.0 * (double)b->nr[f] * (double)(3 * fd.n);
+        const double cost = (double)b->rows[f] * (double)b->nr[f] * (double)(fd.n + b->nr[f]);
+        const double per = cost / (double)b->S[f] + 20.0 * (double)b->nr[f] * (double)(fd.n + b->nr[f]);
         for (int s = 0; s < b->S[f]; s++) items.push_back({per, make_int2(f, s)});
         PolishArgs pa;
         pa.f = &b->dev[f];
@@ -334,6 +335,7 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         }
         RescueTask& rt = rtasks[f];
         rt.stars = fd.star64;
+        rt.poly = fd.poly;
         rt.n = (int)fd.n;
         rt.nr = (int)b->nr[f];
         rt.kappa_s = fd.kappa_s;

@@ -80,7 +80,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 // Workspace layout of cc_critical_curves.
 CurveLayout curve_layout(const cc_field* f, int64_t m) {
     CurveLayout L;
-    const int64_t nr = 2 * f->dev.n;
+    const int64_t nr = f->dev.nr;
     const bool fp64 = f->opt.precision == CC_FP64;
     L.elem = fp64 ? sizeof(double2) : sizeof(float2);
     L.threads = f->opt.block_threads > 0 ? f->opt.block_threads : 512;
@@ -163,8 +163,62 @@ int cc_options_default(cc_options* opt) {
     opt->predictor = 1;
     opt->block_threads = 0;
     opt->far_field = 1;
+    opt->field_shape = CC_FIELD_DISC;
+    opt->rect_t = 0;
+    opt->kappa_star = 0.0;
+    opt->rect_c1 = 0.0;
+    opt->rect_c2 = 0.0;
+    opt->rect_eps = 1e-9;
+    opt->rect_s = 2.0;
     return CC_OK;
 }
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Truncation order of the rectangle's logarithm series (Appendix B): the smallest odd
+// t >= 3 whose bound (kappa_*/pi) (4/(t+1)) s^-(t+1) |c| (s+1)/(s-1) on the error of alpha_s
+// for |z| s < |c| is <= eps, then t + 2 while (t - 1) Arg(c) is within 0.1 pi of a
+// multiple of pi (the leading coefficient of the polynomial vanishes or nearly so).
+int rect_order(double kappa_star, double c1, double c2, double eps, double s) {
+    const double ac = std::hypot(c1, c2), th = std::atan2(c2, c1);
+    int t = 3;
+    while (t <= CC_RECT_MAX_T &&
+           (kappa_star / kPi) * (4.0 / (t + 1)) * std::pow(s, -(double)(t + 1)) * ac * (s + 1.0) / (s - 1.0) > eps)
+        t += 2;
+    for (; t <= CC_RECT_MAX_T; t += 2) {
+        const double r = std::fmod((t - 1) * th, kPi);
+        if (r > 0.1 * kPi && r < 0.9 * kPi) break;
+    }
+    return t;
+}
+
+// Coefficients of the rectangle's smooth-sheet polynomial, normalised by |c|.
+void rect_poly(double kappa_star, double c1, double c2, int t, SmoothPoly& P) {
+    std::memset(&P, 0, sizeof P);
+    const double ac = std::hypot(c1, c2), th = std::atan2(c2, c1);
+    P.K = (t - 1) / 2;
+    P.ac = ac;
+    P.inv_ac = 1.0 / ac;
+    P.acf = (float)ac;
+    P.inv_acf = (float)(1.0 / ac);
+    P.inv_acdf = make_float2((float)(1.0 / ac), (float)(1.0 / ac - (double)(float)(1.0 / ac)));
+    P.rg = ac;
+    for (int k = 0; k <= P.K; k++) {
+        const double q = k == 0 ? kappa_star * (1.0 - 4.0 * th / kPi)
+                                : -(4.0 * kappa_star / kPi) * std::sin(2.0 * k * th) / (2.0 * k);
+        const double v = q / (2.0 * k + 1.0);
+        P.q[k] = q;
+        P.v[k] = v;
+        P.qf[k] = (float)q;
+        const float qh = (float)q, vh = (float)v;
+        P.qdf[k] = make_float2(qh, (float)(q - (double)qh));
+        P.vdf[k] = make_float2(vh, (float)(v - (double)vh));
+    }
+}
+
+}  // namespace
 
 int cc_field_create(const double* x, const double* y, const double* mass, int64_t n, double kappa_s,
                     double gamma, const cc_options* opt, cc_field** out) {
@@ -174,18 +228,43 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
     if (n < 1 || n > (int64_t)1 << 26) return fail(CC_EINVAL, "cc_field_create: n = %lld out of range [1, 2^26]", (long long)n);
     if (!std::isfinite(kappa_s) || !std::isfinite(gamma))
         return fail(CC_EINVAL, "cc_field_create: kappa_s and gamma must be finite");
-    if (std::fabs(1.0 - kappa_s) < 1e-12 || std::fabs(std::fabs(1.0 - kappa_s) - std::fabs(gamma)) < 1e-12)
-        return fail(CC_EDEGENERATE,
-                    "cc_field_create: |1 - kappa_s| = |gamma| (or 1 - kappa_s = 0): a critical point runs to infinity");
     cc_options o;
     cc_options_default(&o);
     if (opt) o = *opt;
+    if (o.field_shape != CC_FIELD_DISC && o.field_shape != CC_FIELD_RECT)
+        return fail(CC_EINVAL, "cc_field_create: field_shape must be CC_FIELD_DISC or CC_FIELD_RECT");
+    if (std::fabs(1.0 - kappa_s) < 1e-12 ||
+        (o.field_shape == CC_FIELD_DISC && std::fabs(std::fabs(1.0 - kappa_s) - std::fabs(gamma)) < 1e-12))
+        return fail(CC_EDEGENERATE,
+                    "cc_field_create: |1 - kappa_s| = |gamma| (or 1 - kappa_s = 0): a critical point runs to infinity");
+    SmoothPoly hpoly;
+    std::memset(&hpoly, 0, sizeof hpoly);
+    bool rect = o.field_shape == CC_FIELD_RECT;
+    if (rect) {
+        if (!(o.kappa_star > 0) || !std::isfinite(o.kappa_star) || !(o.rect_c1 > 0) || !(o.rect_c2 > 0) ||
+            !std::isfinite(o.rect_c1) || !std::isfinite(o.rect_c2))
+            return fail(CC_EINVAL, "cc_field_create: a rectangular field needs kappa_star > 0 and corner c1, c2 > 0");
+        int t = o.rect_t;
+        if (t == 0) {
+            if (!(o.rect_eps > 0) || !(o.rect_s > 1) || !std::isfinite(o.rect_s))
+                return fail(CC_EINVAL, "cc_field_create: rect_eps must be > 0 and rect_s > 1");
+            t = rect_order(o.kappa_star, o.rect_c1, o.rect_c2, o.rect_eps, o.rect_s);
+        }
+        if (t < 3 || !(t & 1) || t > CC_RECT_MAX_T)
+            return fail(CC_EINVAL, "cc_field_create: rect_t = %d must be odd in [3, %d]", t, CC_RECT_MAX_T);
+        if (std::fabs(std::sin((t - 1) * std::atan2(o.rect_c2, o.rect_c1))) < 1e-6)
+            return fail(CC_EDEGENERATE,
+                        "cc_field_create: (t - 1) Arg(c) is a multiple of pi: the sheet polynomial loses its degree");
+        o.rect_t = t;
+        rect_poly(o.kappa_star, o.rect_c1, o.rect_c2, t, hpoly);
+    }
     if (o.precision != CC_MIXED && o.precision != CC_FP64) return fail(CC_EINVAL, "cc_field_create: bad precision");
     if (o.hp_arith != CC_HP_DFLOAT && o.hp_arith != CC_HP_FP64) return fail(CC_EINVAL, "cc_field_create: bad hp_arith");
     if (!(o.tol_abs > 0) || !(o.tol_cert > 0) || o.max_iter_cold < 1 || o.max_iter_warm < 1 || o.max_polish < 1 ||
         o.mu_max < 0 || o.subchains < 0)
         return fail(CC_EINVAL, "cc_field_create: bad options");
     if (o.far_field != 0 && o.far_field != 1) return fail(CC_EINVAL, "cc_field_create: far_field must be 0 or 1");
+    if (o.predictor < 0 || o.predictor > 2) return fail(CC_EINVAL, "cc_field_create: predictor must be 0, 1 or 2");
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 512 || (o.block_threads & 31)))
         return fail(CC_EINVAL, "cc_field_create: block_threads must be 0 or a multiple of 32 in [32, 512]");
 
@@ -234,6 +313,9 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
     f->opt = o;
     f->dev.fmm_cell = fmm_cell;
     f->dev.n = n;
+    f->dev.nr = 2 * n + (rect ? 2 * hpoly.K : 0);
+    f->dev.poly = nullptr;
+    f->dev.poly_K = rect ? hpoly.K : 0;
     f->dev.kappa_s = kappa_s;
     f->dev.gamma = gamma;
     f->dev.unit_mass = unit;
@@ -258,6 +340,14 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
     e = e ? e : cudaMemcpy(f->dev.star_dfm, sdm.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemcpy(f->dev.star_tf, stf.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
     e = e ? e : cudaMemset(f->d_rep, 0, sizeof(DevReport));
+    if (rect && e == cudaSuccess) {
+        SmoothPoly* dp = nullptr;
+        e = cudaMalloc(&dp, sizeof(SmoothPoly));
+        if (e == cudaSuccess) {
+            f->dev.poly = dp;
+            e = cudaMemcpy(dp, &hpoly, sizeof(SmoothPoly), cudaMemcpyHostToDevice);
+        }
+    }
     if (e != cudaSuccess) {
         cc_field_destroy(f);
         return cuda_fail(e, "cc_field_create upload");
@@ -312,6 +402,7 @@ int cc_field_destroy(cc_field* f) {
     cudaFree(f->dev.tcells);
     cudaFree(f->dev.tnear);
     cudaFree(f->dev.tcoeff);
+    cudaFree((void*)f->dev.poly);
     if (f->done) cudaEventDestroy(f->done);
     for (int i = 0; i < 4; i++)
         if (f->ev[i]) cudaEventDestroy(f->ev[i]);
@@ -322,7 +413,7 @@ int cc_field_destroy(cc_field* f) {
 int cc_field_size(const cc_field* f, int64_t* n_stars, int64_t* n_roots) {
     if (!f) return fail(CC_EINVAL, "cc_field_size: field is NULL");
     if (n_stars) *n_stars = f->dev.n;
-    if (n_roots) *n_roots = 2 * f->dev.n;
+    if (n_roots) *n_roots = f->dev.nr;
     return CC_OK;
 }
 
@@ -352,7 +443,7 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
     CC_CUDA(cudaSetDevice(f->device), "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
-    const int64_t nr = 2 * f->dev.n;
+    const int64_t nr = f->dev.nr;
     const bool fp64 = f->opt.precision == CC_FP64;
     DevReport* rep = f->d_rep;
     CC_CUDA(cudaMemsetAsync(rep, 0, sizeof(DevReport), st), "clear report");
@@ -426,6 +517,7 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
             CC_CUDA(launch_polish(pa, st), "polish");
         RescueTask rt;
         rt.stars = f->dev.star64;
+        rt.poly = f->dev.poly;
         rt.n = (int)f->dev.n;
         rt.nr = (int)nr;
         rt.kappa_s = f->dev.kappa_s;
@@ -455,7 +547,7 @@ int cc_field_report(cc_field* f, cc_report* out) {
     CC_CUDA(cudaMemcpy(&r, f->d_rep, sizeof r, cudaMemcpyDeviceToHost), "read report");
     memset(out, 0, sizeof *out);
     out->rows = f->last_m + 1;
-    out->n_roots = 2 * f->dev.n;
+    out->n_roots = f->dev.nr;
     out->subchains = f->last_S;
     out->root_iterations = (int64_t)r.root_iterations;
     out->cold_root_iterations = (int64_t)r.cold_root_iterations;

@@ -30,9 +30,150 @@ struct TCell {
     float far_m_d2;   // sum_far m/|z_i - c|^2 (scale of the far-field rounding noise)
 };
 
+// Smooth-sheet polynomial of a rectangular field (Appendix B): F gains -Q(z),
+//   Q(z) = conj(dalpha_s/dconj z) = sum_{k=0}^{K} q_k z^{2k}  (real q_k, K = (t - 1)/2),
+//   q_0 = kappa_* (1 - 4 Arg(c)/pi),  q_k = -(4 kappa_*/pi) sin(2k Arg c) / (2k |c|^{2k}),
+// and the lens map gains V(conj z) = -sum_k q_k conj(z)^{2k+1} / (2k + 1) (its conj(z)
+// derivative is -conj(Q)); the constant of V is 0.  Both are evaluated in zeta = z / |c|
+// with the O(1) coefficients qn_k = q_k |c|^{2k} (q_k alone underflows FP32 for large |c|):
+//   Q = sum qn_k zeta^{2k},  V = -|c| conj(zeta) sum vn_k conj(zeta)^{2k},  vn_k = qn_k/(2k+1).
+// Device memory, one per field.
+constexpr int POLY_MAX_K = (CC_RECT_MAX_T - 1) / 2;
+struct SmoothPoly {
+    int K;
+    double ac, inv_ac;             // |c| and 1/|c|
+    float acf, inv_acf;
+    float2 inv_acdf;               // 1/|c| as double-float
+    double rg;                     // radius of the extra roots' initial guesses (|c|)
+    float qf[POLY_MAX_K + 1];      // qn_k in FP32 (tracer)
+    double q[POLY_MAX_K + 1];      // qn_k in FP64
+    float2 qdf[POLY_MAX_K + 1];    // qn_k as double-float
+    float2 vdf[POLY_MAX_K + 1];    // vn_k as double-float
+    double v[POLY_MAX_K + 1];      // vn_k in FP64
+};
+
+// Q(z), dQ/dz and d2Q/dz2 by Horner in u = zeta^2 (T = float or double), with
+// qa = sum |qn_k| |zeta|^{2k}, the scale of the rounding error of Q.
+template <typename T>
+__device__ __forceinline__ void poly_eval(const SmoothPoly* P, T zx, T zy, T& Qx, T& Qy, T& Q1x, T& Q1y, T& Q2x,
+                                          T& Q2y, T& qa) {
+    const T* q;
+    T ic;
+    if constexpr (sizeof(T) == 4) {
+        q = (const T*)P->qf;
+        ic = (T)P->inv_acf;
+    } else {
+        q = (const T*)P->q;
+        ic = (T)P->inv_ac;
+    }
+    const T sx = zx * ic, sy = zy * ic;
+    const T ux = sx * sx - sy * sy, uy = (T)2 * sx * sy, au = sx * sx + sy * sy;
+    T px = q[P->K], py = 0, dx = 0, dy = 0, ex = 0, ey = 0;
+    T pa = q[P->K] < (T)0 ? -q[P->K] : q[P->K];
+    for (int k = P->K - 1; k >= 0; k--) {
+        const T nex = ex * ux - ey * uy + dx, ney = ex * uy + ey * ux + dy;
+        const T ndx = dx * ux - dy * uy + px, ndy = dx * uy + dy * ux + py;
+        const T npx = px * ux - py * uy + q[k], npy = px * uy + py * ux;
+        ex = nex;
+        ey = ney;
+        dx = ndx;
+        dy = ndy;
+        px = npx;
+        py = npy;
+        pa = pa * au + (q[k] < (T)0 ? -q[k] : q[k]);
+    }
+    Qx = px;
+    Qy = py;
+    // dQ/dzeta = 2 zeta p'(u);  d2Q/dzeta2 = 2 p'(u) + 4 u p''(u), p''(u) = 2 e;  d/dz = ic d/dzeta
+    Q1x = (T)2 * (sx * dx - sy * dy) * ic;
+    Q1y = (T)2 * (sx * dy + sy * dx) * ic;
+    Q2x = ((T)2 * dx + (T)8 * (ux * ex - uy * ey)) * ic * ic;
+    Q2y = ((T)2 * dy + (T)8 * (ux * ey + uy * ex)) * ic * ic;
+    qa = pa;
+}
+
+// FP32 form for iterates anywhere in the plane: Q and dQ/dz times a common complex scale
+// sc, with |Q sc| = O(1) also where zeta^{2K} would overflow FP32 (an Aberth cold start
+// can fling an iterate far out).  For |u| <= 1 (u = zeta^2) sc = 1; otherwise, with
+// w = 1/u and the reversed polynomial pr(w) = sum_k qn_k w^{K-k} = w^K p(u),
+//   sc = w^K,  sc Q = pr(w),  sc dp/du = w (K pr(w) - w pr'(w)),  sc dQ/dz = 2 zeta ic sc dp/du.
+// qa_sc = |sc| sum |qn_k| |u|^k.  The Aberth step needs only F'/F, and the stop rule
+// compares scaled noise with a scaled |F'|, so the common scale drops out.
+__device__ __forceinline__ void poly_eval_scaled(const SmoothPoly* P, float zx, float zy, float& Qx, float& Qy,
+                                                 float& Q1x, float& Q1y, float& scx, float& scy, float& qa) {
+    const float* q = P->qf;
+    const float ic = P->inv_acf;
+    const float sx = zx * ic, sy = zy * ic;
+    const float ux = sx * sx - sy * sy, uy = 2.f * sx * sy, au = sx * sx + sy * sy;
+    const int K = P->K;
+    float dx, dy;
+    if (au <= 1.f) {
+        float px = q[K], py = 0.f, pa = fabsf(q[K]);
+        dx = 0.f;
+        dy = 0.f;
+        for (int k = K - 1; k >= 0; k--) {
+            const float ndx = dx * ux - dy * uy + px, ndy = dx * uy + dy * ux + py;
+            const float npx = px * ux - py * uy + q[k], npy = px * uy + py * ux;
+            dx = ndx;
+            dy = ndy;
+            px = npx;
+            py = npy;
+            pa = pa * au + fabsf(q[k]);
+        }
+        Qx = px;
+        Qy = py;
+        scx = 1.f;
+        scy = 0.f;
+        qa = pa;
+    } else {
+        const float r = 1.f / (au * au);  // 1/|u|^2
+        const float wx = ux * r, wy = -uy * r, aw = 1.f / au;
+        float px = q[0], py = 0.f, ex = 0.f, ey = 0.f, pa = fabsf(q[0]), cx = 1.f, cy = 0.f;
+        for (int k = 1; k <= K; k++) {
+            const float nex = ex * wx - ey * wy + px, ney = ex * wy + ey * wx + py;
+            const float npx = px * wx - py * wy + q[k], npy = px * wy + py * wx;
+            const float ncx = cx * wx - cy * wy, ncy = cx * wy + cy * wx;
+            ex = nex;
+            ey = ney;
+            px = npx;
+            py = npy;
+            cx = ncx;
+            cy = ncy;
+            pa = pa * aw + fabsf(q[k]);
+        }
+        Qx = px;  // sc Q
+        Qy = py;
+        // sc dp/du = w (K pr - w pr')
+        const float tx = (float)K * px - (wx * ex - wy * ey), ty = (float)K * py - (wx * ey + wy * ex);
+        dx = wx * tx - wy * ty;
+        dy = wx * ty + wy * tx;
+        scx = cx;
+        scy = cy;
+        qa = pa;
+    }
+    Q1x = 2.f * (sx * dx - sy * dy) * ic;
+    Q1y = 2.f * (sx * dy + sy * dx) * ic;
+}
+
+// V(conj z) = -|c| conj(zeta) sum vn_k conj(zeta)^{2k} in FP64.
+__device__ __forceinline__ double2 poly_V(const SmoothPoly* P, double zx, double zy) {
+    const double sx = zx * P->inv_ac, sy = -zy * P->inv_ac;  // conj(zeta)
+    const double ux = sx * sx - sy * sy, uy = 2.0 * sx * sy;
+    double px = P->v[P->K], py = 0.0;
+    for (int k = P->K - 1; k >= 0; k--) {
+        const double npx = px * ux - py * uy + P->v[k], npy = px * uy + py * ux;
+        px = npx;
+        py = npy;
+    }
+    return make_double2(-P->ac * (sx * px - sy * py), -P->ac * (sx * py + sy * px));
+}
+
 // Device-side copy of a field's stars in the layouts the kernels read.
 struct FieldDev {
     int64_t n;
+    int64_t nr;               // roots per row: 2n (disc) or 2n + t - 1 (rectangle)
+    const SmoothPoly* poly;   // rectangle polynomial (device), nullptr for the disc
+    int poly_K;               // host copy of poly->K (0 for the disc)
     double kappa_s, gamma;
     bool unit_mass;
     float fmm_cell;   // far-field cell size aimed at ~6 stars in a 5x5 block of cells
@@ -70,6 +211,7 @@ struct TraceArgs {
 // One field of a batched launch (device table entry).
 struct TraceTask {
     const void* stars;     // FP32 star records
+    const SmoothPoly* poly;
     TfmmParams tfmm;
     const TCell* tcells;
     const int* tnear;
@@ -100,6 +242,7 @@ struct BatchTraceArgs {
 // One field's points for the FP64 rescue of uncertified points.
 struct RescueTask {
     const StarD* stars;
+    const SmoothPoly* poly;
     int n, nr;
     double kappa_s, gamma;
     int64_t m;

@@ -24,6 +24,7 @@ constexpr int PB_THREADS = 256;
 constexpr int TSB = 2048;  // stars per shared-memory tile
 
 struct PolishK {
+    const SmoothPoly* poly;  // rectangular field: smooth-sheet polynomial; nullptr for the disc
     const float4* dfp;
     const float2* dfm;
     const float2* dtf;
@@ -127,8 +128,21 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
                                                 int pass, int32_t it_in, double& est_out, double s2_err = 0.0) {
     const double oms = 1.0 - K.kappa_s;
     const double2 ph = K.phase[row];
-    const double Fx = K.gamma + S2x - oms * ph.x;
-    const double Fy = S2y + oms * ph.y;
+    double Fx = K.gamma + S2x - oms * ph.x;
+    double Fy = S2y + oms * ph.y;
+    const float s3sx = s3x, s3sy = s3y, s4sx = s4x, s4sy = s4y;  // star sums, for the Taylor of S1
+    if (K.poly) {
+        // rectangular field: F -= Q, F' = -2 (S3 + Q'/2), F'' = 6 (S4 - Q''/6)
+        double Qx, Qy, Q1x, Q1y, Q2x, Q2y, qa;
+        poly_eval<double>(K.poly, zx, zy, Qx, Qy, Q1x, Q1y, Q2x, Q2y, qa);
+        Fx -= Qx;
+        Fy -= Qy;
+        s3x += (float)(0.5 * Q1x);
+        s3y += (float)(0.5 * Q1y);
+        s4x -= (float)(Q2x / 6.0);
+        s4y -= (float)(Q2y / 6.0);
+        a3 += (float)(0.5 * (fabs(Q1x) + fabs(Q1y)));
+    }
     // delta = -F / F' = F / (2 S3)
     const double tx = 2.0 * (double)s3x, ty = 2.0 * (double)s3y;
     const double den = tx * tx + ty * ty;
@@ -155,14 +169,19 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
     // S1 at the final point by Taylor expansion about the evaluation point.
     const double d2x = dx * dx - dy * dy, d2y = 2.0 * dx * dy;       // delta^2
     const double d3x = d2x * dx - d2y * dy, d3y = d2x * dy + d2y * dx; // delta^3
-    const double S1nx = S1x - (S2x * dx - S2y * dy) + ((double)s3x * d2x - (double)s3y * d2y) -
-                        ((double)s4x * d3x - (double)s4y * d3y);
-    const double S1ny = S1y - (S2x * dy + S2y * dx) + ((double)s3x * d2y + (double)s3y * d2x) -
-                        ((double)s4x * d3y + (double)s4y * d3x);
+    const double S1nx = S1x - (S2x * dx - S2y * dy) + ((double)s3sx * d2x - (double)s3sy * d2y) -
+                        ((double)s4sx * d3x - (double)s4sy * d3y);
+    const double S1ny = S1y - (S2x * dy + S2y * dx) + ((double)s3sx * d2y + (double)s3sy * d2x) -
+                        ((double)s4sx * d3y + (double)s4sy * d3x);
     K.z_out[point] = make_double2(nzx, nzy);
     if (K.w_out) {
-        const double wx = oms * nzx + K.gamma * nzx - S1nx;
-        const double wy = oms * nzy - K.gamma * nzy + S1ny;
+        double wx = oms * nzx + K.gamma * nzx - S1nx;
+        double wy = oms * nzy - K.gamma * nzy + S1ny;
+        if (K.poly) {
+            const double2 V = poly_V(K.poly, nzx, nzy);
+            wx += V.x;
+            wy += V.y;
+        }
         K.w_out[point] = make_double2(wx, wy);
     }
     if (K.iters_out) K.iters_out[point] = it_in;
@@ -181,6 +200,29 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
     return true;
 }
 
+// Complex double-float and the rectangle's Q(z) in double-float (Horner in u = zeta^2,
+// zeta = z/|c|): the residual F nearly cancels at a critical point, so Q enters it with
+// the precision of the star sums.
+struct dfc {
+    df x, y;
+};
+
+__device__ __forceinline__ dfc dfc_mul(const dfc& a, const dfc& b) {
+    return dfc{df_sub(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_add(df_mul(a.x, b.y), df_mul(a.y, b.x))};
+}
+
+__device__ __forceinline__ dfc poly_Q_df(const SmoothPoly* P, df zx, df zy) {
+    const df ic = df{P->inv_acdf.x, P->inv_acdf.y};
+    const df sx = df_mul(zx, ic), sy = df_mul(zy, ic);
+    const dfc u = dfc{df_sub(df_sqr(sx), df_sqr(sy)), df_mul_f(df_mul(sx, sy), 2.f)};
+    dfc p = dfc{df{P->qdf[P->K].x, P->qdf[P->K].y}, df{0.f, 0.f}};
+    for (int k = P->K - 1; k >= 0; k--) {
+        p = dfc_mul(p, u);
+        p.x = df_add(p.x, df{P->qdf[k].x, P->qdf[k].y});
+    }
+    return p;
+}
+
 // Newton step delta = F / (2 S3) (F' = -2 S3, Eq. 7), certificate and, when done, the
 // outputs, from double-float sums and a triple-float z.  The residual F = S2 + c with
 // c = gamma - (1 - kappa_s) e^{-i phi} is a double-float sum: S2 nearly cancels c at a
@@ -191,9 +233,23 @@ __device__ __forceinline__ bool polish_epilogue(const PolishK& K, int64_t point,
 __device__ __forceinline__ bool polish_epilogue_df(const PolishK& K, int64_t point, int64_t row, const Sums& s,
                                                    const df& cx, const df& cy, tf& zx, tf& zy, float z0x, float z0y,
                                                    int pass, int32_t it_in, double& est_out, float s2_err = 0.f) {
-    const df Fx = df_add(s.S2x, cx), Fy = df_add(s.S2y, cy);
+    df Fx = df_add(s.S2x, cx), Fy = df_add(s.S2y, cy);
+    float s3x = s.s3x, s3y = s.s3y, s4x = s.s4x, s4y = s.s4y, a3 = s.a3;
+    if (K.poly) {
+        // rectangular field: F -= Q (double-float), F' = -2 (S3 + Q'/2), F'' = 6 (S4 - Q''/6)
+        const dfc Q = poly_Q_df(K.poly, df{zx.h, zx.m}, df{zy.h, zy.m});
+        Fx = df_sub(Fx, Q.x);
+        Fy = df_sub(Fy, Q.y);
+        float Qx, Qy, Q1x, Q1y, Q2x, Q2y, qa;
+        poly_eval<float>(K.poly, zx.h, zy.h, Qx, Qy, Q1x, Q1y, Q2x, Q2y, qa);
+        s3x += 0.5f * Q1x;
+        s3y += 0.5f * Q1y;
+        s4x -= Q2x * (1.f / 6.f);
+        s4y -= Q2y * (1.f / 6.f);
+        a3 += 0.5f * (fabsf(Q1x) + fabsf(Q1y)) + qa * (float)K.poly->K * K.poly->inv_acf;
+    }
     const float fx = __fadd_rn(Fx.hi, Fx.lo), fy = __fadd_rn(Fy.hi, Fy.lo);
-    const float tx = 2.f * s.s3x, ty = 2.f * s.s3y;
+    const float tx = 2.f * s3x, ty = 2.f * s3y;
     const float den = fmaf(tx, tx, ty * ty);
     float dx = 0.f, dy = 0.f, est;
     if (den > 0.f && den < FLT_MAX) {
@@ -202,9 +258,9 @@ __device__ __forceinline__ bool polish_epilogue_df(const PolishK& K, int64_t poi
         dy = fmaf(fy, tx, -fx * ty) * rd;
         const float ad = sqrtf(fmaf(dx, dx, dy * dy));
         const float s3a = 0.5f * sqrtf(den);
-        const float s4a = sqrtf(fmaf(s.s4x, s.s4x, s.s4y * s.s4y));
+        const float s4a = sqrtf(fmaf(s4x, s4x, s4y * s4y));
         const float r3 = __frcp_rn(s3a);
-        est = 1.5f * ad * ad * s4a * r3 + ad * (4.f * FLT_EPSILON * s.a3 * r3 + 8.f * FLT_EPSILON) + 0.5f * s2_err * r3;
+        est = 1.5f * ad * ad * s4a * r3 + ad * (4.f * FLT_EPSILON * a3 * r3 + 8.f * FLT_EPSILON) + 0.5f * s2_err * r3;
     } else {
         // F' vanishes (or the sums overflowed): no step, certified only at an exact zero of F
         est = (fx == 0.f && fy == 0.f) ? 0.f : FLT_MAX;
@@ -228,8 +284,13 @@ __device__ __forceinline__ bool polish_epilogue_df(const PolishK& K, int64_t poi
     K.z_out[point] = make_double2(ozx, ozy);
     if (K.w_out) {
         const double oms = 1.0 - K.kappa_s;
-        const double wx = fma(oms + K.gamma, ozx, -df_to_double(S1nx));
-        const double wy = fma(oms - K.gamma, ozy, df_to_double(S1ny));
+        double wx = fma(oms + K.gamma, ozx, -df_to_double(S1nx));
+        double wy = fma(oms - K.gamma, ozy, df_to_double(S1ny));
+        if (K.poly) {
+            const double2 V = poly_V(K.poly, ozx, ozy);
+            wx += V.x;
+            wy += V.y;
+        }
         K.w_out[point] = make_double2(wx, wy);
     }
     if (K.iters_out) K.iters_out[point] = it_in;
@@ -380,6 +441,7 @@ __global__ void __launch_bounds__(PB_THREADS) polish_batch_kernel(const PolishK*
 
 static PolishK make_polish_k(const PolishArgs& a) {
     PolishK K;
+    K.poly = a.f->poly;
     K.dfp = a.f->star_dfp;
     K.dfm = a.f->star_dfm;
     K.dtf = a.f->star_tf;
@@ -918,6 +980,7 @@ cudaError_t launch_finalize_fp64(const FinalizeArgs& a, cudaStream_t st) {
 // - conj(sum m_i/(z - z_i)), star sum in double-float or FP64.
 // ----------------------------------------------------------------------------------
 struct MapK {
+    const SmoothPoly* poly;
     const float4* dfp;
     const float2* dfm;
     const float2* dtf;
@@ -982,13 +1045,16 @@ __global__ void __launch_bounds__(PB_THREADS) map_kernel(MapK K) {
         S1y = df_to_double(ay);
     }
     const double oms = 1.0 - K.kappa_s;
-    K.w[p] = make_double2(oms * z.x + K.gamma * z.x - S1x, oms * z.y - K.gamma * z.y + S1y);
+    double2 V = make_double2(0.0, 0.0);
+    if (K.poly) V = poly_V(K.poly, z.x, z.y);
+    K.w[p] = make_double2(oms * z.x + K.gamma * z.x - S1x + V.x, oms * z.y - K.gamma * z.y + S1y + V.y);
 }
 
 cudaError_t launch_map_caustics(const FieldDev& f, const double2* z, int64_t count, double2* w,
                                 int hp_fp64, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     MapK K;
+    K.poly = f.poly;
     K.dfp = f.star_dfp;
     K.dfm = f.star_dfm;
     K.dtf = f.star_tf;

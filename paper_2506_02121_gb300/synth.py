@@ -55,6 +55,8 @@ class Field:
     gamma: float
     radius: float
     seed: int
+    c1: float = 0.0  # rectangular field: half-width and half-height (0 for a disc)
+    c2: float = 0.0
 
     @property
     def n(self) -> int:
@@ -100,6 +102,19 @@ def disc_field(n: int, kappa_star: float, kappa_s: float, gamma: float, seed: in
     r = radius * np.sqrt(u[0::2])
     th = 2.0 * math.pi * u[1::2]
     return Field(r * np.cos(th), r * np.sin(th), mm, kappa_star, kappa_s, gamma, radius, seed)
+
+
+def rect_field(n: int, kappa_star: float, kappa_s: float, gamma: float, seed: int, aspect: float = 1.0,
+               mass_kind: str = "unit", mass_lo: float = 0.08, mass_hi: float = 1.0,
+               normalise: bool = False) -> Field:
+    """N stars uniform in the rectangle |x| <= c1, |y| <= c2 = aspect c1 whose area
+    4 c1 c2 = sum(m) / kappa_* (the rectangular field of Sec. 4.2)."""
+    mm = masses(mass_kind, n, seed ^ 0x5A5A5A5A, mass_lo, mass_hi, normalise)
+    c1 = math.sqrt(float(mm.sum()) / (4.0 * kappa_star * aspect))
+    c2 = aspect * c1
+    u = uniform(seed, 2 * n)
+    return Field(c1 * (2.0 * u[0::2] - 1.0), c2 * (2.0 * u[1::2] - 1.0), mm, kappa_star, kappa_s, gamma,
+                 math.hypot(c1, c2), seed, c1, c2)
 
 
 # --------------------------------------------------------------------------------------

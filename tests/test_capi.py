@@ -58,3 +58,24 @@ def test_degenerate_field_rejected_before_any_device_work(lib):
     with pytest.raises(cc.CCError) as e:
         cc.cc_field_create(np.zeros(1), np.zeros(1), -np.ones(1), 0.0, 0.3)
     assert e.value.status == cc.CC_EINVAL
+
+
+def test_rect_options_rejected_before_any_device_work(lib):
+    import numpy as np
+    from paper_2506_02121_gb300 import cc
+    x, y, m = np.zeros(1), np.zeros(1), np.ones(1)
+    for kw, status in [(dict(kappa_star=0.0, c1=2.0, c2=1.0), cc.CC_EINVAL),
+                       (dict(kappa_star=0.3, c1=-2.0, c2=1.0), cc.CC_EINVAL),
+                       (dict(kappa_star=0.3, c1=2.0, c2=1.0, t=8), cc.CC_EINVAL),
+                       (dict(kappa_star=0.3, c1=2.0, c2=1.0, t=cc.CC_RECT_MAX_T + 2), cc.CC_EINVAL),
+                       # a square with t - 1 = 8: (t - 1) pi/4 is a multiple of pi
+                       (dict(kappa_star=0.3, c1=2.0, c2=2.0, t=9), cc.CC_EDEGENERATE)]:
+        o = cc.rect_options(**kw)
+        with pytest.raises(cc.CCError) as e:
+            cc.cc_field_create(x, y, m, 0.0, 0.3, o)
+        assert e.value.status == status, kw
+    o = cc.cc_options_default()
+    o.field_shape = 7
+    with pytest.raises(cc.CCError) as e:
+        cc.cc_field_create(x, y, m, 0.0, 0.3, o)
+    assert e.value.status == cc.CC_EINVAL
