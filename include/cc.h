@@ -102,6 +102,9 @@ typedef struct cc_options {
     double rect_c1, rect_c2; /* CC_FIELD_RECT: corner c = c1 + i c2 of the field (half-width,
                               half-height, both > 0) */
     double rect_eps, rect_s; /* CC_FIELD_RECT, rect_t == 0: error target (1e-9) and ratio s > 1 (2) */
+    int32_t row_ctas;      /* CTAs (one thread-block cluster) that share each phi sub-range of the FP32
+                              tracer, each updating a slice of the roots: 0 = automatic (8 when
+                              n_r >= 4096, else 1), 1 = one CTA per sub-range, 2..16 = that many */
 } cc_options;
 
 /* Solve statistics of the last cc_critical_curves on a field (host copy). */

@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("subchains", ctypes.c_int32), ("predictor", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("far_field", ctypes.c_int32), ("field_shape", ctypes.c_int32), ("rect_t", ctypes.c_int32),
                 ("kappa_star", ctypes.c_double), ("rect_c1", ctypes.c_double), ("rect_c2", ctypes.c_double),
-                ("rect_eps", ctypes.c_double), ("rect_s", ctypes.c_double)]
+                ("rect_eps", ctypes.c_double), ("rect_s", ctypes.c_double), ("row_ctas", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):

@@ -126,6 +126,11 @@ struct Ctx {
     float* dprev;
     int *conv, *it, *act;
     bool resident;
+    int lo, hi;       // this CTA's slice [lo, hi) of each direction's roots (all of them unless a
+                      // cluster of CTAs shares the sub-range)
+    int* s_red;       // cluster reductions: [2][4] shared-memory slots, double-buffered
+    int* s_tot;       // [4] reduced totals
+    int* red_parity;
     unsigned long long* n_terms;  // this thread's work counters (registers of the caller)
     unsigned long long* n_far;
 };
@@ -349,8 +354,9 @@ __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool
             const int tn = min(TR, nr - t0);
             __syncthreads();
             for (int j = tid; j < tn; j += P) {
-                if (a0) x.s_root[j] = x.cur[t0 + j];
-                if (a1) x.s_root[TR + j] = x.cur[nr + t0 + j];
+                // L2 loads: in a cluster, other SMs wrote these positions since the last sweep
+                if (a0) x.s_root[j] = __ldcg(&x.cur[t0 + j]);
+                if (a1) x.s_root[TR + j] = __ldcg(&x.cur[nr + t0 + j]);
             }
             __syncthreads();
             if (any) {
@@ -378,12 +384,74 @@ __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool
     }
 }
 
+// Thread-block clusters: several CTAs share one phi sub-range (each updates a slice of the
+// roots and reads all of them); hardware cluster barriers order the sweeps, and per-CTA
+// counts are summed through distributed shared memory.
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of all CTAs of the cluster; global and shared writes before it are visible
+// to every thread of the cluster after it.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int ld_cluster(const int* local, unsigned rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned ra;
+    int v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+// Sum of three CTA-uniform ints over the cluster (called by all threads of every CTA in the
+// same order).  Double-buffered slots: a CTA rewrites a slot two reductions later, after
+// the barrier of the reduction in between, which every reader of the slot has passed.
+template <typename T>
+__device__ __forceinline__ void cluster_sum3(const Ctx<T>& x, int& a, int& b, int& c) {
+    const int p = *x.red_parity;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        x.s_red[4 * p] = a;
+        x.s_red[4 * p + 1] = b;
+        x.s_red[4 * p + 2] = c;
+    }
+    cluster_sync();
+    if (threadIdx.x == 0) {
+        const unsigned G = cluster_size();
+        int sa = 0, sb = 0, sc = 0;
+        for (unsigned r = 0; r < G; r++) {
+            sa += ld_cluster(x.s_red + 4 * p, r);
+            sb += ld_cluster(x.s_red + 4 * p + 1, r);
+            sc += ld_cluster(x.s_red + 4 * p + 2, r);
+        }
+        x.s_tot[0] = sa;
+        x.s_tot[1] = sb;
+        x.s_tot[2] = sc;
+        *x.red_parity = p ^ 1;
+    }
+    __syncthreads();
+    a = x.s_tot[0];
+    b = x.s_tot[1];
+    c = x.s_tot[2];
+}
+
 // Run Jacobi Aberth sweeps on the active rows (dir 0: row0, dir 1: row1) until every root
 // is frozen or max_iter sweeps were made.  Called by all threads of the CTA.  The unfrozen
 // roots of direction d are listed in act[d nr, d nr + A_d).  With many of them the FP32
 // tracer gives each thread several roots of one direction (sweep_blocked); otherwise g
 // lanes share a root and reduce their partial sums with shuffles.
-template <typename T>
+template <typename T, bool WIDE>
 __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int64_t row0, int64_t row1,
                                           int max_iter, bool cold, bool report, int* s_count, int* s_maxit) {
     using C = typename CT<T>::C;
@@ -402,19 +470,29 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         cph1 = (T)ph.x;
         sph1 = (T)ph.y;
     }
+    const int lo = x.lo, W = x.hi - x.lo;
+    Ctx<T> xs = x;
+    xs.act = x.act + lo;  // this CTA's lists: [lo, lo + A0) and [nr + lo, nr + lo + A1)
     for (int iter = 0;; iter++) {
         __syncthreads();
         if (tid < 2) s_count[tid] = 0;
         __syncthreads();
-        for (int key = tid; key < 2 * nr; key += P) {
-            const int d = key >= nr;
+        for (int i = tid; i < 2 * W; i += P) {
+            const int d = i >= W;
+            const int key = d * nr + lo + (i - d * W);
             const bool on = d ? a1 : a0;
-            if (on && !x.conv[key]) x.act[d * nr + atomicAdd(&s_count[d], 1)] = key;
+            if (on && !x.conv[key]) x.act[d * nr + lo + atomicAdd(&s_count[d], 1)] = key;
         }
         __syncthreads();
         const int A0 = s_count[0], A1 = s_count[1];
         const int A = A0 + A1;
-        if (A == 0) break;
+        int At = A;
+        if constexpr (WIDE) {
+            int u0 = A0, u1 = A1, u2 = 0;
+            cluster_sum3(x, u0, u1, u2);  // also publishes the previous sweep's positions
+            At = u0 + u1;
+        }
+        if (At == 0) break;
         if (iter >= max_iter) {
             if (tid == 0 && report) atomicAdd(&K.rep->unconverged, (unsigned long long)A);
             break;
@@ -423,13 +501,17 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             atomicAdd(&K.rep->root_iterations, (unsigned long long)A);
             if (cold) atomicAdd(&K.rep->cold_root_iterations, (unsigned long long)A);
         }
+        if (A == 0) {
+            if constexpr (WIDE) cluster_sync();  // the barrier the other CTAs take before their copies
+            continue;
+        }
         bool blocked = false;
         if constexpr (sizeof(T) == 4) {
             if (A >= 2 * P) {
-                sweep_blocked<4>(x, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                sweep_blocked<4>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
                 blocked = true;
             } else if (A >= P) {
-                sweep_blocked<2>(x, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                sweep_blocked<2>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
                 blocked = true;
             }
         }
@@ -443,7 +525,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             for (int base = 0; base < A; base += groups) {
                 const int slot = base + gid;
                 const bool valid = slot < A;
-                const int key = valid ? (slot < A0 ? x.act[slot] : x.act[nr + slot - A0]) : 0;
+                const int key = valid ? (slot < A0 ? xs.act[slot] : xs.act[nr + slot - A0]) : lo;
                 const int d = key >= nr;
                 const C z = x.cur[key];
                 Acc<T> acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -470,8 +552,8 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                     const int tn = min(TR, nr - t0);
                     __syncthreads();
                     for (int j = tid; j < tn; j += P) {
-                        if (a0) x.s_root[j] = x.cur[t0 + j];
-                        if (a1) x.s_root[TR + j] = x.cur[nr + t0 + j];
+                        if (a0) x.s_root[j] = __ldcg(&x.cur[t0 + j]);
+                        if (a1) x.s_root[TR + j] = __ldcg(&x.cur[nr + t0 + j]);
                     }
                     __syncthreads();
                     if (valid) {
@@ -499,20 +581,28 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 if (valid && lane == 0) finish_root<T>(x, key, z, acc, d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
             }
         }
-        __syncthreads();
+        // every CTA of a cluster has finished reading the positions before any is updated
+        if constexpr (WIDE) cluster_sync();
+        else __syncthreads();
         for (int i = tid; i < A; i += P) {
-            const int key = i < A0 ? x.act[i] : x.act[nr + i - A0];
+            const int key = i < A0 ? xs.act[i] : xs.act[nr + i - A0];
             x.cur[key] = x.nxt[key];
         }
     }
     // directions that still hold unfrozen roots
     bool b0 = false, b1 = false;
-    for (int key = tid; key < 2 * nr; key += P) {
+    for (int i = tid; i < 2 * W; i += P) {
+        const int d = i >= W;
+        const int key = d * nr + lo + (i - d * W);
         if (x.conv[key]) continue;
-        if (key < nr) b0 |= a0;
+        if (d == 0) b0 |= a0;
         else b1 |= a1;
     }
-    const int m0 = __syncthreads_or(b0), m1 = __syncthreads_or(b1);
+    int m0 = __syncthreads_or(b0), m1 = __syncthreads_or(b1);
+    if constexpr (WIDE) {
+        int u2 = 0;
+        cluster_sum3(x, m0, m1, u2);
+    }
     return (m0 ? 1 : 0) | (m1 ? 2 : 0);
 }
 
@@ -529,7 +619,7 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
     const int nr = K.nr;
     const Star* gs = (const Star*)K.stars;
     const int n2 = 2 * K.n;
-    for (int k = threadIdx.x; k < nr; k += blockDim.x) {
+    for (int k = x.lo + threadIdx.x; k < x.hi; k += blockDim.x) {
         const int key = d * nr + k;
         if (k >= n2) {
             // rectangular field: the t - 1 further roots start evenly spread on the circle of
@@ -568,10 +658,12 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
 
 // One sub-range s of one field, start to end, by the whole CTA: cold start at its centre
 // row, then both directions row by row.  w: this CTA's Jacobi scratch.
-template <typename T>
+template <typename T, bool WIDE>
 __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, unsigned char* smem,
                                              int* s_count_p, int* s_maxit_p, unsigned long long* n_terms_p,
-                                             unsigned long long* n_far_p) {
+                                             unsigned long long* n_far_p, int* s_red = nullptr,
+                                             int* s_tot = nullptr, int* red_parity = nullptr, int rank = 0,
+                                             int G = 1) {
     using C = typename CT<T>::C;
     using Star = typename CT<T>::Star;
     constexpr int TS = CT<T>::TS;
@@ -595,15 +687,24 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     x.it = x.conv + 2 * nr;
     x.act = x.it + 2 * nr;
     x.resident = n <= TS;
+    {
+        const int Wd = (nr + G - 1) / G;
+        x.lo = min(nr, rank * Wd);
+        x.hi = min(nr, x.lo + Wd);
+    }
+    x.s_red = s_red;
+    x.s_tot = s_tot;
+    x.red_parity = red_parity;
     x.n_terms = n_terms_p;
     x.n_far = n_far_p;
+    const int lo = x.lo, hi = x.hi;
     const Star* gs = (const Star*)K.stars;
     if (x.resident)
         for (int j = tid; j < n; j += P) x.s_star[j] = gs[j];
 
     seed_guesses<T>(x, 0);
-    for (int k = tid; k < nr; k += P) x.conv[nr + k] = 1;
-    solve_rows<T>(x, true, false, c, -1, K.max_iter_cold, true, true, s_count, &s_maxit);
+    for (int k = lo + tid; k < hi; k += P) x.conv[nr + k] = 1;
+    solve_rows<T, WIDE>(x, true, false, c, -1, K.max_iter_cold, true, true, s_count, &s_maxit);
 
     C* zrows = (C*)K.zrows;
     C* seam = (C*)K.seam;
@@ -612,27 +713,30 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     };
     {
         C* o = dst(c);
-        for (int k = tid; k < nr; k += P) {
+        for (int k = lo + tid; k < hi; k += P) {
             o[k] = x.cur[k];
             x.cur[nr + k] = x.cur[k];
             K.iters[(size_t)c * nr + k] = x.it[k];
         }
     }
-    // hist[d]: rows of direction d already behind the current one that belong to the same
+    // s_hist[d]: rows of direction d already behind the current one that belong to the same
     // chains (a row re-solved from the star guesses has new column labels: history restarts)
-    int hist[2] = {0, 0};
+    __shared__ int s_hist[2];
+    if (tid == 0) s_hist[0] = s_hist[1] = 0;
     for (int64_t t = 1;; t++) {
         const bool a0 = c - t >= b0, a1 = c + t <= b1;
         if (!a0 && !a1) break;
         const int64_t r0 = c - t, r1 = c + t;
         __syncthreads();
-        for (int k = tid; k < 2 * nr; k += P) {
+        for (int i = tid; i < 2 * (hi - lo); i += P) {
+            const int dd = i >= hi - lo;
+            const int k = dd * nr + lo + (i - dd * (hi - lo));
             const bool on = k < nr ? a0 : a1;
             if (!on) {
                 x.conv[k] = 1;
                 continue;
             }
-            const int h = hist[k < nr ? 0 : 1];
+            const int h = s_hist[k < nr ? 0 : 1];
             const C zc = x.cur[k];
             C g = zc;
             if (K.predictor >= 2 && h >= 2) {
@@ -652,11 +756,13 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             x.it[k] = 0;
             x.dprev[k] = FLT_MAX;
         }
-        const int bad = solve_rows<T>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit);
-        if (a0) hist[0] = min(hist[0] + 1, 2);
-        if (a1) hist[1] = min(hist[1] + 1, 2);
-        if (bad & 1) hist[0] = 0;
-        if (bad & 2) hist[1] = 0;
+        const int bad = solve_rows<T, WIDE>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit);
+        if (tid == 0) {  // read again only after the next row's opening barrier
+            if (a0) s_hist[0] = min(s_hist[0] + 1, 2);
+            if (a1) s_hist[1] = min(s_hist[1] + 1, 2);
+            if (bad & 1) s_hist[0] = 0;
+            if (bad & 2) s_hist[1] = 0;
+        }
         if (bad) {
             // A warm start that does not settle (e.g. a phase step so large that the previous
             // row sits on a symmetric, non-converging configuration) restarts that row from
@@ -664,18 +770,18 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             __syncthreads();
             if (bad & 1) seed_guesses<T>(x, 0);
             if (bad & 2) seed_guesses<T>(x, 1);
-            solve_rows<T>(x, bad & 1, (bad & 2) != 0, r0, r1, K.max_iter_cold, true, true, s_count, &s_maxit);
+            solve_rows<T, WIDE>(x, bad & 1, (bad & 2) != 0, r0, r1, K.max_iter_cold, true, true, s_count, &s_maxit);
         }
         if (a0) {
             C* o = dst(r0);
-            for (int k = tid; k < nr; k += P) {
+            for (int k = lo + tid; k < hi; k += P) {
                 o[k] = x.cur[k];
                 K.iters[(size_t)r0 * nr + k] = x.it[k];
             }
         }
         if (a1) {
             C* o = dst(r1);
-            for (int k = tid; k < nr; k += P) {
+            for (int k = lo + tid; k < hi; k += P) {
                 o[k] = x.cur[nr + k];
                 if (!(r1 == b1 && s < K.S - 1)) K.iters[(size_t)r1 * nr + k] = x.it[nr + k];
             }
@@ -690,8 +796,8 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
     __shared__ int s_count[2], s_maxit;
     if (threadIdx.x == 0) s_maxit = 0;
     unsigned long long n_terms = 0, n_far = 0;
-    run_subchain<T>(K, blockIdx.x, K.work + (size_t)blockIdx.x * K.work_stride, smem, s_count, &s_maxit, &n_terms,
-                    &n_far);
+    run_subchain<T, false>(K, blockIdx.x, K.work + (size_t)blockIdx.x * K.work_stride, smem, s_count, &s_maxit,
+                           &n_terms, &n_far);
     for (int off = 16; off > 0; off >>= 1) {
         n_terms += __shfl_xor_sync(0xffffffffu, n_terms, off);
         n_far += __shfl_xor_sync(0xffffffffu, n_far, off);
@@ -701,6 +807,33 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
         atomicAdd(&K.rep->far_evals, n_far);
     }
     if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
+}
+
+// One phi sub-range per thread-block cluster (grid = S clusters of G CTAs): for rows so wide
+// (many roots) that one SM per sub-range would leave most of the GPU idle on a small m.
+__global__ void __launch_bounds__(512, 1) trace_wide_kernel(TK K) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_count[2], s_maxit, s_red[8], s_tot[4], s_parity;
+    if (threadIdx.x == 0) {
+        s_maxit = 0;
+        s_parity = 0;
+    }
+    const int G = (int)cluster_size(), rank = (int)cluster_rank();
+    const int s = (int)blockIdx.x / G;
+    unsigned long long n_terms = 0, n_far = 0;
+    __syncthreads();
+    run_subchain<float, true>(K, s, K.work + (size_t)s * K.work_stride, smem, s_count, &s_maxit, &n_terms, &n_far,
+                              s_red, s_tot, &s_parity, rank, G);
+    for (int off = 16; off > 0; off >>= 1) {
+        n_terms += __shfl_xor_sync(0xffffffffu, n_terms, off);
+        n_far += __shfl_xor_sync(0xffffffffu, n_far, off);
+    }
+    if ((threadIdx.x & 31) == 0 && (n_terms || n_far)) {
+        atomicAdd(&K.rep->star_terms, n_terms);
+        atomicAdd(&K.rep->far_evals, n_far);
+    }
+    if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
+    cluster_sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // Many fields in one persistent launch: resident CTAs take (field, sub-range) items from a
@@ -747,7 +880,7 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
         if (threadIdx.x == 0) s_maxit = 0;
         n_terms = 0;
         n_far = 0;
-        run_subchain<T>(K, fs.y, w, smem, s_count, &s_maxit, &n_terms, &n_far);
+        run_subchain<T, false>(K, fs.y, w, smem, s_count, &s_maxit, &n_terms, &n_far);
         for (int off = 16; off > 0; off >>= 1) {
             n_terms += __shfl_xor_sync(0xffffffffu, n_terms, off);
             n_far += __shfl_xor_sync(0xffffffffu, n_far, off);
@@ -789,6 +922,36 @@ int tracer_blocks_per_sm(bool fp64, int threads) {
         b = 1;
     }
     return b;
+}
+
+int tracer_cluster_size(const cc_options& o, int64_t nr, bool fp64) {
+    if (fp64) return 1;
+    if (o.row_ctas > 0) return o.row_ctas;
+    return nr >= WIDE_MIN_NR ? 8 : 1;
+}
+
+int tracer_max_clusters(int G, int threads) {
+    const size_t smem = tracer_smem_bytes(false);
+    cudaError_t e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && G > 8)
+        e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int n = 0;
+    if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)G);
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)G;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&n, trace_wide_kernel, &cfg);
+    }
+    if (e != cudaSuccess) cudaGetLastError();
+    return n > 0 ? n : 1;
 }
 
 int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms, int blocks_per_sm) {
@@ -833,6 +996,27 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
     K.tcoeff = a.f->tcoeff;
     const size_t smem = tracer_smem_bytes(fp64);
     cudaError_t e;
+    if (!fp64 && a.cluster > 1) {
+        e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess && a.cluster > 8)
+            e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(a.S * a.cluster));
+        cfg.blockDim = dim3((unsigned)a.threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)a.cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, trace_wide_kernel, K);
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     if (fp64) {
         e = cudaFuncSetAttribute(trace_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

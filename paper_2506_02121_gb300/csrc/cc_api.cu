@@ -84,7 +84,15 @@ CurveLayout curve_layout(const cc_field* f, int64_t m) {
     const bool fp64 = f->opt.precision == CC_FP64;
     L.elem = fp64 ? sizeof(double2) : sizeof(float2);
     L.threads = f->opt.block_threads > 0 ? f->opt.block_threads : 512;
-    L.S = subchain_count(m, nr, f->opt, sm_count(f->device), tracer_occupancy(f->device, fp64, L.threads));
+    L.G = tracer_cluster_size(f->opt, nr, fp64);
+    if (L.G > 1) {
+        // one wave of clusters; a sub-range keeps >= 8 rows
+        cc_options o = f->opt;
+        o.subchains = f->opt.subchains > 0 ? f->opt.subchains : std::max(1, tracer_max_clusters(L.G, L.threads));
+        L.S = subchain_count(m, nr, o, 1, 1);
+    } else {
+        L.S = subchain_count(m, nr, f->opt, sm_count(f->device), tracer_occupancy(f->device, fp64, L.threads));
+    }
     L.work_stride = tracer_work_stride(nr, L.elem);
     size_t o = 0;
     L.off_report = o;
@@ -170,6 +178,7 @@ int cc_options_default(cc_options* opt) {
     opt->rect_c2 = 0.0;
     opt->rect_eps = 1e-9;
     opt->rect_s = 2.0;
+    opt->row_ctas = 0;
     return CC_OK;
 }
 
@@ -265,6 +274,7 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
         return fail(CC_EINVAL, "cc_field_create: bad options");
     if (o.far_field != 0 && o.far_field != 1) return fail(CC_EINVAL, "cc_field_create: far_field must be 0 or 1");
     if (o.predictor < 0 || o.predictor > 2) return fail(CC_EINVAL, "cc_field_create: predictor must be 0, 1 or 2");
+    if (o.row_ctas < 0 || o.row_ctas > 16) return fail(CC_EINVAL, "cc_field_create: row_ctas must be in [0, 16]");
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 512 || (o.block_threads & 31)))
         return fail(CC_EINVAL, "cc_field_create: block_threads must be 0 or a multiple of 32 in [32, 512]");
 
@@ -467,6 +477,7 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
     ta.max_iter_warm = f->opt.max_iter_warm;
     ta.predictor = f->opt.predictor;
     ta.threads = L.threads;
+    ta.cluster = L.G;
     CC_CUDA(launch_trace(ta, fp64, st), "trace");
     CC_CUDA(cudaEventRecord(f->ev[1], st), "event record");
     int32_t* perm = (int32_t*)(ws + L.off_perm);

@@ -206,6 +206,7 @@ struct TraceArgs {
     double tol_abs, mu_max;
     int max_iter_cold, max_iter_warm, predictor;
     int threads;
+    int cluster;           // CTAs per sub-range (> 1: one thread-block cluster per sub-range)
 };
 
 // One field of a batched launch (device table entry).
@@ -266,6 +267,7 @@ cudaError_t launch_seam_join_batch(const TraceTask* tasks, int count, const int2
 struct CurveLayout {
     int S;
     int threads;
+    int G;                 // CTAs per sub-range (cluster size; 1 = one CTA)
     size_t elem;           // bytes per tracer complex (8 FP32, 16 FP64)
     size_t off_phase, off_zrows, off_seam, off_iters, off_match, off_hits, off_perm, off_work,
         off_report, off_list, off_nlist, off_fmm, total;
@@ -277,6 +279,9 @@ size_t tracer_work_stride(int64_t nr, size_t elem);
 size_t tracer_smem_bytes(bool fp64);
 int tracer_blocks_per_sm(bool fp64, int threads);
 int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms, int blocks_per_sm);
+constexpr int WIDE_MIN_NR = 4096;   // automatic cluster tracing from this many roots per row
+int tracer_cluster_size(const cc_options& o, int64_t nr, bool fp64);
+int tracer_max_clusters(int G, int threads);  // co-resident clusters of G tracing CTAs
 
 cudaError_t launch_phase_table(double2* phase, int64_t m, cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st);

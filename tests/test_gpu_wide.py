@@ -1,0 +1,65 @@
+"""Cluster tracing (several CTAs per phi sub-range, each updating a slice of the roots):
+the chains match the FP64 oracle and the one-CTA tracer, for explicit cluster sizes on
+small fields and for the automatic choice on a field with n_r >= 4096."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2506_02121_gb300 import cc, synth
+from tests.gpu_util import compare_chain, match_row
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-9
+
+
+def _solve(f, msteps, opt):
+    field = cc.cc_field_create(f.x, f.y, f.m, f.kappa_s, f.gamma, opt)
+    z, w, _ = cc.critical_curves(field, msteps, caustics=True)
+    st, rep = cc.cc_field_report(field)
+    return z.cpu().numpy(), w.cpu().numpy(), st, rep
+
+
+@pytest.mark.parametrize("G", [2, 3, 8])
+def test_cluster_tracer_matches_oracle(G):
+    f = synth.disc_field(60, 0.4, 0.0, 0.4, synth.stream_seed(31, G), "loguniform", normalise=True)
+    o = cc.cc_options_default()
+    o.row_ctas = G
+    zg, wg, st, rep = _solve(f, 200, o)
+    assert st == cc.CC_OK and rep["uncertified"] == 0 and rep["seam_ambiguous"] == 0, rep
+    zo, _, bad = oracle.critical_curves(f.x, f.y, f.m, f.kappa_s, f.gamma, 200)
+    assert bad == 0
+    worst, pairs = compare_chain(zg, zo, TOL)
+    wo = oracle.map_caustics(f.x, f.y, f.m, f.kappa_s, f.gamma, zg)
+    assert np.abs(wg - wo).max() < TOL
+    o1 = cc.cc_options_default()
+    o1.row_ctas = 1
+    z1, w1, st1, _ = _solve(f, 200, o1)
+    compare_chain(zg, z1, 3e-10)
+
+
+def test_cluster_tracer_rectangle():
+    f = synth.rect_field(40, 0.4, 0.0, 0.35, synth.stream_seed(32, 0), 1.2, "loguniform")
+    o = cc.rect_options(f.kappa_star, f.c1, f.c2)
+    o.row_ctas = 4
+    zg, wg, st, rep = _solve(f, 100, o)
+    assert st == cc.CC_OK and rep["uncertified"] == 0, rep
+    t = oracle.rect_choose_t(f.kappa_star, f.c1, f.c2)
+    R = oracle.Rect(f.kappa_star, f.c1, f.c2, t)
+    zo, _, bad = oracle.critical_curves(f.x, f.y, f.m, f.kappa_s, f.gamma, 100, rect=R)
+    compare_chain(zg, zo, TOL)
+
+
+def test_automatic_cluster_on_wide_rows():
+    """n_r = 4200 >= 4096: clusters of 8 CTAs per sub-range by default."""
+    n, msteps = 2100, 40
+    f = synth.disc_field(n, 0.3, 0.1, 0.3, synth.stream_seed(33, 0), "loguniform", normalise=True)
+    zg, wg, st, rep = _solve(f, msteps, cc.cc_options_default())
+    assert st == cc.CC_OK and rep["uncertified"] == 0 and rep["seam_ambiguous"] == 0, rep
+    for j in [0, msteps // 2, msteps]:
+        zo, left = oracle.solve_row(f.x, f.y, f.m, f.kappa_s, f.gamma, oracle.phi(j, msteps))
+        assert left == 0
+        idx, dist, sep = match_row(zg[j], zo)
+        assert dist < TOL and len(set(idx.tolist())) == len(idx)
+        wo = oracle.map_caustics(f.x, f.y, f.m, f.kappa_s, f.gamma, zg[j])
+        assert np.abs(wg[j] - wo).max() < TOL
