@@ -16,6 +16,7 @@
 //     F' = -2B,  P'/P = F'/F + 2C  and the update  z_k -= 1/(P'/P - D)  (Sec. 3.2).
 // Two arithmetics: FP32 (the mixed form; its result is polished afterwards) and FP64 (the
 // plain form with the |dz| < tol stop rule of Sec. 3.2).
+#include <algorithm>
 #include <float.h>
 #include <string.h>
 
@@ -677,7 +678,7 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     Ctx<T> x;
     x.k = &K;
     x.s_star = (Star*)smem;
-    x.s_root = (C*)(smem + sizeof(Star) * TS);
+    x.s_root = (C*)(smem + sizeof(Star) * (size_t)min(n, TS));  // star tile of min(n, TS) stars
     x.cur = (C*)w;
     x.nxt = x.cur + 2 * nr;
     x.prev = x.nxt + 2 * nr;
@@ -893,9 +894,10 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
     }
 }
 
-size_t tracer_smem_bytes(bool fp64) {
-    return fp64 ? CT<double>::TS * sizeof(StarD) + 2 * TR * sizeof(double2)
-                : CT<float>::TS * sizeof(float4) + 2 * TR * sizeof(float2);
+// Shared memory of a tracing CTA: a star tile of min(n, TS) stars, then the root tiles.
+size_t tracer_smem_bytes(bool fp64, int64_t n) {
+    const int64_t ts = std::min<int64_t>(n, fp64 ? CT<double>::TS : CT<float>::TS);
+    return fp64 ? ts * sizeof(StarD) + 2 * TR * sizeof(double2) : ts * sizeof(float4) + 2 * TR * sizeof(float2);
 }
 
 size_t tracer_work_stride(int64_t nr, size_t elem) {
@@ -904,9 +906,9 @@ size_t tracer_work_stride(int64_t nr, size_t elem) {
 }
 
 // Tracing CTAs that fit on one SM at once (registers and shared memory).
-int tracer_blocks_per_sm(bool fp64, int threads) {
+int tracer_blocks_per_sm(bool fp64, int threads, int64_t n) {
     int b = 0;
-    const size_t smem = tracer_smem_bytes(fp64);
+    const size_t smem = tracer_smem_bytes(fp64, n);
     cudaError_t e;
     if (fp64) {
         e = cudaFuncSetAttribute(trace_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -931,7 +933,7 @@ int tracer_cluster_size(const cc_options& o, int64_t nr, bool fp64) {
 }
 
 int tracer_max_clusters(int G, int threads) {
-    const size_t smem = tracer_smem_bytes(false);
+    const size_t smem = tracer_smem_bytes(false, (int64_t)CT<float>::TS);
     cudaError_t e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && G > 8)
         e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -994,7 +996,7 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
     K.tcells = a.f->tcells;
     K.tnear = a.f->tnear;
     K.tcoeff = a.f->tcoeff;
-    const size_t smem = tracer_smem_bytes(fp64);
+    const size_t smem = tracer_smem_bytes(fp64, a.f->n);
     cudaError_t e;
     if (!fp64 && a.cluster > 1) {
         e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1251,7 +1253,7 @@ cudaError_t launch_rescue(const RescueTask* host_task, const RescueTask* dev_tas
 }
 
 cudaError_t launch_trace_batch(const BatchTraceArgs& b, int grid, int threads, cudaStream_t st) {
-    const size_t smem = tracer_smem_bytes(false);
+    const size_t smem = tracer_smem_bytes(false, (int64_t)CT<float>::TS);
     cudaError_t e = cudaFuncSetAttribute(trace_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     trace_batch_kernel<float><<<grid, threads, smem, st>>>(b);
@@ -1272,7 +1274,7 @@ cudaError_t launch_seam_join_batch(const TraceTask* tasks, int count, const int2
 
 int tracer_batch_blocks_per_sm(int threads) {
     int b = 0;
-    const size_t smem = tracer_smem_bytes(false);
+    const size_t smem = tracer_smem_bytes(false, (int64_t)CT<float>::TS);
     cudaError_t e = cudaFuncSetAttribute(trace_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_batch_kernel<float>, threads, smem);
     if (e != cudaSuccess || b < 1) {

@@ -65,14 +65,17 @@ int sm_count(int device) {
 }
 
 // Resident tracing CTAs per SM, per (device, precision, block size); cached.
-int tracer_occupancy(int device, bool fp64, int threads) {
+int tracer_occupancy(int device, bool fp64, int threads, int64_t n) {
     static std::mutex mu;
-    static std::vector<int> cache;  // index: (device * 2 + fp64) * 17 + threads / 32
+    static std::vector<std::pair<int64_t, int>> cache;  // (key, CTAs per SM)
+    const int64_t ts = std::min<int64_t>(n, 4096);
+    const int64_t key = (((int64_t)device * 2 + (fp64 ? 1 : 0)) * 17 + threads / 32) * 8192 + ts;
     std::lock_guard<std::mutex> lk(mu);
-    const size_t key = ((size_t)device * 2 + (fp64 ? 1 : 0)) * 17 + (size_t)(threads / 32);
-    if (cache.size() <= key) cache.resize(key + 1, 0);
-    if (cache[key] == 0) cache[key] = tracer_blocks_per_sm(fp64, threads);
-    return cache[key];
+    for (const auto& kv : cache)
+        if (kv.first == key) return kv.second;
+    const int b = tracer_blocks_per_sm(fp64, threads, n);
+    cache.push_back({key, b});
+    return b;
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -91,7 +94,7 @@ CurveLayout curve_layout(const cc_field* f, int64_t m) {
         o.subchains = f->opt.subchains > 0 ? f->opt.subchains : std::max(1, tracer_max_clusters(L.G, L.threads));
         L.S = subchain_count(m, nr, o, 1, 1);
     } else {
-        L.S = subchain_count(m, nr, f->opt, sm_count(f->device), tracer_occupancy(f->device, fp64, L.threads));
+        L.S = subchain_count(m, nr, f->opt, sm_count(f->device), tracer_occupancy(f->device, fp64, L.threads, f->dev.n));
     }
     L.work_stride = tracer_work_stride(nr, L.elem);
     size_t o = 0;

@@ -537,7 +537,9 @@ struct FmmParams {
     int nbx, nby;
     int ok;                   // 1 while every table is complete (else the direct polish runs)
     int nocc;                 // occupied cells
+    int ncocc;                // occupied coarse cells (FMM_F x FMM_F cells each)
     int pool_used;            // near-list entries handed out
+    int cpool_used;           // coarse star-list entries handed out
     int cap, pool_cap;
 };
 
@@ -631,7 +633,9 @@ __global__ void fmm_setup_kernel(const float4* part, int nparts, float b_target,
     P->nby = min(max(nby, 1), FMM_G);
     P->ok = ok ? 1 : 0;
     P->nocc = 0;
+    P->ncocc = 0;
     P->pool_used = 0;
+    P->cpool_used = 0;
     P->cap = cap;
     P->pool_cap = pool_cap;
 }
@@ -668,15 +672,186 @@ __global__ void fmm_slot_kernel(FmmParams* P, const uint8_t* occ, int* slot, int
     slot[cell] = v;
 }
 
-// One CTA (FMM_WARPS warps) per occupied cell: near list in star order, local expansion
-// of the far stars (lane-private accumulators in shared memory, then a fixed-order sum),
-// truncation bound.
+// Local expansions of the occupied cells, two levels (each cell's expansion is the same
+// sum as with one level; only the work is organised differently):
+//   coarse cells of FMM_F x FMM_F cells; for a coarse cell X with centre C,
+//     Lc_k = -sum m_i / (z_i - C)^(k+1) over the stars outside X's 5x5 block of coarse cells
+//     (|z_i - C| >= 2.5 FMM_F b), and the stars inside that block are listed in star order;
+//   for each occupied cell B inside X, with centre c,
+//     L_k(B) = [Lc re-centred at c]_k + -sum m_i / (z_i - c)^(k+1) over the listed stars
+//     outside B's 5x5 block; the listed stars inside it form B's near list.
+// Re-centring a polynomial is exact (a Taylor shift, O(P^2)), so the far sum's truncation
+// error is that of Lc at the points (ratio <= (|c - C| + 0.72 b) / (2.5 FMM_F b) <= 0.28)
+// plus that of the direct part (ratio <= 0.72 b / 2.5 b); both enter the bound.  Work per
+// coarse cell: one pass over the N stars; per cell: the stars of the coarse block (about
+// 25 FMM_F^2 times the stars per cell) instead of all N.
 constexpr int FMM_WARPS = 4;
 constexpr int FMM_CT = FMM_WARPS * 32;
 constexpr int FMM_ACC = FMM_WARPS * FMM_P * 32;  // floats per accumulator component
-__global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const int2* boxlist, const float4* dfp,
-                                                           const float2* dfm, const float4* s32, int n,
-                                                           BoxInfo* info, float4* coeff, int* pool) {
+constexpr int FMM_F = 8;
+constexpr int FMM_CLIST = 8192;                  // stars of one coarse 5x5 block (more: direct polish)
+constexpr int FMM_COARSE_MAX = (FMM_G / FMM_F) * (FMM_G / FMM_F);
+constexpr int FMM_CPOOL = 1 << 23;               // coarse star-list entries (more: direct polish)
+
+__global__ void fmm_coarse_list_kernel(FmmParams* P, const uint8_t* occ, int2* clist) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (!P->ok) return;
+    const int nbx = P->nbx, nby = P->nby;
+    const int ncx = (nbx + FMM_F - 1) / FMM_F, ncy = (nby + FMM_F - 1) / FMM_F;
+    if (c >= (int64_t)ncx * ncy) return;
+    const int X = (int)(c % ncx), Y = (int)(c / ncx);
+    bool any = false;
+    for (int fy = Y * FMM_F; fy < min(nby, (Y + 1) * FMM_F) && !any; fy++)
+        for (int fx = X * FMM_F; fx < min(nbx, (X + 1) * FMM_F); fx++) any |= occ[(int64_t)fy * nbx + fx] != 0;
+    if (any) {
+        const int i = atomicAdd(&P->ncocc, 1);
+        if (i < FMM_COARSE_MAX) clist[i] = make_int2(X, Y);
+    }
+}
+
+// One star's contribution -m (z_i - c)^-(k+1), k < FMM_P, to this lane's accumulators, and
+// to the bound's sums.
+__device__ __forceinline__ void fmm_acc_star(float* acc, int warp, int lane, const float4 pd, const float2 md,
+                                             const df& cx, const df& cy, float& r2, float& dmin) {
+    const df dx = df_sub(df{pd.x, pd.y}, cx), dy = df_sub(df{pd.z, pd.w}, cy);
+    const df inv = df_rcp(df_add(df_sqr(dx), df_sqr(dy)));
+    const df ux = df_mul(dx, inv), uy = df_neg(df_mul(dy, inv));  // u = 1/(z_i - c)
+    df wx = df_mul(df{md.x, md.y}, ux), wy = df_mul(df{md.x, md.y}, uy);
+    const float dd = sqrtf(dx.hi * dx.hi + dy.hi * dy.hi);
+    r2 += md.x / (dd * dd);
+    dmin = fminf(dmin, dd);
+    for (int k = 0; k < FMM_P; k++) {
+        const int a = ((warp * FMM_P + k) << 5) + lane;
+        df ax = df{acc[a], acc[a + FMM_ACC]}, ay = df{acc[a + 2 * FMM_ACC], acc[a + 3 * FMM_ACC]};
+        ax = df_sub(ax, wx);
+        ay = df_sub(ay, wy);
+        acc[a] = ax.hi;
+        acc[a + FMM_ACC] = ax.lo;
+        acc[a + 2 * FMM_ACC] = ay.hi;
+        acc[a + 3 * FMM_ACC] = ay.lo;
+        const df nx = df_sub(df_mul(wx, ux), df_mul(wy, uy));  // w <- w u
+        const df ny = df_add(df_mul(wx, uy), df_mul(wy, ux));
+        wx = nx;
+        wy = ny;
+    }
+}
+
+// Sum of coefficient k over the lanes and warps, in a fixed order (thread k < FMM_P).
+__device__ __forceinline__ dfc fmm_acc_sum(const float* acc, int k) {
+    df sx = df{0.f, 0.f}, sy = df{0.f, 0.f};
+    for (int w = 0; w < FMM_WARPS; w++)
+        for (int l = 0; l < 32; l++) {
+            const int a = ((w * FMM_P + k) << 5) + l;
+            sx = df_add(sx, df{acc[a], acc[a + FMM_ACC]});
+            sy = df_add(sy, df{acc[a + 2 * FMM_ACC], acc[a + 3 * FMM_ACC]});
+        }
+    return dfc{sx, sy};
+}
+
+__device__ __forceinline__ float fmm_tail(float r2, float rho) {
+    // tail of -S1_far' after FMM_P terms: sum m/|d|^2 * P rho^(P-1) / (1 - rho)^2
+    if (!(r2 > 0.f)) return 0.f;
+    rho = fminf(rho, 0.99f);
+    return r2 * (float)FMM_P * powf(rho, (float)(FMM_P - 1)) / ((1.f - rho) * (1.f - rho));
+}
+
+// Pass 1: one CTA per occupied coarse cell X: the coarse expansion Lc of the stars outside
+// X's 5x5 coarse block, the bound's sums for them, and the block's stars in star order
+// (written to cpool; their count and offset to cinfo).
+struct CoarseInfo {
+    int off, cnt;     // star list in cpool
+    float r2, dmin;   // sum m/|z_i - C|^2 and min |z_i - C| over the stars outside the block
+};
+
+__global__ void __launch_bounds__(FMM_CT) fmm_coarse_kernel(FmmParams* P, const int2* clist, int* cslot,
+                                                            const float4* dfp, const float2* dfm, const float4* s32,
+                                                            int n, float4* cLc, CoarseInfo* cinfo, int* cpool,
+                                                            int cpool_cap) {
+    extern __shared__ __align__(16) float acc[];  // [4 components][warp][k][lane], then the star list
+    int* s_list = (int*)(acc + 4 * FMM_ACC);
+    __shared__ int s_wcnt[FMM_WARPS];
+    __shared__ int s_lcnt, s_off;
+    __shared__ float s_r2[FMM_CT], s_dmin[FMM_CT];
+    __shared__ int s_ok, s_ncocc;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_ok = P->ok;
+        s_ncocc = min(P->ncocc, FMM_COARSE_MAX);
+    }
+    __syncthreads();
+    if (!s_ok) return;  // block-uniform
+    const int ncx = (P->nbx + FMM_F - 1) / FMM_F;
+    const double b = (double)P->b;
+    for (int ci = blockIdx.x; ci < s_ncocc; ci += gridDim.x) {
+        const int2 X = clist[ci];
+        const double Cxd = (double)P->x0 + ((double)(X.x * FMM_F) + 0.5 * FMM_F) * b;
+        const double Cyd = (double)P->y0 + ((double)(X.y * FMM_F) + 0.5 * FMM_F) * b;
+        const df Cx = df_from_double(Cxd), Cy = df_from_double(Cyd);
+        for (int q = tid; q < 4 * FMM_ACC; q += FMM_CT) acc[q] = 0.f;
+        if (tid == 0) s_lcnt = 0;
+        float r2 = 0.f, dmin = 3.0e38f;
+        __syncthreads();
+        for (int j0 = 0; j0 < n; j0 += FMM_CT) {
+            const int j = j0 + tid;
+            bool nearc = false;
+            if (j < n) {
+                const float4 sp = s32[j];
+                const int sx = fmm_cell(sp.x, P->x0, P->inv_b) >> 3, sy = fmm_cell(sp.y, P->y0, P->inv_b) >> 3;
+                nearc = abs(sx - X.x) <= 2 && abs(sy - X.y) <= 2;
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, nearc);
+            if (lane == 0) s_wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int before = 0, total = 0;
+            for (int w = 0; w < FMM_WARPS; w++) {
+                if (w < warp) before += s_wcnt[w];
+                total += s_wcnt[w];
+            }
+            const int pos = s_lcnt + before + __popc(bal & ((1u << lane) - 1u));
+            if (nearc && pos < FMM_CLIST) s_list[pos] = j;
+            __syncthreads();
+            if (tid == 0) s_lcnt += total;
+            if (j < n && !nearc) fmm_acc_star(acc, warp, lane, dfp[j], dfm[j], Cx, Cy, r2, dmin);
+        }
+        s_r2[tid] = r2;
+        s_dmin[tid] = dmin;
+        __syncthreads();
+        const int lcnt = s_lcnt;
+        if (tid == 0) {
+            const int off = lcnt <= FMM_CLIST ? atomicAdd(&P->cpool_used, lcnt) : 0;
+            if (lcnt > FMM_CLIST || off + lcnt > cpool_cap) P->ok = 0;  // the direct polish takes over
+            s_off = off;
+            float R2 = 0.f, D = 3.0e38f;
+            for (int t = 0; t < FMM_CT; t++) {
+                R2 += s_r2[t];
+                D = fminf(D, s_dmin[t]);
+            }
+            CoarseInfo c;
+            c.off = off;
+            c.cnt = lcnt;
+            c.r2 = R2;
+            c.dmin = D;
+            cinfo[ci] = c;
+            cslot[X.y * ncx + X.x] = ci;
+        }
+        if (tid < FMM_P) {
+            const dfc L = fmm_acc_sum(acc, tid);
+            cLc[(size_t)ci * FMM_P + tid] = make_float4(L.x.hi, L.x.lo, L.y.hi, L.y.lo);
+        }
+        __syncthreads();
+        if (lcnt <= FMM_CLIST && s_off + lcnt <= cpool_cap)
+            for (int i = tid; i < lcnt; i += FMM_CT) cpool[s_off + i] = s_list[i];
+        __syncthreads();
+    }
+}
+
+// Pass 2: one CTA per occupied cell B (parent coarse cell X): near list, direct part of the
+// listed stars outside B's block, Lc re-centred at B's centre, bound.
+__global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const int2* boxlist, const int* cslot,
+                                                           const float4* cLc, const CoarseInfo* cinfo,
+                                                           const int* cpool, const float4* dfp, const float2* dfm,
+                                                           const float4* s32, BoxInfo* info, float4* coeff,
+                                                           int* pool) {
     extern __shared__ __align__(16) float acc[];  // [4 components][warp][k][lane]
     __shared__ int s_wcnt[FMM_WARPS];
     __shared__ int s_off, s_cnt;
@@ -689,18 +864,26 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
     }
     __syncthreads();
     if (!s_ok) return;  // block-uniform
-    const int nocc = s_nocc;
-    for (int box = blockIdx.x; box < nocc; box += gridDim.x) {
+    const int ncx = (P->nbx + FMM_F - 1) / FMM_F;
+    const double b = (double)P->b;
+    for (int box = blockIdx.x; box < s_nocc; box += gridDim.x) {
         const int2 bc = boxlist[box];
-        const double cxd = (double)P->x0 + ((double)bc.x + 0.5) * (double)P->b;
-        const double cyd = (double)P->y0 + ((double)bc.y + 0.5) * (double)P->b;
+        const int fx = bc.x, fy = bc.y;
+        const int ci = cslot[(fy / FMM_F) * ncx + fx / FMM_F];
+        const CoarseInfo cI = cinfo[ci];
+        const int* list = cpool + cI.off;
+        const int lcnt = cI.cnt;
+        const double Cxd = (double)P->x0 + ((double)((fx / FMM_F) * FMM_F) + 0.5 * FMM_F) * b;
+        const double Cyd = (double)P->y0 + ((double)((fy / FMM_F) * FMM_F) + 0.5 * FMM_F) * b;
+        const double cxd = (double)P->x0 + ((double)fx + 0.5) * b;
+        const double cyd = (double)P->y0 + ((double)fy + 0.5) * b;
         const df cx = df_from_double(cxd), cy = df_from_double(cyd);
         // near list: count, reserve, ordered write
         int cnt = 0;
-        for (int j = tid; j < n; j += FMM_CT) {
-            const float4 sp = s32[j];
+        for (int i = tid; i < lcnt; i += FMM_CT) {
+            const float4 sp = s32[list[i]];
             const int sx = fmm_cell(sp.x, P->x0, P->inv_b), sy = fmm_cell(sp.y, P->y0, P->inv_b);
-            cnt += (abs(sx - bc.x) <= FMM_K && abs(sy - bc.y) <= FMM_K);
+            cnt += (abs(sx - fx) <= FMM_K && abs(sy - fy) <= FMM_K);
         }
         for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
         if (lane == 0) s_wcnt[warp] = cnt;
@@ -713,16 +896,20 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
             s_off = off;
             s_cnt = tot;
         }
+        for (int q = tid; q < 4 * FMM_ACC; q += FMM_CT) acc[q] = 0.f;
         __syncthreads();
         const bool room = s_off + s_cnt <= P->pool_cap;
         int base = 0;
-        for (int j0 = 0; j0 < n; j0 += FMM_CT) {
-            const int j = j0 + tid;
+        float r2i = 0.f, dmi = 3.0e38f;
+        for (int i0 = 0; i0 < lcnt; i0 += FMM_CT) {
+            const int i = i0 + tid;
             bool nr_ = false;
-            if (j < n) {
+            int j = 0;
+            if (i < lcnt) {
+                j = list[i];
                 const float4 sp = s32[j];
                 const int sx = fmm_cell(sp.x, P->x0, P->inv_b), sy = fmm_cell(sp.y, P->y0, P->inv_b);
-                nr_ = abs(sx - bc.x) <= FMM_K && abs(sy - bc.y) <= FMM_K;
+                nr_ = abs(sx - fx) <= FMM_K && abs(sy - fy) <= FMM_K;
             }
             const unsigned bal = __ballot_sync(0xffffffffu, nr_);
             if (lane == 0) s_wcnt[warp] = __popc(bal);
@@ -735,51 +922,31 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
             if (nr_ && room) pool[s_off + base + before + __popc(bal & ((1u << lane) - 1u))] = j;
             base += total;
             __syncthreads();
+            if (i < lcnt && !nr_) fmm_acc_star(acc, warp, lane, dfp[j], dfm[j], cx, cy, r2i, dmi);
         }
-        // far stars: lane-private accumulation of L_k = -sum m u^(k+1), u = 1/(z_i - c)
-        for (int q = tid; q < 4 * FMM_ACC; q += FMM_CT) acc[q] = 0.f;
-        float r2 = 0.f, dmin = 3.0e38f;
-        __syncthreads();
-        for (int j = tid; j < n; j += FMM_CT) {
-            const float4 sp = s32[j];
-            const int sx = fmm_cell(sp.x, P->x0, P->inv_b), sy = fmm_cell(sp.y, P->y0, P->inv_b);
-            if (abs(sx - bc.x) <= FMM_K && abs(sy - bc.y) <= FMM_K) continue;
-            const float4 pd = dfp[j];
-            const float2 md = dfm[j];
-            const df dx = df_sub(df{pd.x, pd.y}, cx), dy = df_sub(df{pd.z, pd.w}, cy);
-            const df inv = df_rcp(df_add(df_sqr(dx), df_sqr(dy)));
-            const df ux = df_mul(dx, inv), uy = df_neg(df_mul(dy, inv));  // u = 1/(z_i - c)
-            df wx = df_mul(df{md.x, md.y}, ux), wy = df_mul(df{md.x, md.y}, uy);
-            const float dd = sqrtf(dx.hi * dx.hi + dy.hi * dy.hi);
-            r2 += md.x / (dd * dd);
-            dmin = fminf(dmin, dd);
-            for (int k = 0; k < FMM_P; k++) {
-                const int a = ((warp * FMM_P + k) << 5) + lane;
-                df ax = df{acc[a], acc[a + FMM_ACC]}, ay = df{acc[a + 2 * FMM_ACC], acc[a + 3 * FMM_ACC]};
-                ax = df_sub(ax, wx);
-                ay = df_sub(ay, wy);
-                acc[a] = ax.hi;
-                acc[a + FMM_ACC] = ax.lo;
-                acc[a + 2 * FMM_ACC] = ay.hi;
-                acc[a + 3 * FMM_ACC] = ay.lo;
-                const df nx = df_sub(df_mul(wx, ux), df_mul(wy, uy));  // w <- w u
-                const df ny = df_add(df_mul(wx, uy), df_mul(wy, ux));
-                wx = nx;
-                wy = ny;
-            }
-        }
-        s_r2[tid] = r2;
-        s_dmin[tid] = dmin;
+        s_r2[tid] = r2i;
+        s_dmin[tid] = dmi;
         __syncthreads();
         if (tid < FMM_P) {
-            df sx = df{0.f, 0.f}, sy = df{0.f, 0.f};
-            for (int w = 0; w < FMM_WARPS; w++)
-                for (int l = 0; l < 32; l++) {
-                    const int a = ((w * FMM_P + tid) << 5) + l;
-                    sx = df_add(sx, df{acc[a], acc[a + FMM_ACC]});
-                    sy = df_add(sy, df{acc[a + 2 * FMM_ACC], acc[a + 3 * FMM_ACC]});
-                }
-            coeff[(size_t)box * FMM_P + tid] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
+            // Lc re-centred at c (Taylor shift by t0 = c - C: Horner in t0 with binomial
+            // weights C(k, j)), plus the direct part
+            const int jk = tid;
+            const float4* Lc = cLc + (size_t)ci * FMM_P;
+            const df tx = df_from_double(cxd - Cxd), ty = df_from_double(cyd - Cyd);
+            double bin = 1.0;  // C(P-1, jk)
+            for (int i = 0; i < jk; i++) bin = bin * (double)(FMM_P - 1 - i) / (double)(i + 1);
+            const float4 top = Lc[FMM_P - 1];
+            dfc sacc = dfc{df_mul(df_from_double(bin), df{top.x, top.y}), df_mul(df_from_double(bin), df{top.z, top.w})};
+            for (int k = FMM_P - 2; k >= jk; k--) {
+                bin = bin * (double)(k + 1 - jk) / (double)(k + 1);  // C(k, jk) from C(k+1, jk)
+                const float4 lk = Lc[k];
+                sacc = dfc_mul(sacc, dfc{tx, ty});
+                sacc.x = df_add(sacc.x, df_mul(df_from_double(bin), df{lk.x, lk.y}));
+                sacc.y = df_add(sacc.y, df_mul(df_from_double(bin), df{lk.z, lk.w}));
+            }
+            const dfc Ld = fmm_acc_sum(acc, jk);
+            const df lx = df_add(sacc.x, Ld.x), ly = df_add(sacc.y, Ld.y);
+            coeff[(size_t)box * FMM_P + jk] = make_float4(lx.hi, lx.lo, ly.hi, ly.lo);
         }
         if (tid == 0) {
             float R2 = 0.f, D = 3.0e38f;
@@ -791,14 +958,9 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
             bi.c = make_float4(cx.hi, cx.lo, cy.hi, cy.lo);
             bi.near_off = s_off;
             bi.near_cnt = room ? s_cnt : 0;
-            // |z - c| <= 0.72 b (half-diagonal plus the Newton steps); the tail of -S1_far'
-            // after P terms is at most sum_far m/|d|^2 * P rho^(P-1) / (1 - rho)^2
-            float s2e = 0.f;
-            if (R2 > 0.f) {
-                const float rho = fminf(0.72f * P->b / D, 0.99f);
-                s2e = R2 * (float)FMM_P * powf(rho, (float)(FMM_P - 1)) / ((1.f - rho) * (1.f - rho));
-            }
-            bi.s2_err = s2e;
+            // points lie within 0.72 b of c (half-diagonal plus the Newton steps)
+            const float tc = (float)sqrt((cxd - Cxd) * (cxd - Cxd) + (cyd - Cyd) * (cyd - Cyd));
+            bi.s2_err = fmm_tail(R2, 0.72f * P->b / D) + fmm_tail(cI.r2, (tc + 0.72f * P->b) / cI.dmin);
             bi.pad = 0.f;
             info[box] = bi;
         }
@@ -908,6 +1070,11 @@ size_t fmm_workspace_bytes(int64_t points) {
     add(sizeof(BoxInfo) * cap);
     add(sizeof(float4) * FMM_P * cap);
     add(sizeof(int) * pool);
+    add(sizeof(int2) * (size_t)FMM_COARSE_MAX);  // occupied coarse cells
+    add(sizeof(int) * (size_t)FMM_COARSE_MAX);   // coarse slots
+    add(sizeof(float4) * FMM_P * (size_t)FMM_COARSE_MAX);
+    add(sizeof(CoarseInfo) * (size_t)FMM_COARSE_MAX);
+    add(sizeof(int) * (size_t)FMM_CPOOL);
     return b;
 }
 
@@ -929,18 +1096,29 @@ cudaError_t launch_polish_fmm(const PolishArgs& a, void* ws, cudaStream_t st) {
     BoxInfo* info = (BoxInfo*)take(sizeof(BoxInfo) * cap);
     float4* coeff = (float4*)take(sizeof(float4) * FMM_P * (size_t)cap);
     int* pool = (int*)take(sizeof(int) * (size_t)pool_cap);
+    int2* clist = (int2*)take(sizeof(int2) * (size_t)FMM_COARSE_MAX);
+    int* cslot = (int*)take(sizeof(int) * (size_t)FMM_COARSE_MAX);
+    float4* cLc = (float4*)take(sizeof(float4) * FMM_P * (size_t)FMM_COARSE_MAX);
+    CoarseInfo* cinfo = (CoarseInfo*)take(sizeof(CoarseInfo) * (size_t)FMM_COARSE_MAX);
+    int* cpool = (int*)take(sizeof(int) * (size_t)FMM_CPOOL);
     cudaError_t e;
     fmm_extent_kernel<<<512, 256, 0, st>>>(a.zrows, points, part);
     fmm_setup_kernel<<<1, 32, 0, st>>>(part, 512, a.f->fmm_cell, cap, pool_cap, P);
     if ((e = cudaMemsetAsync(occ, 0, (size_t)FMM_G * FMM_G, st)) != cudaSuccess) return e;
     fmm_occupy_kernel<<<(unsigned)((points + 255) / 256), 256, 0, st>>>(a.zrows, points, P, occ);
     fmm_slot_kernel<<<(unsigned)(((int64_t)FMM_G * FMM_G + 255) / 256), 256, 0, st>>>(P, occ, slot, boxlist);
-    const size_t csmem = sizeof(float) * 4 * FMM_ACC;
-    if ((e = cudaFuncSetAttribute(fmm_coeff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem)) !=
-        cudaSuccess)
+    fmm_coarse_list_kernel<<<(unsigned)((FMM_COARSE_MAX + 255) / 256), 256, 0, st>>>(P, occ, clist);
+    const size_t csmem1 = sizeof(float) * 4 * FMM_ACC + sizeof(int) * FMM_CLIST;
+    const size_t csmem2 = sizeof(float) * 4 * FMM_ACC;
+    if ((e = cudaFuncSetAttribute(fmm_coarse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem1)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(fmm_coeff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem2)) !=
+            cudaSuccess)
         return e;
-    fmm_coeff_kernel<<<1216, FMM_CT, csmem, st>>>(P, boxlist, a.f->star_dfp, a.f->star_dfm, a.f->star32,
-                                                  (int)a.f->n, info, coeff, pool);
+    fmm_coarse_kernel<<<608, FMM_CT, csmem1, st>>>(P, clist, cslot, a.f->star_dfp, a.f->star_dfm, a.f->star32,
+                                                   (int)a.f->n, cLc, cinfo, cpool, FMM_CPOOL);
+    fmm_coeff_kernel<<<1216, FMM_CT, csmem2, st>>>(P, boxlist, cslot, cLc, cinfo, cpool, a.f->star_dfp, a.f->star_dfm,
+                                                   a.f->star32, info, coeff, pool);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     PolishK K = make_polish_k(a);
     const int64_t warps = ((a.m + 1 + 31) / 32) * a.nr;
