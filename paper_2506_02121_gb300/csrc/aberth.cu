@@ -146,6 +146,40 @@ __device__ __forceinline__ void acc_root_f(float zx, float zy, float rx, float r
     Dy = fmaf(-dy, inv, Dy);
 }
 
+// Packed FP32 pairs (two IEEE FP32 operations per instruction, round to nearest).
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p f2_pack(float a, float b) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2p v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2p f2_sub(f2p a, f2p b) {
+    f2p r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2p f2_fma(f2p a, f2p b, f2p c) {
+    f2p r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Two other roots at once, (x1, x2), (y1, y2): D += 1/(z - z_1) + 1/(z - z_2), kept as
+// packed partial sums Dx2 = (.., ..), Dy2 accumulating +dy/|d|^2 (D_y = -(sum)).
+__device__ __forceinline__ void acc_root_f2(f2p zxx, f2p zyy, f2p px, f2p py, f2p& Dx2, f2p& Dy2) {
+    const f2p eps = f2_pack(1e-30f, 1e-30f);
+    const f2p dx = f2_sub(zxx, px), dy = f2_sub(zyy, py);
+    const f2p r2 = f2_fma(dx, dx, f2_fma(dy, dy, eps));
+    float ra, rb;
+    f2_unpack(r2, ra, rb);
+    const f2p inv = f2_pack(rcp_approx(ra), rcp_approx(rb));
+    Dx2 = f2_fma(dx, inv, Dx2);
+    Dy2 = f2_fma(dy, inv, Dy2);
+}
+
 // 16-byte load from shared memory (two FP32 roots); a warp that reads one address gets it
 // by broadcast.
 __device__ __forceinline__ float4 lds_f4(unsigned addr) {
@@ -351,33 +385,56 @@ __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool
                 }
             }
         }
+        f2p zxx[R], zyy[R], Dx2[R], Dy2[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            zxx[r] = f2_pack(z[r].x, z[r].x);
+            zyy[r] = f2_pack(z[r].y, z[r].y);
+            Dx2[r] = f2_pack(0.f, 0.f);
+            Dy2[r] = f2_pack(0.f, 0.f);
+        }
         for (int t0 = 0; t0 < nr; t0 += TR) {
             const int tn = min(TR, nr - t0);
+            const int tp = (tn + 1) >> 1;  // root pairs in the tile (an odd tail pairs with a root at 1e30)
             __syncthreads();
-            for (int j = tid; j < tn; j += P) {
+            for (int j = tid; j < 2 * tp; j += P) {
+                // pair-interleaved tile: pair i = (x_2i, x_2i+1, y_2i, y_2i+1)
+                float* s0 = (float*)(x.s_root) + 4 * (j >> 1) + (j & 1);
+                float* s1 = (float*)(x.s_root + TR) + 4 * (j >> 1) + (j & 1);
                 // L2 loads: in a cluster, other SMs wrote these positions since the last sweep
-                if (a0) x.s_root[j] = __ldcg(&x.cur[t0 + j]);
-                if (a1) x.s_root[TR + j] = __ldcg(&x.cur[nr + t0 + j]);
+                C v0 = make_float2(1e30f, 1e30f), v1 = v0;
+                if (j < tn) {
+                    if (a0) v0 = __ldcg(&x.cur[t0 + j]);
+                    if (a1) v1 = __ldcg(&x.cur[nr + t0 + j]);
+                }
+                if (a0) {
+                    s0[0] = v0.x;
+                    s0[2] = v0.y;
+                }
+                if (a1) {
+                    s1[0] = v1.x;
+                    s1[2] = v1.y;
+                }
             }
             __syncthreads();
             if (any) {
                 const unsigned base = (unsigned)__cvta_generic_to_shared(x.s_root + d * TR);
-                const int tn2 = tn >> 1;
-#pragma unroll 2
-                for (int j2 = 0; j2 < tn2; j2++) {
+#pragma unroll 8
+                for (int j2 = 0; j2 < tp; j2++) {
                     const float4 p = lds_f4(base + 16u * (unsigned)j2);
+                    const f2p px = f2_pack(p.x, p.y), py = f2_pack(p.z, p.w);
 #pragma unroll
-                    for (int r = 0; r < R; r++) {
-                        acc_root_f(z[r].x, z[r].y, p.x, p.y, acc[r].Dx, acc[r].Dy);
-                        acc_root_f(z[r].x, z[r].y, p.z, p.w, acc[r].Dx, acc[r].Dy);
-                    }
-                }
-                if (tn & 1) {
-                    const C p = x.s_root[d * TR + tn - 1];
-#pragma unroll
-                    for (int r = 0; r < R; r++) acc_root_f(z[r].x, z[r].y, p.x, p.y, acc[r].Dx, acc[r].Dy);
+                    for (int r = 0; r < R; r++) acc_root_f2(zxx[r], zyy[r], px, py, Dx2[r], Dy2[r]);
                 }
             }
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            float a, b, c2, d2;
+            f2_unpack(Dx2[r], a, b);
+            f2_unpack(Dy2[r], c2, d2);
+            acc[r].Dx += a + b;
+            acc[r].Dy -= c2 + d2;
         }
 #pragma unroll
         for (int r = 0; r < R; r++)
