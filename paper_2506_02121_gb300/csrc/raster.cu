@@ -180,15 +180,29 @@ __global__ void __launch_bounds__(XS_THREADS) crossing_scatter_kernel(CrossK K) 
         const double py = pix(K.y0, K.sy, r);
         if (!(ylo <= py && py < yhi)) continue;  // exact half-open row test
         const int sgn = up ? 1 : -1;
-        // prefix length c: centres with orient(a, b, P) == sgn; FP32 estimate, exact settle
+        // prefix length c: the centres with orient(a, b, P) == sgn are those left of the
+        // crossing abscissa xc, i.e. with index i < u = (xc - x0)/sx - 0.5, so c = ceil(u).
+        // u in FP32 from FP64 differences; its error is at most
+        //   (2.4e-7 |x_a - x0| + 5e-7 |x_b - x_a|) / sx + 6e-8 (|u| + 0.5)
+        // (each difference rounded once to FP32, |t| <= 1, IEEE division and products); with
+        // no centre index within 4x that bound of u the count is settled, else the exact
+        // orientation predicate settles it.
+        const float sxr = (float)(sa.x - K.x0);
         const float exf = (float)(sb.x - sa.x), eyf = (float)(sb.y - sa.y);
-        const float xcf = (float)sa.x + exf * ((float)(py - sa.y) / eyf);
-        float ce = ceilf((xcf - K.x0f) * K.inv_sxf - 0.5f);
-        ce = fminf(fmaxf(ce, 0.0f), (float)K.W);
-        if (!(ce == ce)) ce = 0.0f;  // NaN guard
-        int64_t c = (int64_t)ce;
-        while (c > 0 && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c - 1), py) != sgn) c--;
-        while (c < K.W && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c), py) == sgn) c++;
+        const float tf = __fdiv_rn((float)(py - sa.y), eyf);
+        const float u = __fsub_rn(__fmul_rn(__fadd_rn(sxr, __fmul_rn(exf, tf)), K.inv_sxf), 0.5f);
+        const float err = 4.0f * ((4e-7f * (fabsf(sxr) + fabsf(exf))) * K.inv_sxf + 2.4e-7f * fabsf(u) + 1e-6f);
+        int64_t c;
+        if (isfinite(u) && isfinite(err) && ceilf(u - err) == ceilf(u + err)) {
+            c = (int64_t)fminf(fmaxf(ceilf(u), 0.0f), (float)K.W);
+        } else {
+            float ce = ceilf(u);
+            ce = fminf(fmaxf(ce, 0.0f), (float)K.W);
+            if (!(ce == ce)) ce = 0.0f;  // NaN guard
+            c = (int64_t)ce;
+            while (c > 0 && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c - 1), py) != sgn) c--;
+            while (c < K.W && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c), py) == sgn) c++;
+        }
         if (c > 0) atomicAdd(&K.D[r * K.W + (c - 1)], sgn);
     }
 }
