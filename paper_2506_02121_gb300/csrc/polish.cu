@@ -529,6 +529,7 @@ cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st) {
 // asynchronous.
 // ----------------------------------------------------------------------------------
 constexpr int FMM_P = 32;
+constexpr int FMM_K0 = 20;  // expansion terms k >= FMM_K0 evaluated in FP32 (see fmm_polish_kernel)
 constexpr int FMM_K = 2;
 constexpr int FMM_G = 2048;
 
@@ -763,6 +764,16 @@ struct CoarseInfo {
     float r2, dmin;   // sum m/|z_i - C|^2 and min |z_i - C| over the stars outside the block
 };
 
+// Rounding of the FP32 Horner steps (terms k >= FMM_K0) in S2: their sum of magnitudes is
+// at most sum m/|d|^2 * K0 rho^(K0-1) / (1 - rho)^2; complex Horner in FP32 over
+// FMM_P - FMM_K0 steps errs by at most 4 (FMM_P - FMM_K0) 2^-24 of it.
+__device__ __forceinline__ float fmm_fp32_part(float r2, float rho) {
+    if (!(r2 > 0.f)) return 0.f;
+    rho = fminf(rho, 0.99f);
+    const float mag = r2 * (float)FMM_K0 * powf(rho, (float)(FMM_K0 - 1)) / ((1.f - rho) * (1.f - rho));
+    return mag * (4.0f * (float)(FMM_P - FMM_K0) * 5.97e-8f);
+}
+
 __global__ void __launch_bounds__(FMM_CT) fmm_coarse_kernel(FmmParams* P, const int2* clist, int* cslot,
                                                             const float4* dfp, const float2* dfm, const float4* s32,
                                                             int n, float4* cLc, CoarseInfo* cinfo, int* cpool,
@@ -960,7 +971,9 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
             bi.near_cnt = room ? s_cnt : 0;
             // points lie within 0.72 b of c (half-diagonal plus the Newton steps)
             const float tc = (float)sqrt((cxd - Cxd) * (cxd - Cxd) + (cyd - Cyd) * (cyd - Cyd));
-            bi.s2_err = fmm_tail(R2, 0.72f * P->b / D) + fmm_tail(cI.r2, (tc + 0.72f * P->b) / cI.dmin);
+            const float rho1 = 0.72f * P->b / D, rho2 = (tc + 0.72f * P->b) / cI.dmin;
+            bi.s2_err = fmm_tail(R2, rho1) + fmm_tail(cI.r2, rho2) +
+                        fmm_fp32_part(R2, rho1) + fmm_fp32_part(cI.r2, rho2);
             bi.pad = 0.f;
             info[box] = bi;
         }
@@ -1007,12 +1020,32 @@ __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const
         }
         // far field: Horner with derivatives in t = z - c
         const df tx = tf_sub(zxt, bi.c.x, bi.c.y, 0.f), ty = tf_sub(zyt, bi.c.z, bi.c.w, 0.f);
-        const float4 top = L[FMM_P - 1];
-        df b0x = df{top.x, top.y}, b0y = df{top.z, top.w};
-        df b1x = df{0.f, 0.f}, b1y = df{0.f, 0.f};
-        float b2x = 0.f, b2y = 0.f, b3x = 0.f, b3y = 0.f;
+        // Horner steps FMM_P-2 .. FMM_K0 in FP32: the terms k >= FMM_K0 carry at most
+        // R2 K0 rho^(K0-1) / (1 - rho)^2 of S2 (and less of S1), so their FP32 rounding
+        // is negligible and enters the bound; the steps below in double-float
         const float tfx = tx.hi, tfy = ty.hi;
-        for (int kk = FMM_P - 2; kk >= 0; kk--) {
+        const float4 top = L[FMM_P - 1];
+        float h0x = top.x, h0y = top.z, h1x = 0.f, h1y = 0.f;
+        float b2x = 0.f, b2y = 0.f, b3x = 0.f, b3y = 0.f;
+#pragma unroll
+        for (int kk = FMM_P - 2; kk >= FMM_K0; kk--) {
+            const float n3x = fmaf(b3x, tfx, fmaf(-b3y, tfy, b2x)), n3y = fmaf(b3x, tfy, fmaf(b3y, tfx, b2y));
+            const float n2x = fmaf(b2x, tfx, fmaf(-b2y, tfy, h1x)), n2y = fmaf(b2x, tfy, fmaf(b2y, tfx, h1y));
+            const float n1x = fmaf(h1x, tfx, fmaf(-h1y, tfy, h0x)), n1y = fmaf(h1x, tfy, fmaf(h1y, tfx, h0y));
+            const float4 Lk = L[kk];
+            const float n0x = fmaf(h0x, tfx, fmaf(-h0y, tfy, Lk.x)), n0y = fmaf(h0x, tfy, fmaf(h0y, tfx, Lk.z));
+            b3x = n3x;
+            b3y = n3y;
+            b2x = n2x;
+            b2y = n2y;
+            h1x = n1x;
+            h1y = n1y;
+            h0x = n0x;
+            h0y = n0y;
+        }
+        df b0x = df{h0x, 0.f}, b0y = df{h0y, 0.f};
+        df b1x = df{h1x, 0.f}, b1y = df{h1y, 0.f};
+        for (int kk = FMM_K0 - 1; kk >= 0; kk--) {
             // b3 <- b3 t + b2 ; b2 <- b2 t + b1 ; b1 <- b1 t + b0 ; b0 <- b0 t + L_k
             const float n3x = fmaf(b3x, tfx, fmaf(-b3y, tfy, b2x)), n3y = fmaf(b3x, tfy, fmaf(b3y, tfx, b2y));
             const float n2x = fmaf(b2x, tfx, fmaf(-b2y, tfy, b1x.hi)), n2y = fmaf(b2x, tfy, fmaf(b2y, tfx, b1y.hi));
