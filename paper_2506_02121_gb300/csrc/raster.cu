@@ -18,6 +18,8 @@
 // exact integer fractions).
 #include <float.h>
 
+#include <algorithm>
+
 #include "cc_internal.h"
 
 namespace ccg {
@@ -373,7 +375,16 @@ __device__ __forceinline__ bool edt_keep(int u, long long cu, int v, long long c
     return (cw - cv) * (long long)(v - u) > (cv - cu) * (long long)(w - v);
 }
 
-__global__ void __launch_bounds__(32) edt_row_band_kernel(const int32_t* g, int W, double pixel, double* d_out) {
+// sqrt(k) for k < T by the same IEEE FP64 square root the row pass would take, so that a
+// table hit returns the same bits (squared distances are integers).
+constexpr int EDT_SQRT_T = 65536;
+__global__ void edt_sqrt_table_kernel(double* tab, int T) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < T) tab[k] = sqrt((double)k);
+}
+
+__global__ void __launch_bounds__(32) edt_row_band_kernel(const int32_t* g, int W, double pixel, double* d_out,
+                                                          const double* sqtab, int T) {
     extern __shared__ uint16_t edt_sh[];
     __shared__ int s_lo[32], s_hi[32];
     const int r = blockIdx.x, lane = threadIdx.x;
@@ -513,7 +524,7 @@ __global__ void __launch_bounds__(32) edt_row_band_kernel(const int32_t* g, int 
                 cq = c2;
             }
             const long long d2 = (long long)(i - q) * (i - q) + (long long)gq * gq;
-            out[i] = pixel * sqrt((double)d2);
+            out[i] = pixel * (d2 < T ? sqtab[d2] : sqrt((double)d2));
         }
         const int last = min(31, W - 1 - t0);
         cl = __shfl_sync(0xffffffffu, L, last);
@@ -636,8 +647,9 @@ size_t distance_workspace_bytes(int32_t W, int32_t H) {
 }
 
 // Scratch: plane 0 = g (int32 per pixel); plane 1 = feature flags (bytes) during the
-// column pass, then the envelope stacks of the global-memory row pass.  The chunk
-// summaries of the column pass live in d_out, which the row pass overwrites entirely.
+// column pass, then the square-root table of the band row pass (or the envelope stacks of
+// the global-memory row pass).  The chunk summaries of the column pass live in d_out, which
+// the row pass overwrites entirely.
 cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel,
                                 double* d_out, void* ws, cudaStream_t st) {
     const size_t plane = ((size_t)W * H * sizeof(int32_t) + 255) / 256 * 256;
@@ -656,10 +668,14 @@ cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (W <= EDT_BAND_MAX_W && H <= EDT_BAND_MAX_H) {
+        // square-root table in plane 1 (the row pass needs no stacks there)
+        const int T = (int)std::min<size_t>((size_t)EDT_SQRT_T, plane / sizeof(double));
+        double* sqtab = (double*)v;
+        edt_sqrt_table_kernel<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(sqtab, T);
         const size_t smem = edt_band_smem(W);
         e = cudaFuncSetAttribute(edt_row_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        edt_row_band_kernel<<<(unsigned)H, 32, smem, st>>>(g, W, pixel, d_out);
+        edt_row_band_kernel<<<(unsigned)H, 32, smem, st>>>(g, W, pixel, d_out, sqtab, T);
     } else {
         edt_row_kernel<<<(unsigned)((H + 63) / 64), 64, 0, st>>>(g, W, H, pixel, v, d_out);
     }
