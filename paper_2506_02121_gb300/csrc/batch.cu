@@ -152,6 +152,12 @@ int cc_batch_create(cc_field* const* fields, int32_t count, const int64_t* m, in
             delete b;
             return berr(CC_EINVAL, "cc_batch_create: all fields must live on one device");
         }
+        // the field's uploads and tables were enqueued on stream 0: finished before any
+        // batched launch (which may be captured into a graph)
+        if (fd->ready && cudaEventSynchronize(fd->ready) != cudaSuccess) {
+            delete b;
+            return berr(CC_ECUDA, "cc_batch_create: field set-up failed");
+        }
         b->fields.push_back(fields[f]);
         b->dev.push_back(*fd);
         b->m.push_back(m[f]);

@@ -18,9 +18,11 @@ struct cc_field {
     FieldDev dev;
     cc_options opt;
     int device;
-    DevReport* d_rep;
-    cudaEvent_t done;
-    cudaEvent_t ev[4];  // stage boundaries: start, after trace, after join, end
+    void* block = nullptr;      // the one device allocation of the field
+    DevReport* d_rep = nullptr;
+    cudaEvent_t ready = nullptr;  // stars and tables on the device
+    cudaEvent_t done = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage boundaries: start, after trace, after join, end
     bool solved;
     int64_t last_m;
     int last_S;
@@ -322,52 +324,11 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
     for (int64_t i = 0; i < n; i++) r2max = std::max(r2max, (hx[i] - mx) * (hx[i] - mx) + (hy[i] - my) * (hy[i] - my));
     const double density = r2max > 0.0 ? (double)n / (3.14159265358979323846 * r2max) : 0.0;
     const float fmm_cell = density > 0.0 ? (float)std::sqrt(6.0 / (25.0 * density)) : 1.0f;
-    cc_field* f = new cc_field();
-    f->opt = o;
-    f->dev.fmm_cell = fmm_cell;
-    f->dev.n = n;
-    f->dev.nr = 2 * n + (rect ? 2 * hpoly.K : 0);
-    f->dev.poly = nullptr;
-    f->dev.poly_K = rect ? hpoly.K : 0;
-    f->dev.kappa_s = kappa_s;
-    f->dev.gamma = gamma;
-    f->dev.unit_mass = unit;
-    f->solved = false;
-    cudaGetDevice(&f->device);
-    cudaError_t e = cudaSuccess;
-    e = e ? e : cudaMalloc(&f->dev.star32, sizeof(float4) * n);
-    e = e ? e : cudaMalloc(&f->dev.star64, sizeof(StarD) * n);
-    e = e ? e : cudaMalloc(&f->dev.star_dfp, sizeof(float4) * n);
-    e = e ? e : cudaMalloc(&f->dev.star_dfm, sizeof(float2) * n);
-    e = e ? e : cudaMalloc(&f->dev.star_tf, sizeof(float2) * n);
-    e = e ? e : cudaMalloc(&f->d_rep, sizeof(DevReport));
-    e = e ? e : cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming);
-    for (int i = 0; i < 4; i++) e = e ? e : cudaEventCreate(&f->ev[i]);
-    if (e != cudaSuccess) {
-        cc_field_destroy(f);
-        return fail(e == cudaErrorMemoryAllocation ? CC_ENOMEM : CC_ECUDA, "cc_field_create: %s", cudaGetErrorString(e));
-    }
-    e = e ? e : cudaMemcpy(f->dev.star32, s32.data(), sizeof(float4) * n, cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemcpy(f->dev.star64, s64.data(), sizeof(StarD) * n, cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemcpy(f->dev.star_dfp, sdp.data(), sizeof(float4) * n, cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemcpy(f->dev.star_dfm, sdm.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemcpy(f->dev.star_tf, stf.data(), sizeof(float2) * n, cudaMemcpyHostToDevice);
-    e = e ? e : cudaMemset(f->d_rep, 0, sizeof(DevReport));
-    if (rect && e == cudaSuccess) {
-        SmoothPoly* dp = nullptr;
-        e = cudaMalloc(&dp, sizeof(SmoothPoly));
-        if (e == cudaSuccess) {
-            f->dev.poly = dp;
-            e = cudaMemcpy(dp, &hpoly, sizeof(SmoothPoly), cudaMemcpyHostToDevice);
-        }
-    }
-    if (e != cudaSuccess) {
-        cc_field_destroy(f);
-        return cuda_fail(e, "cc_field_create upload");
-    }
-    // tracer far-field tables: cells of the polish cell size over the stars' bounding box
+    // tracer far-field grid: cells of the polish cell size over the stars' bounding box
     // plus three cells on every side (roots outside sum every star directly)
-    f->dev.tfmm.ok = 0;
+    TfmmParams tp;
+    std::memset(&tp, 0, sizeof tp);
+    size_t tcells = 0;
     if (o.far_field && n >= FMM_MIN_STARS) {
         float xmn = s32[0].x, xmx = s32[0].x, ymn = s32[0].y, ymx = s32[0].y;
         for (int64_t i = 1; i < n; i++) {
@@ -379,25 +340,83 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
         float b = fmm_cell > 0.f ? fmm_cell : 1.0f;
         const float span = std::max(xmx - xmn, ymx - ymn);
         if (span / b + 8.0f > 512.0f) b = span / 504.0f;
-        TfmmParams P;
-        P.b = b;
-        P.inv_b = 1.0f / b;
-        P.x0 = xmn - 3.0f * b;
-        P.y0 = ymn - 3.0f * b;
-        P.nbx = (int)std::ceil((xmx - P.x0) * P.inv_b) + 4;
-        P.nby = (int)std::ceil((ymx - P.y0) * P.inv_b) + 4;
-        P.ok = 1;
-        const size_t cells = (size_t)P.nbx * P.nby;
-        e = cudaMalloc(&f->dev.tcells, sizeof(TCell) * cells);
-        e = e ? e : cudaMalloc(&f->dev.tnear, sizeof(int) * cells * TFMM_NEAR_MAX);
-        e = e ? e : cudaMalloc(&f->dev.tcoeff, sizeof(float4) * cells * TFMM_P);
-        e = e ? e : launch_tracer_far_field(f->dev.star32, (int)n, P, f->dev.tcells, f->dev.tnear, f->dev.tcoeff, 0);
-        e = e ? e : cudaDeviceSynchronize();
-        if (e != cudaSuccess) {
-            cc_field_destroy(f);
-            return cuda_fail(e, "cc_field_create far-field tables");
-        }
-        f->dev.tfmm = P;
+        tp.b = b;
+        tp.inv_b = 1.0f / b;
+        tp.x0 = xmn - 3.0f * b;
+        tp.y0 = ymn - 3.0f * b;
+        tp.nbx = (int)std::ceil((xmx - tp.x0) * tp.inv_b) + 4;
+        tp.nby = (int)std::ceil((ymx - tp.y0) * tp.inv_b) + 4;
+        tp.ok = 1;
+        tcells = (size_t)tp.nbx * tp.nby;
+    }
+    // one device block for everything the field holds: the uploaded star layouts (and the
+    // rectangle's polynomial) first, then the report and the far-field tables
+    size_t off = 0;
+    auto region = [&](size_t bytes) {
+        const size_t o2 = off;
+        off += align256(bytes);
+        return o2;
+    };
+    const size_t o32 = region(sizeof(float4) * n), o64 = region(sizeof(StarD) * n), odp = region(sizeof(float4) * n),
+                 odm = region(sizeof(float2) * n), otf = region(sizeof(float2) * n),
+                 opoly = rect ? region(sizeof(SmoothPoly)) : off;
+    const size_t upload = off;
+    const size_t orep = region(sizeof(DevReport)), ocell = region(sizeof(TCell) * tcells),
+                 onear = region(sizeof(int) * tcells * TFMM_NEAR_MAX), ocoef = region(sizeof(float4) * tcells * TFMM_P);
+    std::vector<unsigned char> host(upload);
+    std::memcpy(host.data() + o32, s32.data(), sizeof(float4) * n);
+    std::memcpy(host.data() + o64, s64.data(), sizeof(StarD) * n);
+    std::memcpy(host.data() + odp, sdp.data(), sizeof(float4) * n);
+    std::memcpy(host.data() + odm, sdm.data(), sizeof(float2) * n);
+    std::memcpy(host.data() + otf, stf.data(), sizeof(float2) * n);
+    if (rect) std::memcpy(host.data() + opoly, &hpoly, sizeof(SmoothPoly));
+
+    cc_field* f = new cc_field();
+    f->opt = o;
+    f->dev.fmm_cell = fmm_cell;
+    f->dev.n = n;
+    f->dev.nr = 2 * n + (rect ? 2 * hpoly.K : 0);
+    f->dev.poly = nullptr;
+    f->dev.poly_K = rect ? hpoly.K : 0;
+    f->dev.kappa_s = kappa_s;
+    f->dev.gamma = gamma;
+    f->dev.unit_mass = unit;
+    f->dev.tfmm.ok = 0;
+    f->solved = false;
+    cudaGetDevice(&f->device);
+    cudaError_t e = cudaMalloc(&f->block, off);
+    e = e ? e : cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming);
+    e = e ? e : cudaEventCreateWithFlags(&f->ready, cudaEventDisableTiming);
+    for (int i = 0; i < 4; i++) e = e ? e : cudaEventCreate(&f->ev[i]);
+    if (e != cudaSuccess) {
+        cc_field_destroy(f);
+        return fail(e == cudaErrorMemoryAllocation ? CC_ENOMEM : CC_ECUDA, "cc_field_create: %s", cudaGetErrorString(e));
+    }
+    char* base = (char*)f->block;
+    f->dev.star32 = (float4*)(base + o32);
+    f->dev.star64 = (StarD*)(base + o64);
+    f->dev.star_dfp = (float4*)(base + odp);
+    f->dev.star_dfm = (float2*)(base + odm);
+    f->dev.star_tf = (float2*)(base + otf);
+    if (rect) f->dev.poly = (const SmoothPoly*)(base + opoly);
+    f->d_rep = (DevReport*)(base + orep);
+    // stream 0: ordered with the caller's later work through the ready event, with no
+    // host wait here
+    e = cudaMemcpyAsync(base, host.data(), upload, cudaMemcpyHostToDevice, 0);
+    e = e ? e : cudaMemsetAsync(f->d_rep, 0, sizeof(DevReport), 0);
+    if (e == cudaSuccess && tp.ok) {
+        f->dev.tcells = (TCell*)(base + ocell);
+        f->dev.tnear = (int*)(base + onear);
+        f->dev.tcoeff = (float4*)(base + ocoef);
+        e = launch_tracer_far_field(f->dev.star32, (int)n, tp, f->dev.tcells, f->dev.tnear, f->dev.tcoeff, 0);
+        f->dev.tfmm = tp;
+    }
+    // (a pageable upload has copied the host buffer by the time cudaMemcpyAsync returns)
+    e = e ? e : cudaEventRecord(f->ready, 0);
+    f->dev.ready = f->ready;
+    if (e != cudaSuccess) {
+        cc_field_destroy(f);
+        return cuda_fail(e, "cc_field_create upload");
     }
     *out = f;
     return CC_OK;
@@ -406,17 +425,10 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
 int cc_field_destroy(cc_field* f) {
     if (!f) return CC_OK;
     if (f->done) cudaEventSynchronize(f->done);
-    cudaFree(f->dev.star32);
-    cudaFree(f->dev.star64);
-    cudaFree(f->dev.star_dfp);
-    cudaFree(f->dev.star_dfm);
-    cudaFree(f->dev.star_tf);
-    cudaFree(f->d_rep);
-    cudaFree(f->dev.tcells);
-    cudaFree(f->dev.tnear);
-    cudaFree(f->dev.tcoeff);
-    cudaFree((void*)f->dev.poly);
+    if (f->ready) cudaEventSynchronize(f->ready);
+    cudaFree(f->block);
     if (f->done) cudaEventDestroy(f->done);
+    if (f->ready) cudaEventDestroy(f->ready);
     for (int i = 0; i < 4; i++)
         if (f->ev[i]) cudaEventDestroy(f->ev[i]);
     delete f;
@@ -455,6 +467,7 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
         return fail(CC_ENOMEM, "cc_critical_curves: workspace has %zu bytes, needs %zu", workspace_bytes, L.total);
     CC_CUDA(cudaSetDevice(f->device), "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
+    CC_CUDA(cudaStreamWaitEvent(st, f->ready, 0), "wait for the field");
     char* ws = (char*)workspace;
     const int64_t nr = f->dev.nr;
     const bool fp64 = f->opt.precision == CC_FP64;
@@ -592,6 +605,7 @@ int cc_map_caustics(cc_field* f, const double* z, int64_t count, double* w_out, 
     if (count == 0) return CC_OK;
     if (!z || !w_out) return fail(CC_EINVAL, "cc_map_caustics: NULL buffer");
     CC_CUDA(cudaSetDevice(f->device), "cudaSetDevice");
+    CC_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, f->ready, 0), "wait for the field");
     CC_CUDA(launch_map_caustics(f->dev, (const double2*)z, count, (double2*)w_out, f->opt.hp_arith == CC_HP_FP64,
                                 (cudaStream_t)stream),
             "map caustics");

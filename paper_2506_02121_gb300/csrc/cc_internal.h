@@ -170,6 +170,7 @@ __device__ __forceinline__ double2 poly_V(const SmoothPoly* P, double zx, double
 
 // Device-side copy of a field's stars in the layouts the kernels read.
 struct FieldDev {
+    cudaEvent_t ready;        // recorded after the field's uploads and tables (stream 0)
     int64_t n;
     int64_t nr;               // roots per row: 2n (disc) or 2n + t - 1 (rectangle)
     const SmoothPoly* poly;   // rectangle polynomial (device), nullptr for the disc
