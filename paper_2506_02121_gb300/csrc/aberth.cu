@@ -1094,28 +1094,39 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
 // next); each of s's columns is matched to its nearest root of s+1's row, and the column
 // permutations are composed so that global column g follows one chain across all rows.
 // ----------------------------------------------------------------------------------
+// Each of seam s's columns k (one thread each) against the first row of sub-range s + 1,
+// read through shared-memory tiles of SM_TILE roots that the whole block shares.  Distances
+// in the tracer's own precision: roots of one row are separated by far more than the
+// tracer's rounding error, so FP32 suffices for the mixed form.
+constexpr int SM_TILE = 1024;
 template <typename C, typename T>
-__device__ __forceinline__ void seam_match_one(const C* zrows, const C* seam, int64_t m, int S, int nr, int s,
-                                               int k, int32_t* match, int32_t* hits, DevReport* rep) {
-    // Distances in the tracer's own precision: roots of one row are separated by far more
-    // than the tracer's rounding error, so FP32 suffices for the mixed form.
+__device__ __forceinline__ void seam_match_block(const C* zrows, const C* seam, int64_t m, int S, int nr, int s,
+                                                 int32_t* match, int32_t* hits, DevReport* rep, C* tile) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = subchain_begin(s + 1, m, S);
-    const C q = seam[(size_t)s * nr + k];
     const C* B = zrows + (size_t)row * nr;
+    const C q = k < nr ? seam[(size_t)s * nr + k] : C{};
     T best = (T)3.0e38, second = (T)3.0e38;
     int bi = 0;
-    for (int j = 0; j < nr; j++) {
-        const C b = B[j];
-        const T dx = b.x - q.x, dy = b.y - q.y;
-        const T d2 = dx * dx + dy * dy;
-        if (d2 < best) {
-            second = best;
-            best = d2;
-            bi = j;
-        } else if (d2 < second) {
-            second = d2;
+    for (int t0 = 0; t0 < nr; t0 += SM_TILE) {
+        const int tn = min(SM_TILE, nr - t0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < tn; j += blockDim.x) tile[j] = B[t0 + j];
+        __syncthreads();
+        for (int j = 0; j < tn; j++) {
+            const C b = tile[j];
+            const T dx = b.x - q.x, dy = b.y - q.y;
+            const T d2 = dx * dx + dy * dy;
+            if (d2 < best) {
+                second = best;
+                best = d2;
+                bi = t0 + j;
+            } else if (d2 < second) {
+                second = d2;
+            }
         }
     }
+    if (k >= nr) return;
     match[(size_t)s * nr + k] = bi;
     atomicAdd(&hits[(size_t)s * nr + bi], 1);
     if (!(best <= (T)1e-4 * second)) atomicAdd(&rep->seam_ambiguous, 1ull);
@@ -1124,44 +1135,46 @@ __device__ __forceinline__ void seam_match_one(const C* zrows, const C* seam, in
 template <typename C, typename T>
 __global__ void seam_match_kernel(const C* zrows, const C* seam, int64_t m, int S, int nr,
                                   int32_t* match, int32_t* hits, DevReport* rep) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nr) return;
-    seam_match_one<C, T>(zrows, seam, m, S, nr, blockIdx.y, k, match, hits, rep);
+    __shared__ C tile[SM_TILE];
+    if ((int)(blockIdx.x * blockDim.x) >= nr) return;  // block-uniform
+    seam_match_block<C, T>(zrows, seam, m, S, nr, blockIdx.y, match, hits, rep, tile);
 }
 
 // Batched: blockIdx.y indexes all seams of all fields.
 __global__ void seam_match_batch_kernel(const TraceTask* tasks, const int2* seams) {
+    __shared__ float2 tile[SM_TILE];
     const int2 fs = seams[blockIdx.y];
     const TraceTask& t = tasks[fs.x];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= t.nr) return;
-    seam_match_one<float2, float>((const float2*)t.zrows, (const float2*)t.seam, t.m, t.S, t.nr, fs.y, k,
-                                  t.match, t.hits, t.rep);
+    if ((int)(blockIdx.x * blockDim.x) >= t.nr) return;  // block-uniform
+    seam_match_block<float2, float>((const float2*)t.zrows, (const float2*)t.seam, t.m, t.S, t.nr, fs.y, t.match,
+                                    t.hits, t.rep, tile);
 }
 
+// Chain permutations: perm_{s+1}[g] = match_s[perm_s[g]], perm_0 = identity.  Each column g
+// is an independent chain through the seams, so one thread carries it in a register.
 __device__ __forceinline__ void compose_perm_body(int S, int nr, const int32_t* match, const int32_t* hits,
-                                                  int32_t* perm, DevReport* rep) {
-    const int tid = threadIdx.x, P = blockDim.x;
-    for (int g = tid; g < nr; g += P) perm[g] = g;
-    for (int s = 0; s + 1 < S; s++) {
-        __syncthreads();
-        int bad = 0;
-        for (int g = tid; g < nr; g += P) {
-            perm[(size_t)(s + 1) * nr + g] = match[(size_t)s * nr + perm[(size_t)s * nr + g]];
+                                                  int32_t* perm, DevReport* rep, int g0, int gstride) {
+    int bad = 0;
+    for (int g = g0; g < nr; g += gstride) {
+        int p = g;
+        perm[g] = g;
+        for (int s = 0; s + 1 < S; s++) {
+            p = match[(size_t)s * nr + p];
+            perm[(size_t)(s + 1) * nr + g] = p;
             bad += hits[(size_t)s * nr + g] != 1;
         }
-        if (bad) atomicAdd(&rep->seam_ambiguous, (unsigned long long)bad);
     }
+    if (bad) atomicAdd(&rep->seam_ambiguous, (unsigned long long)bad);
 }
 
 __global__ void compose_perm_kernel(int S, int nr, const int32_t* match, const int32_t* hits,
                                     int32_t* perm, DevReport* rep) {
-    compose_perm_body(S, nr, match, hits, perm, rep);
+    compose_perm_body(S, nr, match, hits, perm, rep, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 __global__ void compose_perm_batch_kernel(const TraceTask* tasks) {
     const TraceTask& t = tasks[blockIdx.x];
-    compose_perm_body(t.S, t.nr, t.match, t.hits, t.perm, t.rep);
+    compose_perm_body(t.S, t.nr, t.match, t.hits, t.perm, t.rep, threadIdx.x, blockDim.x);
 }
 
 cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int S, int64_t nr,
@@ -1180,7 +1193,7 @@ cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    compose_perm_kernel<<<1, 1024, 0, st>>>(S, (int)nr, match, hits, perm, rep);
+    compose_perm_kernel<<<(unsigned)((nr + 127) / 128), 128, 0, st>>>(S, (int)nr, match, hits, perm, rep);
     return cudaGetLastError();
 }
 

@@ -641,18 +641,31 @@ __global__ void fmm_setup_kernel(const float4* part, int nparts, float b_target,
     P->pool_cap = pool_cap;
 }
 
-__global__ void fmm_occupy_kernel(const float2* z, int64_t npts, FmmParams* P, uint8_t* occ) {
-    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= npts || !P->ok) return;
-    const float2 v = z[p];
-    const int cx = fmm_cell(v.x, P->x0, P->inv_b), cy = fmm_cell(v.y, P->y0, P->inv_b);
-    if (cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby) {
-        // most points fall in cells already marked: test first, so that each cell takes a
-        // handful of stores instead of one per point (a stale 0 only repeats a store)
-        uint8_t* o = occ + (int64_t)cy * P->nbx + cx;
+// Occupied cells.  A warp takes one tracer column over 32 consecutive rows: one chain
+// (within a sub-range), whose points mostly share a cell, so after a warp-level match of the
+// cell indices one lane per distinct cell tests and marks it.
+__global__ void fmm_occupy_kernel(const float2* z, int64_t rows, int64_t nr, FmmParams* P, uint8_t* occ) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t col = w % nr, row = (w / nr) * 32 + lane;
+    if (w >= nr * ((rows + 31) / 32)) return;  // warp-uniform
+    // other warps may clear ok while this one runs: one read per warp keeps the return
+    // warp-uniform (the full-warp match below needs every lane)
+    if (!__shfl_sync(0xffffffffu, P->ok, 0)) return;
+    int64_t cell = -1;
+    if (row < rows) {
+        const float2 v = z[row * nr + col];
+        const int cx = fmm_cell(v.x, P->x0, P->inv_b), cy = fmm_cell(v.y, P->y0, P->inv_b);
+        if (cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby)
+            cell = (int64_t)cy * P->nbx + cx;
+        else
+            P->ok = 0;
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, cell);
+    if (cell >= 0 && lane == __ffs(same) - 1) {
+        // a stale 0 only repeats a store
+        uint8_t* o = occ + cell;
         if (*o == 0) *o = 1;
-    } else {
-        P->ok = 0;
     }
 }
 
@@ -1138,7 +1151,10 @@ cudaError_t launch_polish_fmm(const PolishArgs& a, void* ws, cudaStream_t st) {
     fmm_extent_kernel<<<512, 256, 0, st>>>(a.zrows, points, part);
     fmm_setup_kernel<<<1, 32, 0, st>>>(part, 512, a.f->fmm_cell, cap, pool_cap, P);
     if ((e = cudaMemsetAsync(occ, 0, (size_t)FMM_G * FMM_G, st)) != cudaSuccess) return e;
-    fmm_occupy_kernel<<<(unsigned)((points + 255) / 256), 256, 0, st>>>(a.zrows, points, P, occ);
+    {
+        const int64_t warps = ((a.m + 1 + 31) / 32) * a.nr;
+        fmm_occupy_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(a.zrows, a.m + 1, a.nr, P, occ);
+    }
     fmm_slot_kernel<<<(unsigned)(((int64_t)FMM_G * FMM_G + 255) / 256), 256, 0, st>>>(P, occ, slot, boxlist);
     fmm_coarse_list_kernel<<<(unsigned)((FMM_COARSE_MAX + 255) / 256), 256, 0, st>>>(P, occ, clist);
     const size_t csmem1 = sizeof(float) * 4 * FMM_ACC + sizeof(int) * FMM_CLIST;
