@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--batched-fields", type=int, default=64)
     p.add_argument("--batched-m", type=int, default=1000)
     p.add_argument("--served-requests", type=int, default=48)
+    p.add_argument("--root-refresh", type=int, default=0,
+                   help="FP32 tracer: exact far part of the Aberth root sum every K warm rows (0 = every sweep)")
     return p.parse_args()
 
 
@@ -203,7 +205,9 @@ def run_ours(args):
     roots_per_step = rows * nr
 
     # outputs and scratch, allocated once
-    probe = cc.cc_field_create(xs, ys, ms, f.kappa_s, f.gamma)
+    fopt = cc.cc_options_default()
+    fopt.root_refresh = args.root_refresh
+    probe = cc.cc_field_create(xs, ys, ms, f.kappa_s, f.gamma, fopt)
     ws_cc = cc.workspace(cc.cc_critical_curves_workspace_bytes(probe, m), dev)
     del probe
     z = torch.empty((rows, nr), dtype=torch.complex128, device=dev)
@@ -217,7 +221,7 @@ def run_ours(args):
 
     def step(timers=None):
         nonlocal launches_per_step
-        field = cc.cc_field_create(xs, ys, ms, f.kappa_s, f.gamma)
+        field = cc.cc_field_create(xs, ys, ms, f.kappa_s, f.gamma, fopt)
         cc.cc_critical_curves(field, m, z, w, None, ws_cc, stream)
         ev = None
         if timers is not None:
@@ -282,7 +286,7 @@ def run_ours(args):
     peaks, peak_src = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak_tops = 152 * 128 * sm_max * 1e6 / 1e12  # FP32 lane-ops per second at max clock
-    trace_ops = (rep["star_terms"] * TRACE_OPS_PER_STAR + rep["root_iterations"] * nr * TRACE_OPS_PER_ROOT
+    trace_ops = (rep["star_terms"] * TRACE_OPS_PER_STAR + rep["root_terms"] * TRACE_OPS_PER_ROOT
                  + rep["far_evals"] * TRACE_OPS_PER_FAR_EVAL)
     stage = {"trace_ms": trace_ms, "join_ms": join_ms, "polish_caustic_ms": polish_ms,
              "crossing_ms": cross_ms, "distance_ms": dist_ms}
@@ -293,8 +297,8 @@ def run_ours(args):
                 "peak_source": f"152 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (FP32 pipe ops, FADD/FMUL/FFMA = 1)",
                 "ops_per_unit": {"star_term": TRACE_OPS_PER_STAR, "root_term": TRACE_OPS_PER_ROOT,
                                  "far_eval": TRACE_OPS_PER_FAR_EVAL},
-                "units": f"{rep['star_terms']} star terms, {rep['root_iterations']} root-iterations x {nr} root "
-                         f"terms, {rep['far_evals']} expansion evaluations"}
+                "units": f"{rep['star_terms']} star terms, {rep['root_terms']} root terms "
+                         f"({rep['root_iterations']} root-iterations), {rep['far_evals']} expansion evaluations"}
     # crossing map: algorithmic bytes = vertex reads + one int32 read+write per pixel for
     # the scan + the clearing store
     cross_bytes = rows * nr * 16 + 3 * px * px * 4
@@ -314,7 +318,8 @@ def run_ours(args):
         "config": {"workload": wl.name, "n_stars": f.n, "n_roots": nr, "phi_steps": m,
                    "root_points_per_step": roots_per_step, "map": f"{px}x{px} over +-{ext}",
                    "kappa_star": f.kappa_star, "kappa_s": f.kappa_s, "gamma": f.gamma,
-                   "subchains": rep["subchains"], "l2": "flushed (256 MiB write) between timed steps",
+                   "subchains": rep["subchains"], "root_refresh": args.root_refresh,
+                   "l2": "flushed (256 MiB write) between timed steps",
                    "precision": "FP32 Aberth tracer + double-float certified polish/caustics; FP64 segment tests"},
         "roofline": roofline,
         "stages_ms": {k: round(v, 3) for k, v in stage.items()},
@@ -322,7 +327,8 @@ def run_ours(args):
         "accuracy": {"max_err_est": rep["max_err_est"], "uncertified": rep["uncertified"],
                      "unconverged": rep["unconverged"], "status_ok": status_ok,
                      "polish_passes_per_point": round(rep["polish_passes"] / roots_per_step, 4),
-                     "tracer_iterations_per_point": round(rep["root_iterations"] / roots_per_step, 4)},
+                     "tracer_iterations_per_point": round(rep["root_iterations"] / roots_per_step, 4),
+                     "jumped": rep["jumped"], "rescued": rep["rescued_points"]},
         "clocks": clocks,
         "gpu_launches": launches_per_step * args.steps,
         "wall_s": round(wall, 3),
@@ -420,7 +426,9 @@ def batched(args, dev):
     import torch
     from paper_2506_02121_gb300 import autotune, cc, synth
     wl = synth.workload_batched(args.batched_fields, args.batched_m)
-    fields = [cc.cc_field_create(f.x, f.y, f.m, f.kappa_s, f.gamma) for f in wl.fields]
+    fopt = cc.cc_options_default()
+    fopt.root_refresh = args.root_refresh
+    fields = [cc.cc_field_create(f.x, f.y, f.m, f.kappa_s, f.gamma, fopt) for f in wl.fields]
     ms = [wl.msteps] * len(fields)
     t, items, info = autotune.tune(fields, ms, probe_steps=32, repeats=1)
     b = cc.cc_batch_create(fields, ms, t, items)

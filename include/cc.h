@@ -105,6 +105,12 @@ typedef struct cc_options {
     int32_t row_ctas;      /* CTAs (one thread-block cluster) that share each phi sub-range of the FP32
                               tracer, each updating a slice of the roots: 0 = automatic (8 when
                               n_r >= 4096, else 1), 1 = one CTA per sub-range, 2..16 = that many */
+    int32_t root_refresh;  /* Aberth root sum of the FP32 tracer's warm rows (one CTA per sub-range):
+                              0 or 1 = exact in every sweep (Sec. 3.2); K >= 2 = exact every K-th row
+                              of a chain, where each root's sum is split into the roots of the 3 x 3
+                              cells around it (summed exactly in every sweep) and the rest (kept
+                              from the refresh row).  The roots found are the same zeros of F; only
+                              the Aberth iteration path changes.  At most 4096. */
 } cc_options;
 
 /* Solve statistics of the last cc_critical_curves on a field (host copy). */
@@ -131,6 +137,9 @@ typedef struct cc_report {
                                   root (a sign of a root swap; diagnostic) */
     int64_t star_terms;        /* tracer: star terms summed directly (all roots, iterations) */
     int64_t far_evals;         /* tracer: root updates that used a cell's local expansions */
+    int64_t root_terms;        /* tracer: root-root terms summed (all roots, iterations) */
+    int64_t split_redone_rows; /* root_refresh >= 2: rows solved again with the exact root sum
+                                  because an iterate moved beyond its displacement limit */
 } cc_report;
 
 /* Fill *opt with the defaults listed above. */

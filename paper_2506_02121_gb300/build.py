@@ -20,6 +20,12 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 SOURCES = ["cc_api.cu", "aberth.cu", "polish.cu", "raster.cu", "static_scratch.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# The tracer inlines its per-root code once per thread slot, and the slot a root takes in a
+# sweep follows the order of shared-memory atomics; with contraction of a*b + c into FMA left
+# to the compiler, the copies could round differently and a root's result would depend on
+# its slot.  Its fused operations are all written out (fmaf, packed fma), so contraction is
+# off there and every copy computes the same value.
+EXTRA = {"aberth.cu": ["-fmad=false"]}
 
 
 def nvcc() -> str:
@@ -30,7 +36,8 @@ def nvcc() -> str:
 
 
 def _deps_mtime() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "cc.h")]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "cc.h"),
+                                                                 os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files if os.path.isfile(f))
 
 
@@ -42,7 +49,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src: str) -> str:
         obj = os.path.join(BUILD_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *EXTRA.get(src, []), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

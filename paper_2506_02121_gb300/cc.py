@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
                 ("subchains", ctypes.c_int32), ("predictor", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("far_field", ctypes.c_int32), ("field_shape", ctypes.c_int32), ("rect_t", ctypes.c_int32),
                 ("kappa_star", ctypes.c_double), ("rect_c1", ctypes.c_double), ("rect_c2", ctypes.c_double),
-                ("rect_eps", ctypes.c_double), ("rect_s", ctypes.c_double), ("row_ctas", ctypes.c_int32)]
+                ("rect_eps", ctypes.c_double), ("rect_s", ctypes.c_double), ("row_ctas", ctypes.c_int32),
+                ("root_refresh", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -52,7 +53,8 @@ class Report(ctypes.Structure):
                 ("max_iter_row", ctypes.c_int32), ("timeout", ctypes.c_int32), ("max_err_est", ctypes.c_double),
                 ("trace_ms", ctypes.c_float), ("join_ms", ctypes.c_float), ("polish_ms", ctypes.c_float),
                 ("rescued_points", ctypes.c_int64), ("jumped", ctypes.c_int64),
-                ("star_terms", ctypes.c_int64), ("far_evals", ctypes.c_int64)]
+                ("star_terms", ctypes.c_int64), ("far_evals", ctypes.c_int64),
+                ("root_terms", ctypes.c_int64), ("split_redone_rows", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -109,6 +109,7 @@ struct TK {
     DevReport* rep;
     double tol_abs, mu_max;
     int max_iter_cold, max_iter_warm, predictor;
+    int root_refresh;  // FP32 warm rows: exact far part of the root sum every root_refresh rows (< 2: every sweep)
     // FP32 far-field tables (tfmm.ok == 0: every star summed directly)
     TfmmParams tfmm;
     const TCell* tcells;
@@ -134,6 +135,20 @@ struct Ctx {
     int* red_parity;
     unsigned long long* n_terms;  // this thread's work counters (registers of the caller)
     unsigned long long* n_far;
+    unsigned long long* n_root;
+    // near/far split of the root sum (per direction d: [d nr, d nr + nr) of each array)
+    float2* nfar;   // far part of root k's sum, captured at the last refresh row
+    float2* npos;   // current positions in cell order
+    int* nkey;      // refresh cell of root k
+    int* nord;      // roots in cell order (row-major cells, index order within a cell)
+    int* ncst;      // [d (ncm + 1) + c]: first entry of cell c in nord
+    int* nfill;     // [d ncm + c]: scatter counters
+    float2* nref;   // positions at the last refresh
+    float2* npred;  // this row's predicted positions
+    int ncm;        // cells available per direction
+    int* s_ngrid;   // shared: nbx, nby of direction d at [2 d], [2 d + 1]
+    float* s_nlim2; // shared: squared displacement limit (h / 4)^2 of direction d
+    int* s_nesc;    // shared: an iterate left its limit during this row
 };
 
 // One other root in FP32, without a branch: D += 1/(z_k - z_r).  The tiny constant added
@@ -327,10 +342,170 @@ __device__ __forceinline__ void finish_root(const Ctx<T>& x, int key, typename C
     x.nxt[key] = zn;
 }
 
+// ----------------------------------------------------------------------------------
+// Near/far split of the Aberth root sum on warm rows (FP32 tracer).  The Aberth correction
+// sum_{r != k} 1/(z_k - z_r) only shapes the iteration, not its fixed points (F(z_k) = 0 is
+// decided by F alone, and every point is then polished by Newton on F and certified), and
+// on a warm row the predictor already puts each root within a small fraction of the root
+// spacing of its zero.  So at a refresh row the exact sum is split into the roots of the
+// 3 x 3 cells around root k (its near set) and the rest (its far part, stored); on the
+// following rows the near set is summed exactly at the current positions and the stored far
+// part is reused.  A perturbation e of the sum moves an Aberth step delta by about
+// e delta^2, far below the FP32 stop threshold once delta is small; the near roots, whose
+// repulsion keeps two iterates from settling on one zero, are always exact.  Every position
+// used is kept within h/4 of its refresh position (h the cell side): a root and any root
+// outside its near set, at least h apart at the refresh, then stay h/2 apart, so an iterate
+// can neither settle on a far root's zero nor make the stored part stale by more than that
+// motion allows.  A prediction beyond the limit makes its row a refresh row; an iterate
+// beyond it has its row solved again with the exact sum in every sweep.
+// ----------------------------------------------------------------------------------
+constexpr int NEAR_PER_CELL = 4;  // roots per cell on average over the bounding box
+
+// sum over the near set of root key (direction key >= nr) at the positions in npos; returns
+// the number of terms.  Its own entry contributes 0 (see acc_root_f).
+__device__ __forceinline__ int near_sum(const Ctx<float>& x, int key, float zx, float zy, float& Dx, float& Dy) {
+    const int nr = x.k->nr;
+    const int d = key >= nr ? 1 : 0;
+    const int nbx = x.s_ngrid[2 * d], nby = x.s_ngrid[2 * d + 1];
+    const int c = x.nkey[key];
+    const int cx = c % nbx, cy = c / nbx;
+    const int* cst = x.ncst + (size_t)d * (x.ncm + 1);
+    const float2* p = x.npos + (size_t)d * nr;
+    const int xa = max(cx - 1, 0), xb = min(cx + 1, nbx - 1);
+    int cnt = 0;
+    for (int yy = max(cy - 1, 0); yy <= min(cy + 1, nby - 1); yy++) {
+        const int i0 = cst[yy * nbx + xa], i1 = cst[yy * nbx + xb + 1];
+        cnt += i1 - i0;
+        for (int i = i0; i < i1; i++) {
+            const float2 r = p[i];
+            acc_root_f(zx, zy, r.x, r.y, Dx, Dy);
+        }
+    }
+    return cnt;
+}
+
+// In-place inclusive prefix sum of a[0, n) by the whole block (blockDim a multiple of 32).
+__device__ void block_scan_inclusive(int* a, int n, int* s_scan) {
+    const int tid = threadIdx.x, P = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = P >> 5;
+    const int ch = (n + P - 1) / P;
+    const int i0 = min(n, tid * ch), i1 = min(n, i0 + ch);
+    int s = 0;
+    for (int i = i0; i < i1; i++) s += a[i];
+    int v = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) s_scan[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int u = lane < nw ? s_scan[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, u, o);
+            if (lane >= o) u += t;
+        }
+        if (lane < nw) s_scan[lane] = u;
+    }
+    __syncthreads();
+    int off = v - s + (wid > 0 ? s_scan[wid - 1] : 0);
+    for (int i = i0; i < i1; i++) {
+        off += a[i];
+        a[i] = off;
+    }
+    __syncthreads();
+}
+
+// Refresh row, direction d (whole block): cells of side h over the bounding box of the
+// current roots with about NEAR_PER_CELL roots per cell (at most ncm cells), every root's
+// cell, and the roots listed cell by cell (row-major), each cell in root-index order so that
+// the near sums add their terms in a fixed order.
+__device__ void near_build(const Ctx<float>& x, int d) {
+    __shared__ float s_box[4][32];
+    __shared__ float s_g[3];
+    __shared__ int s_scan[32];
+    const int nr = x.k->nr, tid = threadIdx.x, P = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = P >> 5;
+    const float2* z = x.cur + (size_t)d * nr;
+    float b[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};  // min x, min y, -max x, -max y
+    for (int k = tid; k < nr; k += P) {
+        const float2 v = z[k];
+        b[0] = fminf(b[0], v.x);
+        b[1] = fminf(b[1], v.y);
+        b[2] = fminf(b[2], -v.x);
+        b[3] = fminf(b[3], -v.y);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        for (int o = 16; o > 0; o >>= 1) b[q] = fminf(b[q], __shfl_xor_sync(0xffffffffu, b[q], o));
+        if (lane == 0) s_box[q][wid] = b[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < nw; w++)
+            for (int q = 0; q < 4; q++) b[q] = fminf(b[q], s_box[q][w]);
+        const float x0 = b[0], y0 = b[1];
+        const float wd = fmaxf(-b[2] - x0, 1e-3f), ht = fmaxf(-b[3] - y0, 1e-3f);
+        float h = sqrtf(wd * ht * (float)NEAR_PER_CELL / (float)nr);
+        h = fmaxf(h, fmaxf(wd, ht) * (1.f / 1024.f));
+        int nbx, nby;
+        for (;;) {
+            nbx = (int)(wd / h) + 1;
+            nby = (int)(ht / h) + 1;
+            if (nbx * nby <= x.ncm) break;
+            h *= 1.25f;
+        }
+        x.s_ngrid[2 * d] = nbx;
+        x.s_ngrid[2 * d + 1] = nby;
+        x.s_nlim2[d] = 0.0625f * h * h;
+        s_g[0] = x0;
+        s_g[1] = y0;
+        s_g[2] = 1.f / h;
+    }
+    __syncthreads();
+    const int nbx = x.s_ngrid[2 * d], nby = x.s_ngrid[2 * d + 1], nc = nbx * nby;
+    const float x0 = s_g[0], y0 = s_g[1], ih = s_g[2];
+    int* key = x.nkey + (size_t)d * nr;
+    int* ord = x.nord + (size_t)d * nr;
+    int* cst = x.ncst + (size_t)d * (x.ncm + 1);
+    int* fill = x.nfill + (size_t)d * x.ncm;
+    for (int c = tid; c <= nc; c += P) cst[c] = 0;
+    for (int c = tid; c < nc; c += P) fill[c] = 0;
+    __syncthreads();
+    for (int k = tid; k < nr; k += P) {
+        const float2 v = z[k];
+        x.nref[(size_t)d * nr + k] = v;
+        // clamped in floating point first (a NaN position lands in cell 0)
+        const float fx = fminf(fmaxf((v.x - x0) * ih, 0.f), (float)(nbx - 1));
+        const float fy = fminf(fmaxf((v.y - y0) * ih, 0.f), (float)(nby - 1));
+        const int c = (int)fy * nbx + (int)fx;
+        key[k] = c;
+        atomicAdd(&cst[c + 1], 1);
+    }
+    __syncthreads();
+    block_scan_inclusive(cst + 1, nc, s_scan);
+    for (int k = tid; k < nr; k += P) {
+        const int c = key[k];
+        ord[cst[c] + atomicAdd(&fill[c], 1)] = k;
+    }
+    __syncthreads();
+    for (int c = tid; c < nc; c += P) {
+        const int a = cst[c], e = cst[c + 1];
+        for (int i = a + 1; i < e; i++) {
+            const int v = ord[i];
+            int j = i - 1;
+            while (j >= a && ord[j] > v) {
+                ord[j + 1] = ord[j];
+                j--;
+            }
+            ord[j + 1] = v;
+        }
+    }
+    __syncthreads();
+}
+
 // One sweep over the active FP32 roots with R roots per thread.  Slots [0, A0) hold the
 // direction-0 roots, [A0p, A0p + A1) the direction-1 roots, A0p = A0 rounded up to 32 R so
 // that a warp never mixes the directions and every root-tile load is a broadcast.
-template <int R>
+template <int R, bool CAPTURE>
 __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool a1, int A0, int A1, float cph0,
                                               float sph0, float cph1, float sph1, int* s_maxit) {
     using C = float2;
@@ -436,9 +611,55 @@ __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool
             acc[r].Dx += a + b;
             acc[r].Dy -= c2 + d2;
         }
+        if constexpr (CAPTURE) {
+#pragma unroll
+            for (int r = 0; r < R; r++)
+                if (valid[r]) {
+                    float nx = 0.f, ny = 0.f;
+                    *x.n_root += (unsigned long long)near_sum(x, key[r], z[r].x, z[r].y, nx, ny);
+                    x.nfar[key[r]] = make_float2(acc[r].Dx - nx, acc[r].Dy - ny);
+                }
+        }
 #pragma unroll
         for (int r = 0; r < R; r++)
             if (valid[r]) finish_root<float>(x, key[r], z[r], acc[r], d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
+    }
+}
+
+// One sweep of a row between refreshes: each active root (one per thread) sums its stars as
+// in the full sweep, its near roots exactly at their current positions, and adds its stored
+// far part.
+__device__ void sweep_light(const Ctx<float>& x, int A0, int A1, float cph0, float sph0, float cph1, float sph1,
+                            int* s_maxit) {
+    const TK& K = *x.k;
+    const int nr = K.nr, n = K.n;
+    const float4* gs = (const float4*)K.stars;
+    for (int slot = threadIdx.x; slot < A0 + A1; slot += blockDim.x) {
+        const int key = slot < A0 ? x.act[slot] : x.act[nr + slot - A0];
+        const int d = key >= nr ? 1 : 0;
+        const float2 z = x.cur[key];
+        Acc<float> acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        const int cell = far_cell<float>(K, z.x, z.y);
+        *x.n_terms += (unsigned long long)(cell >= 0 ? K.tcells[cell].near_cnt : n);
+        *x.n_far += cell >= 0 ? 1ull : 0ull;
+        if (cell >= 0) {
+            cell_part<float>(x, cell, z.x, z.y, 0, 1, acc);
+        } else if (x.resident) {
+#pragma unroll 4
+            for (int j = 0; j < n; j++) acc_star(z.x, z.y, x.s_star[j], acc);
+        } else {
+#pragma unroll 4
+            for (int j = 0; j < n; j++) acc_star(z.x, z.y, gs[j], acc);
+        }
+        float Dx = 0.f, Dy = 0.f;
+        *x.n_root += (unsigned long long)near_sum(x, key, z.x, z.y, Dx, Dy);
+        const float2 f = x.nfar[key];
+        acc.Dx = Dx + f.x;
+        acc.Dy = Dy + f.y;
+        finish_root<float>(x, key, z, acc, d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
+        const float2 zn = x.nxt[key], zr = x.nref[key];
+        const float ex = zn.x - zr.x, ey = zn.y - zr.y;
+        if (!(ex * ex + ey * ey <= x.s_nlim2[d])) *x.s_nesc = 1;
     }
 }
 
@@ -509,9 +730,14 @@ __device__ __forceinline__ void cluster_sum3(const Ctx<T>& x, int& a, int& b, in
 // roots of direction d are listed in act[d nr, d nr + A_d).  With many of them the FP32
 // tracer gives each thread several roots of one direction (sweep_blocked); otherwise g
 // lanes share a root and reduce their partial sums with shuffles.
+// Root-sum modes of a row's sweeps: every sweep exact; or the first sweep exact with the far
+// parts captured and the rest near + far; or every sweep near + far (FP32, one CTA per row).
+enum SumMode { SUM_FULL = 0, SUM_CAPTURE = 1, SUM_LIGHT = 2 };
+
 template <typename T, bool WIDE>
 __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int64_t row0, int64_t row1,
-                                          int max_iter, bool cold, bool report, int* s_count, int* s_maxit) {
+                                          int max_iter, bool cold, bool report, int* s_count, int* s_maxit,
+                                          int mode = SUM_FULL) {
     using C = typename CT<T>::C;
     constexpr int TS = CT<T>::TS;
     const TK& K = *x.k;
@@ -531,6 +757,19 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
     const int lo = x.lo, W = x.hi - x.lo;
     Ctx<T> xs = x;
     xs.act = x.act + lo;  // this CTA's lists: [lo, lo + A0) and [nr + lo, nr + lo + A1)
+    if constexpr (sizeof(T) != 4 || WIDE) mode = SUM_FULL;
+    const bool split = mode != SUM_FULL;
+    if constexpr (sizeof(T) == 4 && !WIDE) {
+        if (split) {
+            __syncthreads();
+            if (tid == 0) *x.s_nesc = 0;
+        }
+        if (mode == SUM_CAPTURE) {
+            __syncthreads();
+            if (a0) near_build(x, 0);
+            if (a1) near_build(x, 1);
+        }
+    }
     for (int iter = 0;; iter++) {
         __syncthreads();
         if (tid < 2) s_count[tid] = 0;
@@ -564,12 +803,31 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             continue;
         }
         bool blocked = false;
-        if constexpr (sizeof(T) == 4) {
-            if (A >= 2 * P) {
-                sweep_blocked<4>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+        if constexpr (sizeof(T) == 4 && !WIDE) {
+            if (mode != SUM_FULL) {
+                // the active directions' current positions in cell order
+                for (int i = tid; i < nr; i += P) {
+                    if (a0) x.npos[i] = x.cur[x.nord[i]];
+                    if (a1) x.npos[nr + i] = x.cur[nr + x.nord[nr + i]];
+                }
+                __syncthreads();
+            }
+            if (mode == SUM_LIGHT) {
+                sweep_light(xs, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
                 blocked = true;
-            } else if (A >= P) {
-                sweep_blocked<2>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+            }
+        }
+        if (mode != SUM_LIGHT && tid == 0) *x.n_root += (unsigned long long)A * nr;
+        if constexpr (sizeof(T) == 4) {
+            if (!blocked && A >= P) {
+                const bool cap = !WIDE && mode == SUM_CAPTURE;
+                if (A >= 2 * P) {
+                    if (cap) sweep_blocked<4, !WIDE>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                    else sweep_blocked<4, false>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                } else {
+                    if (cap) sweep_blocked<2, !WIDE>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                    else sweep_blocked<2, false>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                }
                 blocked = true;
             }
         }
@@ -636,9 +894,17 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                     acc.Dy += shfl_x(acc.Dy, off);
                     acc.Am += shfl_x(acc.Am, off);
                 }
+                if constexpr (sizeof(T) == 4 && !WIDE) {
+                    if (mode == SUM_CAPTURE && valid && lane == 0) {
+                        float nx = 0.f, ny = 0.f;
+                        *x.n_root += (unsigned long long)near_sum(x, key, z.x, z.y, nx, ny);
+                        x.nfar[key] = make_float2(acc.Dx - nx, acc.Dy - ny);
+                    }
+                }
                 if (valid && lane == 0) finish_root<T>(x, key, z, acc, d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
             }
         }
+        if (mode == SUM_CAPTURE) mode = SUM_LIGHT;
         // every CTA of a cluster has finished reading the positions before any is updated
         if constexpr (WIDE) cluster_sync();
         else __syncthreads();
@@ -661,7 +927,9 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         int u2 = 0;
         cluster_sum3(x, m0, m1, u2);
     }
-    return (m0 ? 1 : 0) | (m1 ? 2 : 0);
+    int esc = 0;
+    if constexpr (sizeof(T) == 4 && !WIDE) esc = split && *x.s_nesc;
+    return (m0 ? 1 : 0) | (m1 ? 2 : 0) | (esc ? 4 : 0);
 }
 
 // Star guesses z_i +- 1 (Sec. 3.2) into direction d, tilted to z_i +- (1 + i/64):
@@ -719,7 +987,8 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
 template <typename T, bool WIDE>
 __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, unsigned char* smem,
                                              int* s_count_p, int* s_maxit_p, unsigned long long* n_terms_p,
-                                             unsigned long long* n_far_p, int* s_red = nullptr,
+                                             unsigned long long* n_far_p, unsigned long long* n_root_p,
+                                             int* s_red = nullptr,
                                              int* s_tot = nullptr, int* red_parity = nullptr, int rank = 0,
                                              int G = 1) {
     using C = typename CT<T>::C;
@@ -744,6 +1013,31 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     x.conv = (int*)(x.dprev + 2 * nr);
     x.it = x.conv + 2 * nr;
     x.act = x.it + 2 * nr;
+    {
+        char* nb = (char*)(x.act + 2 * nr);
+        x.ncm = near_cells_max(nr);
+        x.nfar = (float2*)nb;
+        nb += sizeof(float2) * 2 * (size_t)nr;
+        x.npos = (float2*)nb;
+        nb += sizeof(float2) * 2 * (size_t)nr;
+        x.nkey = (int*)nb;
+        nb += sizeof(int) * 2 * (size_t)nr;
+        x.nord = (int*)nb;
+        nb += sizeof(int) * 2 * (size_t)nr;
+        x.ncst = (int*)nb;
+        nb += sizeof(int) * 2 * (size_t)(x.ncm + 1);
+        x.nfill = (int*)nb;
+        nb += sizeof(int) * 2 * (size_t)x.ncm;
+        nb = (char*)(((uintptr_t)nb + 15) & ~(uintptr_t)15);
+        x.nref = (float2*)nb;
+        nb += sizeof(float2) * 2 * (size_t)nr;
+        x.npred = (float2*)nb;
+    }
+    __shared__ int s_ngrid[4], s_nesc;
+    __shared__ float s_nlim2[2];
+    x.s_ngrid = s_ngrid;
+    x.s_nlim2 = s_nlim2;
+    x.s_nesc = &s_nesc;
     x.resident = n <= TS;
     {
         const int Wd = (nr + G - 1) / G;
@@ -755,6 +1049,7 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     x.red_parity = red_parity;
     x.n_terms = n_terms_p;
     x.n_far = n_far_p;
+    x.n_root = n_root_p;
     const int lo = x.lo, hi = x.hi;
     const Star* gs = (const Star*)K.stars;
     if (x.resident)
@@ -780,7 +1075,11 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     // s_hist[d]: rows of direction d already behind the current one that belong to the same
     // chains (a row re-solved from the star guesses has new column labels: history restarts)
     __shared__ int s_hist[2];
+    // s_refresh: the near/far split needs new cells (first warm row, or a row after a restart)
+    __shared__ int s_refresh;
     if (tid == 0) s_hist[0] = s_hist[1] = 0;
+    if (tid == 0) s_refresh = 1;
+    const int KR = (sizeof(T) == 4 && !WIDE) ? K.root_refresh : 0;
     for (int64_t t = 1;; t++) {
         const bool a0 = c - t >= b0, a1 = c + t <= b1;
         if (!a0 && !a1) break;
@@ -810,17 +1109,56 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             if (h >= 1) x.prev2[k] = x.prev[k];
             x.prev[k] = zc;
             x.cur[k] = g;
+            if constexpr (sizeof(T) == 4)
+                if (KR >= 2) x.npred[k] = g;
             x.conv[k] = 0;
             x.it[k] = 0;
             x.dprev[k] = FLT_MAX;
         }
-        const int bad = solve_rows<T, WIDE>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit);
+        int mode = SUM_FULL;
+        if (KR >= 2) {
+            mode = (s_refresh || (t - 1) % KR == 0) ? SUM_CAPTURE : SUM_LIGHT;
+            if (mode == SUM_LIGHT) {
+                // a prediction beyond its displacement limit: refresh at this row
+                bool out = false;
+                if constexpr (sizeof(T) == 4) {
+                    for (int i = tid; i < 2 * (hi - lo); i += P) {
+                        const int dd = i >= hi - lo;
+                        if (!(dd ? a1 : a0)) continue;
+                        const int k = dd * nr + lo + (i - dd * (hi - lo));
+                        const float2 g = x.npred[k], r = x.nref[k];
+                        const float ex = g.x - r.x, ey = g.y - r.y;
+                        out |= !(ex * ex + ey * ey <= s_nlim2[dd]);
+                    }
+                }
+                if (__syncthreads_or(out)) mode = SUM_CAPTURE;
+            }
+        }
+        int bad = solve_rows<T, WIDE>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit, mode);
+        if (bad & 4) {
+            // an iterate went beyond its limit: this row again from its predictions, with the
+            // exact root sum in every sweep
+            __syncthreads();
+            for (int i = tid; i < 2 * (hi - lo); i += P) {
+                const int dd = i >= hi - lo;
+                if (!(dd ? a1 : a0)) continue;
+                const int k = dd * nr + lo + (i - dd * (hi - lo));
+                if constexpr (sizeof(T) == 4) x.cur[k] = x.npred[k];
+                x.conv[k] = 0;
+                x.it[k] = 0;
+                x.dprev[k] = FLT_MAX;
+            }
+            bad = solve_rows<T, WIDE>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit);
+            if (tid == 0) atomicAdd(&K.rep->split_redone_rows, 1ull);
+        }
         if (tid == 0) {  // read again only after the next row's opening barrier
             if (a0) s_hist[0] = min(s_hist[0] + 1, 2);
             if (a1) s_hist[1] = min(s_hist[1] + 1, 2);
             if (bad & 1) s_hist[0] = 0;
             if (bad & 2) s_hist[1] = 0;
+            s_refresh = (bad & 3) ? 1 : 0;
         }
+        bad &= 3;
         if (bad) {
             // A warm start that does not settle (e.g. a phase step so large that the previous
             // row sits on a symmetric, non-converging configuration) restarts that row from
@@ -848,22 +1186,30 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     __syncthreads();
 }
 
+// Per-thread work counters summed over the warp, one atomic per warp.
+__device__ __forceinline__ void add_work_counters(DevReport* rep, unsigned long long n_terms,
+                                                  unsigned long long n_far, unsigned long long n_root) {
+    for (int off = 16; off > 0; off >>= 1) {
+        n_terms += __shfl_xor_sync(0xffffffffu, n_terms, off);
+        n_far += __shfl_xor_sync(0xffffffffu, n_far, off);
+        n_root += __shfl_xor_sync(0xffffffffu, n_root, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (n_terms) atomicAdd(&rep->star_terms, n_terms);
+        if (n_far) atomicAdd(&rep->far_evals, n_far);
+        if (n_root) atomicAdd(&rep->root_terms, n_root);
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_count[2], s_maxit;
     if (threadIdx.x == 0) s_maxit = 0;
-    unsigned long long n_terms = 0, n_far = 0;
+    unsigned long long n_terms = 0, n_far = 0, n_root = 0;
     run_subchain<T, false>(K, blockIdx.x, K.work + (size_t)blockIdx.x * K.work_stride, smem, s_count, &s_maxit,
-                           &n_terms, &n_far);
-    for (int off = 16; off > 0; off >>= 1) {
-        n_terms += __shfl_xor_sync(0xffffffffu, n_terms, off);
-        n_far += __shfl_xor_sync(0xffffffffu, n_far, off);
-    }
-    if ((threadIdx.x & 31) == 0 && (n_terms || n_far)) {
-        atomicAdd(&K.rep->star_terms, n_terms);
-        atomicAdd(&K.rep->far_evals, n_far);
-    }
+                           &n_terms, &n_far, &n_root);
+    add_work_counters(K.rep, n_terms, n_far, n_root);
     if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
 }
 
@@ -878,18 +1224,11 @@ __global__ void __launch_bounds__(512, 1) trace_wide_kernel(TK K) {
     }
     const int G = (int)cluster_size(), rank = (int)cluster_rank();
     const int s = (int)blockIdx.x / G;
-    unsigned long long n_terms = 0, n_far = 0;
+    unsigned long long n_terms = 0, n_far = 0, n_root = 0;
     __syncthreads();
     run_subchain<float, true>(K, s, K.work + (size_t)s * K.work_stride, smem, s_count, &s_maxit, &n_terms, &n_far,
-                              s_red, s_tot, &s_parity, rank, G);
-    for (int off = 16; off > 0; off >>= 1) {
-        n_terms += __shfl_xor_sync(0xffffffffu, n_terms, off);
-        n_far += __shfl_xor_sync(0xffffffffu, n_far, off);
-    }
-    if ((threadIdx.x & 31) == 0 && (n_terms || n_far)) {
-        atomicAdd(&K.rep->star_terms, n_terms);
-        atomicAdd(&K.rep->far_evals, n_far);
-    }
+                              &n_root, s_red, s_tot, &s_parity, rank, G);
+    add_work_counters(K.rep, n_terms, n_far, n_root);
     if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
     cluster_sync();  // no CTA leaves while another may still read its shared memory
 }
@@ -900,7 +1239,7 @@ template <typename T>
 __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_count[2], s_maxit, s_item;
-    unsigned long long n_terms = 0, n_far = 0;
+    unsigned long long n_terms = 0, n_far = 0, n_root = 0;
     char* w = (char*)B.work + (size_t)blockIdx.x * B.work_stride;
     for (;;) {
         __syncthreads();
@@ -935,18 +1274,13 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
         K.tcells = t.tcells;
         K.tnear = t.tnear;
         K.tcoeff = t.tcoeff;
+        K.root_refresh = B.root_refresh;
         if (threadIdx.x == 0) s_maxit = 0;
         n_terms = 0;
         n_far = 0;
-        run_subchain<T, false>(K, fs.y, w, smem, s_count, &s_maxit, &n_terms, &n_far);
-        for (int off = 16; off > 0; off >>= 1) {
-            n_terms += __shfl_xor_sync(0xffffffffu, n_terms, off);
-            n_far += __shfl_xor_sync(0xffffffffu, n_far, off);
-        }
-        if ((threadIdx.x & 31) == 0 && (n_terms || n_far)) {
-            atomicAdd(&K.rep->star_terms, n_terms);
-            atomicAdd(&K.rep->far_evals, n_far);
-        }
+        n_root = 0;
+        run_subchain<T, false>(K, fs.y, w, smem, s_count, &s_maxit, &n_terms, &n_far, &n_root);
+        add_work_counters(K.rep, n_terms, n_far, n_root);
         if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
     }
 }
@@ -959,6 +1293,11 @@ size_t tracer_smem_bytes(bool fp64, int64_t n) {
 
 size_t tracer_work_stride(int64_t nr, size_t elem) {
     size_t b = (size_t)(2 * nr) * (4 * elem + 4 * 4);
+    // near/far split of the root sum: far part, ordered, refresh and predicted positions
+    // (float2), cell and ordered index (int) per root; cell starts and scatter counters per
+    // direction
+    b += (size_t)(2 * nr) * (4 * sizeof(float2) + 2 * sizeof(int)) +
+         (size_t)2 * (2 * (size_t)near_cells_max((int)nr) + 1) * sizeof(int) + 16;
     return (b + 255) / 256 * 256;
 }
 
@@ -1048,6 +1387,7 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
     K.max_iter_cold = a.max_iter_cold;
     K.max_iter_warm = a.max_iter_warm;
     K.predictor = a.predictor;
+    K.root_refresh = a.root_refresh;
     K.tfmm = a.f->tfmm;
     if (fp64) K.tfmm.ok = 0;
     K.tcells = a.f->tcells;

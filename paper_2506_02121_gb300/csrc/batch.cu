@@ -95,6 +95,7 @@ cudaError_t enqueue(cc_batch* b, cudaStream_t st, bool capturing) {
     a.max_iter_cold = b->opt.max_iter_cold;
     a.max_iter_warm = b->opt.max_iter_warm;
     a.predictor = b->opt.predictor;
+    a.root_refresh = b->opt.root_refresh;
     if ((e = launch_trace_batch(a, b->grid, b->threads, st)) != cudaSuccess) return e;
     if ((e = rec(b->ev[1], st, capturing)) != cudaSuccess) return e;
     if ((e = launch_seam_join_batch(tasks, b->count, (const int2*)(ws + b->off_seams), b->nseams, b->max_nr, st)) !=
@@ -450,6 +451,8 @@ int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
         q.jumped = (int64_t)r[f].jumped;
         q.star_terms = (int64_t)r[f].star_terms;
         q.far_evals = (int64_t)r[f].far_evals;
+        q.root_terms = (int64_t)r[f].root_terms;
+        q.split_redone_rows = (int64_t)r[f].split_redone_rows;
         if (per_field) per_field[f] = q;
         tot.rows += q.rows;
         tot.n_roots += q.n_roots;
@@ -467,6 +470,8 @@ int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
         tot.jumped += q.jumped;
         tot.star_terms += q.star_terms;
         tot.far_evals += q.far_evals;
+        tot.root_terms += q.root_terms;
+        tot.split_redone_rows += q.split_redone_rows;
         bad = bad || q.unconverged || q.uncertified;
     }
     tot.trace_ms = t01;

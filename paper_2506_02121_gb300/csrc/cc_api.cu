@@ -184,6 +184,7 @@ int cc_options_default(cc_options* opt) {
     opt->rect_eps = 1e-9;
     opt->rect_s = 2.0;
     opt->row_ctas = 0;
+    opt->root_refresh = 0;
     return CC_OK;
 }
 
@@ -280,6 +281,8 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
     if (o.far_field != 0 && o.far_field != 1) return fail(CC_EINVAL, "cc_field_create: far_field must be 0 or 1");
     if (o.predictor < 0 || o.predictor > 2) return fail(CC_EINVAL, "cc_field_create: predictor must be 0, 1 or 2");
     if (o.row_ctas < 0 || o.row_ctas > 16) return fail(CC_EINVAL, "cc_field_create: row_ctas must be in [0, 16]");
+    if (o.root_refresh < 0 || o.root_refresh > 4096)
+        return fail(CC_EINVAL, "cc_field_create: root_refresh must be in [0, 4096]");
     if (o.block_threads != 0 && (o.block_threads < 32 || o.block_threads > 512 || (o.block_threads & 31)))
         return fail(CC_EINVAL, "cc_field_create: block_threads must be 0 or a multiple of 32 in [32, 512]");
 
@@ -492,6 +495,7 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
     ta.max_iter_cold = f->opt.max_iter_cold;
     ta.max_iter_warm = f->opt.max_iter_warm;
     ta.predictor = f->opt.predictor;
+    ta.root_refresh = f->opt.root_refresh;
     ta.threads = L.threads;
     ta.cluster = L.G;
     CC_CUDA(launch_trace(ta, fp64, st), "trace");
@@ -589,6 +593,8 @@ int cc_field_report(cc_field* f, cc_report* out) {
     out->jumped = (int64_t)r.jumped;
     out->star_terms = (int64_t)r.star_terms;
     out->far_evals = (int64_t)r.far_evals;
+    out->root_terms = (int64_t)r.root_terms;
+    out->split_redone_rows = (int64_t)r.split_redone_rows;
     CC_CUDA(cudaEventElapsedTime(&out->trace_ms, f->ev[0], f->ev[1]), "stage time");
     CC_CUDA(cudaEventElapsedTime(&out->join_ms, f->ev[1], f->ev[2]), "stage time");
     CC_CUDA(cudaEventElapsedTime(&out->polish_ms, f->ev[2], f->ev[3]), "stage time");

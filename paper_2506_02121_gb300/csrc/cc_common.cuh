@@ -159,6 +159,8 @@ struct DevReport {
     unsigned long long rescued_points;  // uncertified points re-solved in FP64 (converged)
     unsigned long long star_terms;      // tracer: star terms summed directly
     unsigned long long far_evals;       // tracer: root updates that used a cell expansion
+    unsigned long long root_terms;      // tracer: root-root terms summed
+    unsigned long long split_redone_rows;  // tracer: rows solved again with the exact root sum
     int max_iter_row;
     int timeout;
     double max_err_est;          // stored as the bit pattern of a non-negative double

@@ -206,6 +206,7 @@ struct TraceArgs {
     DevReport* rep;
     double tol_abs, mu_max;
     int max_iter_cold, max_iter_warm, predictor;
+    int root_refresh;      // FP32 warm rows: exact far part of the root sum every root_refresh rows
     int threads;
     int cluster;           // CTAs per sub-range (> 1: one thread-block cluster per sub-range)
 };
@@ -239,6 +240,7 @@ struct BatchTraceArgs {
     size_t work_stride;
     double tol_abs;
     int max_iter_cold, max_iter_warm, predictor;
+    int root_refresh;
 };
 
 // One field's points for the FP64 rescue of uncertified points.
@@ -276,6 +278,8 @@ struct CurveLayout {
     size_t work_stride;
 };
 
+// Cells per direction available to the near/far split of the tracer's root sum.
+__host__ __device__ inline int near_cells_max(int nr) { return nr / 4 + 64; }
 size_t tracer_work_stride(int64_t nr, size_t elem);
 size_t tracer_smem_bytes(bool fp64, int64_t n);
 int tracer_blocks_per_sm(bool fp64, int threads, int64_t n);
