@@ -60,8 +60,9 @@ def parse():
     p.add_argument("--batched-fields", type=int, default=64)
     p.add_argument("--batched-m", type=int, default=1000)
     p.add_argument("--served-requests", type=int, default=48)
-    p.add_argument("--root-refresh", type=int, default=0,
-                   help="FP32 tracer: exact far part of the Aberth root sum every K warm rows (0 = every sweep)")
+    p.add_argument("--root-refresh", type=int, default=None,
+                   help="FP32 tracer: exact far part of the Aberth root sum every K warm rows (0 = exact in "
+                        "every sweep; default: the library's)")
     return p.parse_args()
 
 
@@ -206,7 +207,8 @@ def run_ours(args):
 
     # outputs and scratch, allocated once
     fopt = cc.cc_options_default()
-    fopt.root_refresh = args.root_refresh
+    if args.root_refresh is not None:
+        fopt.root_refresh = args.root_refresh
     probe = cc.cc_field_create(xs, ys, ms, f.kappa_s, f.gamma, fopt)
     ws_cc = cc.workspace(cc.cc_critical_curves_workspace_bytes(probe, m), dev)
     del probe
@@ -318,7 +320,7 @@ def run_ours(args):
         "config": {"workload": wl.name, "n_stars": f.n, "n_roots": nr, "phi_steps": m,
                    "root_points_per_step": roots_per_step, "map": f"{px}x{px} over +-{ext}",
                    "kappa_star": f.kappa_star, "kappa_s": f.kappa_s, "gamma": f.gamma,
-                   "subchains": rep["subchains"], "root_refresh": args.root_refresh,
+                   "subchains": rep["subchains"], "root_refresh": fopt.root_refresh,
                    "l2": "flushed (256 MiB write) between timed steps",
                    "precision": "FP32 Aberth tracer + double-float certified polish/caustics; FP64 segment tests"},
         "roofline": roofline,
@@ -427,7 +429,8 @@ def batched(args, dev):
     from paper_2506_02121_gb300 import autotune, cc, synth
     wl = synth.workload_batched(args.batched_fields, args.batched_m)
     fopt = cc.cc_options_default()
-    fopt.root_refresh = args.root_refresh
+    if args.root_refresh is not None:
+        fopt.root_refresh = args.root_refresh
     fields = [cc.cc_field_create(f.x, f.y, f.m, f.kappa_s, f.gamma, fopt) for f in wl.fields]
     ms = [wl.msteps] * len(fields)
     t, items, info = autotune.tune(fields, ms, probe_steps=32, repeats=1)

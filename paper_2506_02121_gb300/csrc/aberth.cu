@@ -297,10 +297,12 @@ __device__ __forceinline__ void finish_root(const Ctx<T>& x, int key, typename C
     }
     C zn = z;
     T ad = 0;
+    T q2 = (T)3.0e38;  // |F'/F|^2: the inverse square of the Newton step (huge at F = 0)
     if (Fx != (T)0 || Fy != (T)0) {
         const T fden = Fx * Fx + Fy * Fy;
         const T qx = qdiv(dFx * Fx + dFy * Fy, fden);
         const T qy = qdiv(dFy * Fx - dFx * Fy, fden);
+        q2 = qx * qx + qy * qy;
         const T px = qx + (T)2 * acc.Cx - acc.Dx;
         const T py = qy + (T)2 * acc.Cy - acc.Dy;
         const T pden = px * px + py * py;
@@ -325,8 +327,13 @@ __device__ __forceinline__ void finish_root(const Ctx<T>& x, int key, typename C
         // never looser than 64x the ulp floor: an iterate that runs away where F' vanishes
         // must not count as converged
         tolz = fmin(tolz, (T)(512.0 * FLT_EPSILON) * sc);
-        // a non-finite step (ad NaN) never freezes a root: it would poison every root sum
-        done = ad < tolz || (its >= 3 && ad > (T)0.25 * (T)x.dprev[key] && ad < (T)4 * tolz);
+        // a non-finite step (ad NaN) never freezes a root: it would poison every root sum.
+        // The Newton step |F/F'| itself must also be near the floor: a small Aberth step can
+        // come from a large root or star sum rather than from F ~ 0 (an iterate stalled
+        // beside another root, or a stale far part of the root sum).
+        const T nlim = (T)16 * tolz;
+        done = (ad < tolz || (its >= 3 && ad > (T)0.25 * (T)x.dprev[key] && ad < (T)4 * tolz)) &&
+               q2 * nlim * nlim > (T)1;
         if (!(ad == ad)) zn = z;
     } else {
         done = ad < (T)K.tol_abs;

@@ -79,3 +79,17 @@ def test_rect_options_rejected_before_any_device_work(lib):
     with pytest.raises(cc.CCError) as e:
         cc.cc_field_create(x, y, m, 0.0, 0.3, o)
     assert e.value.status == cc.CC_EINVAL
+
+
+def test_root_refresh_default_and_range(lib):
+    import numpy as np
+    from paper_2506_02121_gb300 import cc
+    o = cc.cc_options_default()
+    assert o.root_refresh == 8 and o.row_ctas == 0
+    x, y, m = np.zeros(1), np.zeros(1), np.ones(1)
+    for bad in (-1, 4097):
+        o = cc.cc_options_default()
+        o.root_refresh = bad
+        with pytest.raises(cc.CCError) as e:
+            cc.cc_field_create(x, y, m, 0.0, 0.3, o)
+        assert e.value.status == cc.CC_EINVAL, bad

@@ -84,3 +84,19 @@ def test_split_batched_equals_single_and_replay():
     for f, m, z in zip(flds, ms, b.z):
         zo, _, bad = oracle.critical_curves(f.x, f.y, f.m, f.kappa_s, f.gamma, m)
         compare_chain(z.cpu().numpy(), zo, 1e-9)
+
+
+@pytest.mark.parametrize("k", [0, 8])
+def test_repeated_solves_are_bit_identical(k):
+    """Rows wide enough for the blocked sweep (n_r >= 2 x 512) with both phi directions
+    active: each root's arithmetic must not depend on the thread slot the active list gives
+    it, whose order follows shared-memory atomics."""
+    f = synth.disc_field(700, 0.4, 0.1, 0.3, synth.stream_seed(14, k))
+    m = 120
+    outs = []
+    for _ in range(3):
+        fld = cc.cc_field_create(f.x, f.y, f.m, f.kappa_s, f.gamma, _opt(k))
+        z, w, it = cc.critical_curves(fld, m, caustics=True, iters=True)
+        outs.append((z, w, it))
+    for z, w, it in outs[1:]:
+        assert torch.equal(z, outs[0][0]) and torch.equal(w, outs[0][1]) and torch.equal(it, outs[0][2])
