@@ -221,21 +221,26 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     launches_per_step = 0
 
-    def step(timers=None):
+    def step():
+        """Enqueue one step on the stream; returns the field, the stage events and an event
+        recorded after the step's last kernel (the field is released, and its report read,
+        only after that event: neither is part of the step's work)."""
         nonlocal launches_per_step
         field = cc.cc_field_create(xs, ys, ms, f.kappa_s, f.gamma, fopt)
         cc.cc_critical_curves(field, m, z, w, None, ws_cc, stream)
-        ev = None
-        if timers is not None:
-            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-                  torch.cuda.Event(enable_timing=True))
-            ev[0].record(stream)
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+              torch.cuda.Event(enable_timing=True))
+        ev[0].record(stream)
         cc.cc_crossing_map(w, -ext, ext, -ext, ext, px, px, ncc, stream)
-        if ev:
-            ev[1].record(stream)
+        ev[1].record(stream)
         cc.cc_distance_map(ncc, pixel, dmap, ws_d, stream)
-        if ev:
-            ev[2].record(stream)
+        ev[2].record(stream)
+        end = torch.cuda.Event(enable_timing=True)
+        end.record(stream)
+        return field, ev, end
+
+    def report(field):
+        nonlocal launches_per_step
         status, rep = cc.cc_field_report(field)
         S = rep["subchains"]
         # phase table, tracer, seam match (S > 1), permutation compose; polish stage (far field:
@@ -244,12 +249,13 @@ def run_ours(args):
         # distance map feature, chunk, column and row kernels
         polish_kernels = 7 if f.n >= 128 else 1
         launches_per_step = 1 + 1 + (1 if S > 1 else 0) + 1 + polish_kernels + 1 + 2 + 4
-        if timers is not None:
-            timers.append((rep, ev, status))
         return status, rep
 
     for _ in range(args.warmup):
-        step()
+        fld, _, end = step()
+        end.synchronize()
+        report(fld)
+        del fld
     torch.cuda.synchronize()
 
     timers = []
@@ -261,12 +267,13 @@ def run_ours(args):
         for _ in range(args.steps):
             flush.fill_(1)  # L2 flush between timed steps (outside the step's events)
             e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(timers)
-            e1.record(stream)
+            fld, ev, e1 = step()
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
+            status, rep = report(fld)
+            timers.append((rep, ev, status))
+            del fld
         torch.cuda.synchronize()
         barrier()
         wall = time.perf_counter() - t_wall0

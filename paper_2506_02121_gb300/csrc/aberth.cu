@@ -110,6 +110,7 @@ struct TK {
     double tol_abs, mu_max;
     int max_iter_cold, max_iter_warm, predictor;
     int root_refresh;  // FP32 warm rows: exact far part of the root sum every root_refresh rows (< 2: every sweep)
+    int near_cap;      // rows of up to near_cap roots keep the split's ordered positions in shared memory
     // FP32 far-field tables (tfmm.ok == 0: every star summed directly)
     TfmmParams tfmm;
     const TCell* tcells;
@@ -145,6 +146,8 @@ struct Ctx {
     int* nfill;     // [d ncm + c]: scatter counters
     float2* nref;   // positions at the last refresh
     float2* npred;  // this row's predicted positions
+    int* nrank;     // position of root k in nord
+    int* act2;      // second active list (split sweeps alternate between act and act2)
     int ncm;        // cells available per direction
     int* s_ngrid;   // shared: nbx, nby of direction d at [2 d], [2 d + 1]
     float* s_nlim2; // shared: squared displacement limit (h / 4)^2 of direction d
@@ -379,15 +382,27 @@ __device__ __forceinline__ int near_sum(const Ctx<float>& x, int key, float zx, 
     const int* cst = x.ncst + (size_t)d * (x.ncm + 1);
     const float2* p = x.npos + (size_t)d * nr;
     const int xa = max(cx - 1, 0), xb = min(cx + 1, nbx - 1);
+    const f2p zxx = f2_pack(zx, zx), zyy = f2_pack(zy, zy);
+    f2p Dx2 = f2_pack(0.f, 0.f), Dy2 = Dx2;
     int cnt = 0;
     for (int yy = max(cy - 1, 0); yy <= min(cy + 1, nby - 1); yy++) {
         const int i0 = cst[yy * nbx + xa], i1 = cst[yy * nbx + xb + 1];
         cnt += i1 - i0;
-        for (int i = i0; i < i1; i++) {
+        int i = i0;
+        for (; i + 1 < i1; i += 2) {
+            const float2 r0 = p[i], r1 = p[i + 1];
+            acc_root_f2(zxx, zyy, f2_pack(r0.x, r1.x), f2_pack(r0.y, r1.y), Dx2, Dy2);
+        }
+        if (i < i1) {
             const float2 r = p[i];
             acc_root_f(zx, zy, r.x, r.y, Dx, Dy);
         }
     }
+    float ua, ub, va, vb;
+    f2_unpack(Dx2, ua, ub);
+    f2_unpack(Dy2, va, vb);
+    Dx += ua + ub;
+    Dy -= va + vb;
     return cnt;
 }
 
@@ -506,6 +521,9 @@ __device__ void near_build(const Ctx<float>& x, int d) {
             ord[j + 1] = v;
         }
     }
+    __syncthreads();
+    int* rank = x.nrank + (size_t)d * nr;
+    for (int i = tid; i < nr; i += P) rank[ord[i]] = i;
     __syncthreads();
 }
 
@@ -777,18 +795,60 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             if (a1) near_build(x, 1);
         }
     }
+    int Ap0 = 0, Ap1 = 0;  // previous sweep's list lengths (split sweeps)
     for (int iter = 0;; iter++) {
         __syncthreads();
         if (tid < 2) s_count[tid] = 0;
         __syncthreads();
-        for (int i = tid; i < 2 * W; i += P) {
-            const int d = i >= W;
-            const int key = d * nr + lo + (i - d * W);
-            const bool on = d ? a1 : a0;
-            if (on && !x.conv[key]) x.act[d * nr + lo + atomicAdd(&s_count[d], 1)] = key;
+        bool listed = false;
+        if constexpr (sizeof(T) == 4 && !WIDE) {
+            if (split) {
+                listed = true;
+                if (iter == 0) {
+                    // every root of the active directions (all unfrozen at a row's start), in
+                    // cell order so that a warp's roots are neighbours (near sets of equal
+                    // length over the same entries), and all positions in cell order
+                    for (int i = tid; i < nr; i += P) {
+                        if (a0) {
+                            const int k = x.nord[i];
+                            x.act[i] = k;
+                            x.npos[i] = x.cur[k];
+                        }
+                        if (a1) {
+                            const int k = x.nord[nr + i];
+                            x.act[nr + i] = nr + k;
+                            x.npos[nr + i] = x.cur[nr + k];
+                        }
+                    }
+                    if (tid == 0) {
+                        s_count[0] = a0 ? nr : 0;
+                        s_count[1] = a1 ? nr : 0;
+                    }
+                } else {
+                    // the previous list's unfrozen roots, into the other list
+                    const int* src = xs.act;
+                    int* dst = xs.act == x.act ? x.act2 : x.act;
+                    for (int i = tid; i < Ap0 + Ap1; i += P) {
+                        const int key = i < Ap0 ? src[i] : src[nr + i - Ap0];
+                        const int d = key >= nr ? 1 : 0;
+                        if (!x.conv[key]) dst[d * nr + atomicAdd(&s_count[d], 1)] = key;
+                    }
+                    xs.act = dst;
+                }
+            }
+        }
+        if (!listed) {
+            for (int i = tid; i < 2 * W; i += P) {
+                const int d = i >= W;
+                const int key = d * nr + lo + (i - d * W);
+                const bool on = d ? a1 : a0;
+                if (on && !x.conv[key]) x.act[d * nr + lo + atomicAdd(&s_count[d], 1)] = key;
+            }
         }
         __syncthreads();
         const int A0 = s_count[0], A1 = s_count[1];
+        Ap0 = A0;
+        Ap1 = A1;
         const int A = A0 + A1;
         int At = A;
         if constexpr (WIDE) {
@@ -811,14 +871,6 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         }
         bool blocked = false;
         if constexpr (sizeof(T) == 4 && !WIDE) {
-            if (mode != SUM_FULL) {
-                // the active directions' current positions in cell order
-                for (int i = tid; i < nr; i += P) {
-                    if (a0) x.npos[i] = x.cur[x.nord[i]];
-                    if (a1) x.npos[nr + i] = x.cur[nr + x.nord[nr + i]];
-                }
-                __syncthreads();
-            }
             if (mode == SUM_LIGHT) {
                 sweep_light(xs, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
                 blocked = true;
@@ -918,6 +970,8 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         for (int i = tid; i < A; i += P) {
             const int key = i < A0 ? xs.act[i] : xs.act[nr + i - A0];
             x.cur[key] = x.nxt[key];
+            if constexpr (sizeof(T) == 4 && !WIDE)
+                if (split) x.npos[(key >= nr ? nr : 0) + x.nrank[key]] = x.nxt[key];
         }
     }
     // directions that still hold unfrozen roots
@@ -1039,6 +1093,16 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
         x.nref = (float2*)nb;
         nb += sizeof(float2) * 2 * (size_t)nr;
         x.npred = (float2*)nb;
+        nb += sizeof(float2) * 2 * (size_t)nr;
+        x.nrank = (int*)nb;
+        nb += sizeof(int) * 2 * (size_t)nr;
+        x.act2 = (int*)nb;
+        if (nr <= K.near_cap) {
+            // ordered positions and cell starts in shared memory, after the root tiles
+            unsigned char* ns = (unsigned char*)(x.s_root + 2 * TR);
+            x.npos = (float2*)ns;
+            x.ncst = (int*)(ns + sizeof(float2) * 2 * (size_t)nr);
+        }
     }
     __shared__ int s_ngrid[4], s_nesc;
     __shared__ float s_nlim2[2];
@@ -1282,6 +1346,7 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
         K.tnear = t.tnear;
         K.tcoeff = t.tcoeff;
         K.root_refresh = B.root_refresh;
+        K.near_cap = B.near_cap;
         if (threadIdx.x == 0) s_maxit = 0;
         n_terms = 0;
         n_far = 0;
@@ -1292,18 +1357,22 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
     }
 }
 
-// Shared memory of a tracing CTA: a star tile of min(n, TS) stars, then the root tiles.
-size_t tracer_smem_bytes(bool fp64, int64_t n) {
+// Shared memory of a tracing CTA: a star tile of min(n, TS) stars, then the root tiles, then
+// (near_cap > 0) the split's ordered positions and cell starts for rows of up to near_cap roots.
+size_t tracer_smem_bytes(bool fp64, int64_t n, int near_cap) {
     const int64_t ts = std::min<int64_t>(n, fp64 ? CT<double>::TS : CT<float>::TS);
-    return fp64 ? ts * sizeof(StarD) + 2 * TR * sizeof(double2) : ts * sizeof(float4) + 2 * TR * sizeof(float2);
+    size_t b = fp64 ? ts * sizeof(StarD) + 2 * TR * sizeof(double2) : ts * sizeof(float4) + 2 * TR * sizeof(float2);
+    if (near_cap > 0)
+        b += sizeof(float2) * 2 * (size_t)near_cap + sizeof(int) * 2 * (size_t)(near_cells_max(near_cap) + 1);
+    return b;
 }
 
 size_t tracer_work_stride(int64_t nr, size_t elem) {
     size_t b = (size_t)(2 * nr) * (4 * elem + 4 * 4);
     // near/far split of the root sum: far part, ordered, refresh and predicted positions
-    // (float2), cell and ordered index (int) per root; cell starts and scatter counters per
-    // direction
-    b += (size_t)(2 * nr) * (4 * sizeof(float2) + 2 * sizeof(int)) +
+    // (float2), cell, ordered index, rank and a second active list (int) per root; cell starts
+    // and scatter counters per direction
+    b += (size_t)(2 * nr) * (4 * sizeof(float2) + 4 * sizeof(int)) +
          (size_t)2 * (2 * (size_t)near_cells_max((int)nr) + 1) * sizeof(int) + 16;
     return (b + 255) / 256 * 256;
 }
@@ -1400,7 +1469,8 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
     K.tcells = a.f->tcells;
     K.tnear = a.f->tnear;
     K.tcoeff = a.f->tcoeff;
-    const size_t smem = tracer_smem_bytes(fp64, a.f->n);
+    K.near_cap = (!fp64 && a.cluster <= 1 && a.root_refresh >= 2 && a.f->nr <= NEAR_SMEM_NR) ? (int)a.f->nr : 0;
+    const size_t smem = tracer_smem_bytes(fp64, a.f->n, K.near_cap);
     cudaError_t e;
     if (!fp64 && a.cluster > 1) {
         e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1670,7 +1740,7 @@ cudaError_t launch_rescue(const RescueTask* host_task, const RescueTask* dev_tas
 }
 
 cudaError_t launch_trace_batch(const BatchTraceArgs& b, int grid, int threads, cudaStream_t st) {
-    const size_t smem = tracer_smem_bytes(false, (int64_t)CT<float>::TS);
+    const size_t smem = tracer_smem_bytes(false, (int64_t)CT<float>::TS, b.near_cap);
     cudaError_t e = cudaFuncSetAttribute(trace_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     trace_batch_kernel<float><<<grid, threads, smem, st>>>(b);
@@ -1689,9 +1759,9 @@ cudaError_t launch_seam_join_batch(const TraceTask* tasks, int count, const int2
     return cudaGetLastError();
 }
 
-int tracer_batch_blocks_per_sm(int threads) {
+int tracer_batch_blocks_per_sm(int threads, int near_cap) {
     int b = 0;
-    const size_t smem = tracer_smem_bytes(false, (int64_t)CT<float>::TS);
+    const size_t smem = tracer_smem_bytes(false, (int64_t)CT<float>::TS, near_cap);
     cudaError_t e = cudaFuncSetAttribute(trace_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, trace_batch_kernel<float>, threads, smem);
     if (e != cudaSuccess || b < 1) {

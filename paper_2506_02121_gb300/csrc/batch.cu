@@ -28,6 +28,7 @@ struct cc_batch {
     cc_options opt;
     int threads = 512, grid = 1;
     int nitems = 0, nseams = 0, max_nr = 0;
+    int near_cap = 0;  // rows of up to near_cap roots keep the tracer's split in shared memory
     int64_t max_m = 0, total_blocks = 0;
     // workspace layout
     std::vector<size_t> off_phase, off_zrows, off_seam, off_iters, off_match, off_perm, off_hits;
@@ -96,6 +97,7 @@ cudaError_t enqueue(cc_batch* b, cudaStream_t st, bool capturing) {
     a.max_iter_warm = b->opt.max_iter_warm;
     a.predictor = b->opt.predictor;
     a.root_refresh = b->opt.root_refresh;
+    a.near_cap = b->near_cap;
     if ((e = launch_trace_batch(a, b->grid, b->threads, st)) != cudaSuccess) return e;
     if ((e = rec(b->ev[1], st, capturing)) != cudaSuccess) return e;
     if ((e = launch_seam_join_batch(tasks, b->count, (const int2*)(ws + b->off_seams), b->nseams, b->max_nr, st)) !=
@@ -177,7 +179,8 @@ int cc_batch_create(cc_field* const* fields, int32_t count, const int64_t* m, in
     b->threads = block_threads > 0 ? block_threads : (b->opt.block_threads > 0 ? b->opt.block_threads : 512);
     int sms = 1;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    b->grid = sms * tracer_batch_blocks_per_sm(b->threads);
+    b->near_cap = b->opt.root_refresh >= 2 ? std::min(b->max_nr, NEAR_SMEM_NR) : 0;
+    b->grid = sms * tracer_batch_blocks_per_sm(b->threads, b->near_cap);
     // sub-ranges per field: about items_per_cta (default 4) items per resident CTA overall,
     // each field's items of similar size; a sub-range keeps >= 32 rows so its cold start
     // stays a small overhead

@@ -241,6 +241,7 @@ struct BatchTraceArgs {
     double tol_abs;
     int max_iter_cold, max_iter_warm, predictor;
     int root_refresh;
+    int near_cap;           // shared-memory rows of the split (0: none)
 };
 
 // One field's points for the FP64 rescue of uncertified points.
@@ -260,7 +261,7 @@ constexpr int RESCUE_MAX_POINTS = 65536;
 cudaError_t launch_rescue(const RescueTask* host_task, const RescueTask* dev_tasks, const int4* list, const int* nlist,
                           int max_list, double tol_abs, int max_iter, cudaStream_t st);
 
-int tracer_batch_blocks_per_sm(int threads);
+int tracer_batch_blocks_per_sm(int threads, int near_cap);
 cudaError_t launch_phase_batch(const TraceTask* tasks, int count, int64_t max_m, cudaStream_t st);
 cudaError_t launch_trace_batch(const BatchTraceArgs& b, int grid, int threads, cudaStream_t st);
 cudaError_t launch_seam_join_batch(const TraceTask* tasks, int count, const int2* seams, int nseams, int max_nr,
@@ -280,8 +281,10 @@ struct CurveLayout {
 
 // Cells per direction available to the near/far split of the tracer's root sum.
 __host__ __device__ inline int near_cells_max(int nr) { return nr / 4 + 64; }
+// Rows of up to this many roots keep the split's ordered positions in shared memory.
+constexpr int NEAR_SMEM_NR = 4096;
 size_t tracer_work_stride(int64_t nr, size_t elem);
-size_t tracer_smem_bytes(bool fp64, int64_t n);
+size_t tracer_smem_bytes(bool fp64, int64_t n, int near_cap = 0);
 int tracer_blocks_per_sm(bool fp64, int threads, int64_t n);
 int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms, int blocks_per_sm);
 constexpr int WIDE_MIN_NR = 4096;   // automatic cluster tracing from this many roots per row
