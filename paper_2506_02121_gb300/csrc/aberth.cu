@@ -141,12 +141,12 @@ struct Ctx {
     float2* nfar;   // far part of root k's sum, captured at the last refresh row
     float2* npos;   // current positions in cell order
     int* nkey;      // refresh cell of root k
-    int* nord;      // roots in cell order (row-major cells, index order within a cell)
+    int* nord;      // keys d nr + k of direction d's roots in cell order (row-major cells, index order within a cell)
     int* ncst;      // [d (ncm + 1) + c]: first entry of cell c in nord
     int* nfill;     // [d ncm + c]: scatter counters
     float2* nref;   // positions at the last refresh
     float2* npred;  // this row's predicted positions
-    int* nrank;     // position of root k in nord
+    int* nrank;     // [key]: position of the root within its direction's part of nord
     int* act2;      // second active list (split sweeps alternate between act and act2)
     int ncm;        // cells available per direction
     int* s_ngrid;   // shared: nbx, nby of direction d at [2 d], [2 d + 1]
@@ -230,6 +230,7 @@ __device__ __forceinline__ void cell_part(const Ctx<T>& x, int cell, T zx, T zy,
     const TCell tc = K.tcells[cell];
     const int* nl = K.tnear + (size_t)cell * TFMM_NEAR_MAX;
     const typename CT<T>::Star* gs = (const typename CT<T>::Star*)K.stars;
+#pragma unroll 4
     for (int q = lane; q < tc.near_cnt; q += g) {
         const int j = nl[q];
         acc_star(zx, zy, x.resident ? x.s_star[j] : gs[j], acc);
@@ -389,6 +390,7 @@ __device__ __forceinline__ int near_sum(const Ctx<float>& x, int key, float zx, 
         const int i0 = cst[yy * nbx + xa], i1 = cst[yy * nbx + xb + 1];
         cnt += i1 - i0;
         int i = i0;
+#pragma unroll 4
         for (; i + 1 < i1; i += 2) {
             const float2 r0 = p[i], r1 = p[i + 1];
             acc_root_f2(zxx, zyy, f2_pack(r0.x, r1.x), f2_pack(r0.y, r1.y), Dx2, Dy2);
@@ -506,7 +508,7 @@ __device__ void near_build(const Ctx<float>& x, int d) {
     block_scan_inclusive(cst + 1, nc, s_scan);
     for (int k = tid; k < nr; k += P) {
         const int c = key[k];
-        ord[cst[c] + atomicAdd(&fill[c], 1)] = k;
+        ord[cst[c] + atomicAdd(&fill[c], 1)] = d * nr + k;
     }
     __syncthreads();
     for (int c = tid; c < nc; c += P) {
@@ -522,8 +524,7 @@ __device__ void near_build(const Ctx<float>& x, int d) {
         }
     }
     __syncthreads();
-    int* rank = x.nrank + (size_t)d * nr;
-    for (int i = tid; i < nr; i += P) rank[ord[i]] = i;
+    for (int i = tid; i < nr; i += P) x.nrank[ord[i]] = i;
     __syncthreads();
 }
 
@@ -651,40 +652,68 @@ __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool
     }
 }
 
-// One sweep of a row between refreshes: each active root (one per thread) sums its stars as
-// in the full sweep, its near roots exactly at their current positions, and adds its stored
-// far part.
+// One sweep of a row between refreshes: each active root sums its stars as in the full sweep,
+// its near roots exactly at their current positions, and adds its stored far part.  Each
+// thread takes RL roots (slots base, base + P, ...) whose independent loads and sums the
+// compiler interleaves.
+template <int RL>
 __device__ void sweep_light(const Ctx<float>& x, int A0, int A1, float cph0, float sph0, float cph1, float sph1,
                             int* s_maxit) {
     const TK& K = *x.k;
-    const int nr = K.nr, n = K.n;
+    const int nr = K.nr, n = K.n, P = blockDim.x, A = A0 + A1;
     const float4* gs = (const float4*)K.stars;
-    for (int slot = threadIdx.x; slot < A0 + A1; slot += blockDim.x) {
-        const int key = slot < A0 ? x.act[slot] : x.act[nr + slot - A0];
-        const int d = key >= nr ? 1 : 0;
-        const float2 z = x.cur[key];
-        Acc<float> acc = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        const int cell = far_cell<float>(K, z.x, z.y);
-        *x.n_terms += (unsigned long long)(cell >= 0 ? K.tcells[cell].near_cnt : n);
-        *x.n_far += cell >= 0 ? 1ull : 0ull;
-        if (cell >= 0) {
-            cell_part<float>(x, cell, z.x, z.y, 0, 1, acc);
-        } else if (x.resident) {
-#pragma unroll 4
-            for (int j = 0; j < n; j++) acc_star(z.x, z.y, x.s_star[j], acc);
-        } else {
-#pragma unroll 4
-            for (int j = 0; j < n; j++) acc_star(z.x, z.y, gs[j], acc);
+    for (int base = threadIdx.x; base < A; base += RL * P) {
+        int key[RL], cell[RL];
+        bool valid[RL];
+        float2 z[RL];
+        Acc<float> acc[RL];
+#pragma unroll
+        for (int r = 0; r < RL; r++) {
+            const int slot = base + r * P;
+            valid[r] = slot < A;
+            const int sl = valid[r] ? slot : base;
+            key[r] = sl < A0 ? x.act[sl] : x.act[nr + sl - A0];
         }
-        float Dx = 0.f, Dy = 0.f;
-        *x.n_root += (unsigned long long)near_sum(x, key, z.x, z.y, Dx, Dy);
-        const float2 f = x.nfar[key];
-        acc.Dx = Dx + f.x;
-        acc.Dy = Dy + f.y;
-        finish_root<float>(x, key, z, acc, d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
-        const float2 zn = x.nxt[key], zr = x.nref[key];
-        const float ex = zn.x - zr.x, ey = zn.y - zr.y;
-        if (!(ex * ex + ey * ey <= x.s_nlim2[d])) *x.s_nesc = 1;
+#pragma unroll
+        for (int r = 0; r < RL; r++) {
+            z[r] = x.cur[key[r]];
+            acc[r] = Acc<float>{0, 0, 0, 0, 0, 0, 0, 0, 0};
+            cell[r] = far_cell<float>(K, z[r].x, z[r].y);
+        }
+#pragma unroll
+        for (int r = 0; r < RL; r++) {
+            if (!valid[r]) continue;
+            *x.n_terms += (unsigned long long)(cell[r] >= 0 ? K.tcells[cell[r]].near_cnt : n);
+            *x.n_far += cell[r] >= 0 ? 1ull : 0ull;
+            if (cell[r] >= 0) {
+                cell_part<float>(x, cell[r], z[r].x, z[r].y, 0, 1, acc[r]);
+            } else if (x.resident) {
+#pragma unroll 4
+                for (int j = 0; j < n; j++) acc_star(z[r].x, z[r].y, x.s_star[j], acc[r]);
+            } else {
+#pragma unroll 4
+                for (int j = 0; j < n; j++) acc_star(z[r].x, z[r].y, gs[j], acc[r]);
+            }
+        }
+        float Dx[RL], Dy[RL];
+#pragma unroll
+        for (int r = 0; r < RL; r++) {
+            Dx[r] = 0.f;
+            Dy[r] = 0.f;
+            if (valid[r]) *x.n_root += (unsigned long long)near_sum(x, key[r], z[r].x, z[r].y, Dx[r], Dy[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < RL; r++) {
+            if (!valid[r]) continue;
+            const int d = key[r] >= nr ? 1 : 0;
+            const float2 f = x.nfar[key[r]];
+            acc[r].Dx = Dx[r] + f.x;
+            acc[r].Dy = Dy[r] + f.y;
+            finish_root<float>(x, key[r], z[r], acc[r], d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
+            const float2 zn = x.nxt[key[r]], zr = x.nref[key[r]];
+            const float ex = zn.x - zr.x, ey = zn.y - zr.y;
+            if (!(ex * ex + ey * ey <= x.s_nlim2[d])) *x.s_nesc = 1;
+        }
     }
 }
 
@@ -807,19 +836,15 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 if (iter == 0) {
                     // every root of the active directions (all unfrozen at a row's start), in
                     // cell order so that a warp's roots are neighbours (near sets of equal
-                    // length over the same entries), and all positions in cell order
-                    for (int i = tid; i < nr; i += P) {
-                        if (a0) {
-                            const int k = x.nord[i];
-                            x.act[i] = k;
-                            x.npos[i] = x.cur[k];
+                    // length over the same entries): the cell-ordered list itself.  After a
+                    // refresh the positions are gathered in that order; between refreshes the
+                    // prediction pass has already stored them.
+                    if (mode == SUM_CAPTURE)
+                        for (int i = tid; i < nr; i += P) {
+                            if (a0) x.npos[i] = x.cur[x.nord[i]];
+                            if (a1) x.npos[nr + i] = x.cur[x.nord[nr + i]];
                         }
-                        if (a1) {
-                            const int k = x.nord[nr + i];
-                            x.act[nr + i] = nr + k;
-                            x.npos[nr + i] = x.cur[nr + k];
-                        }
-                    }
+                    xs.act = x.nord;
                     if (tid == 0) {
                         s_count[0] = a0 ? nr : 0;
                         s_count[1] = a1 ? nr : 0;
@@ -827,7 +852,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 } else {
                     // the previous list's unfrozen roots, into the other list
                     const int* src = xs.act;
-                    int* dst = xs.act == x.act ? x.act2 : x.act;
+                    int* dst = xs.act == x.act ? x.act2 : x.act;  // (after the first sweep src is nord)
                     for (int i = tid; i < Ap0 + Ap1; i += P) {
                         const int key = i < Ap0 ? src[i] : src[nr + i - Ap0];
                         const int d = key >= nr ? 1 : 0;
@@ -872,7 +897,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         bool blocked = false;
         if constexpr (sizeof(T) == 4 && !WIDE) {
             if (mode == SUM_LIGHT) {
-                sweep_light(xs, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                sweep_light<1>(xs, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
                 blocked = true;
             }
         }
@@ -1156,6 +1181,7 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
         if (!a0 && !a1) break;
         const int64_t r0 = c - t, r1 = c + t;
         __syncthreads();
+        const bool refresh_due = s_refresh != 0;
         for (int i = tid; i < 2 * (hi - lo); i += P) {
             const int dd = i >= hi - lo;
             const int k = dd * nr + lo + (i - dd * (hi - lo));
@@ -1180,8 +1206,14 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             if (h >= 1) x.prev2[k] = x.prev[k];
             x.prev[k] = zc;
             x.cur[k] = g;
-            if constexpr (sizeof(T) == 4)
-                if (KR >= 2) x.npred[k] = g;
+            if constexpr (sizeof(T) == 4) {
+                if (KR >= 2) {
+                    x.npred[k] = g;
+                    // cells from an earlier refresh: the prediction goes to its place in cell
+                    // order (a refresh row gathers all positions again after its new cells)
+                    if (!refresh_due) x.npos[(k >= nr ? nr : 0) + x.nrank[k]] = g;
+                }
+            }
             x.conv[k] = 0;
             x.it[k] = 0;
             x.dprev[k] = FLT_MAX;
