@@ -404,13 +404,23 @@ def e2e(args, f, m, ext, px, pixel, dev, world):
     hd = torch.empty((px, px), dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream(dev)
 
+    copy_stream = torch.cuda.Stream(dev)
+
     def once():
         field = cc.cc_field_create(hx, hy, hm, f.kappa_s, f.gamma)
         z, w, _ = cc.critical_curves(field, m, caustics=True, stream=stream)
+        # the critical points and caustics are final here: copy them back on a second stream
+        # while the maps are computed
+        ready = torch.cuda.Event()
+        ready.record(stream)
+        copy_stream.wait_event(ready)
+        with torch.cuda.stream(copy_stream):
+            hz.copy_(z, non_blocking=True)
+            hw.copy_(w, non_blocking=True)
+        z.record_stream(copy_stream)
+        w.record_stream(copy_stream)
         ncc = cc.crossing_map(w, -ext, ext, -ext, ext, px, px, stream)
         d = cc.distance_map(ncc, pixel, stream)
-        hz.copy_(z, non_blocking=True)
-        hw.copy_(w, non_blocking=True)
         hn.copy_(ncc, non_blocking=True)
         hd.copy_(d, non_blocking=True)
         torch.cuda.synchronize()

@@ -1018,19 +1018,28 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
     return (m0 ? 1 : 0) | (m1 ? 2 : 0) | (esc ? 4 : 0);
 }
 
-// Star guesses z_i +- 1 (Sec. 3.2) into direction d, tilted to z_i +- (1 + i/64):
-// [2i] = z_i + (1 + i/64), [2i+1] = z_i - (1 + i/64).  The tilt breaks the mirror symmetry
-// about the line through a star parallel to the real axis, which FP32 arithmetic keeps
-// exactly (an isolated star at phi = pi would otherwise never leave that line).  A guess
-// equal to an earlier one moves by 1e-3 (1 + i) per earlier copy.
+// Cold-start guesses for direction d at phase phi (cos, sin).  Near star i alone,
+// F = c_i + m_i/(z - z_i)^2 with c_i = gamma - (1 - kappa_s) e^{-i phi} plus the other stars'
+// m_j/(z_i - z_j)^2: its two zeros z_i +- sqrt(-m_i/c_i) start each pair of roots next to
+// where an isolated star's critical points lie, far closer than the generic z_i +- 1
+// (Sec. 3.2), so the cold Aberth solve takes fewer sweeps; the roots it converges to are
+// the same.  A scale 1 + (i mod 64) 2^-12 keeps the guesses of coincident stars apart.
+// Fallback (rectangular field, N > CT<T>::TS, or |c_i| ~ 0): the star guesses
+// z_i +- (1 + i/64), [2i] = z_i + (1 + i/64), [2i+1] = z_i - (1 + i/64).  The tilt breaks
+// the mirror symmetry about the line through a star parallel to the real axis, which FP32
+// arithmetic keeps exactly (an isolated star at phi = pi would otherwise never leave that
+// line).  A guess equal to an earlier one moves by 1e-3 (1 + i) per earlier copy.
 template <typename T>
-__device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
+__device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d, T cph, T sph) {
     using C = typename CT<T>::C;
     using Star = typename CT<T>::Star;
     const TK& K = *x.k;
-    const int nr = K.nr;
+    const int nr = K.nr, n = K.n;
     const Star* gs = (const Star*)K.stars;
     const int n2 = 2 * K.n;
+    const T oms = (T)(1.0 - K.kappa_s);
+    const T c0x = (T)K.gamma - oms * cph, c0y = oms * sph;
+    const bool local = !K.poly && n <= CT<T>::TS;
     for (int k = x.lo + threadIdx.x; k < x.hi; k += blockDim.x) {
         const int key = d * nr + k;
         if (k >= n2) {
@@ -1048,8 +1057,38 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d) {
             x.dprev[key] = FLT_MAX;
             continue;
         }
-        const Star si = gs[k >> 1];
+        const int i = k >> 1;
+        const Star si = gs[i];
         const T sg = (k & 1) ? (T)-1 : (T)1;
+        if (local) {
+            T ax = c0x, ay = c0y;
+            for (int j = 0; j < n; j++) {
+                const Star sj = x.resident ? x.s_star[j] : gs[j];
+                const T dx = (T)si.x - (T)sj.x, dy = (T)si.y - (T)sj.y;
+                const T r2 = dx * dx + dy * dy;
+                if (j == i || !(r2 > (T)0)) continue;
+                const T inv = (T)1 / r2;
+                const T ux = dx * inv, uy = -dy * inv;
+                ax += (T)sj.z * (ux * ux - uy * uy);
+                ay += (T)sj.z * ((T)2 * ux * uy);
+            }
+            const T den = ax * ax + ay * ay;
+            // w = -m_i / c_i, and its principal square root
+            const T wx = -(T)si.z * ax / den, wy = (T)si.z * ay / den;
+            const T r = sqrt(wx * wx + wy * wy);
+            const T sr = sqrt((T)0.5 * (r + wx)), sq = copysign(sqrt((T)0.5 * fmax(r - wx, (T)0)), wy);
+            if (den > (T)1e-12 && sr == sr && sq == sq && r < (T)1e12) {
+                const T sc = sg * ((T)1 + (T)(i & 63) * (T)2.44140625e-4);
+                C z;
+                z.x = (T)si.x + sc * sr;
+                z.y = (T)si.y + sc * sq;
+                x.cur[key] = z;
+                x.conv[key] = 0;
+                x.it[key] = 0;
+                x.dprev[key] = FLT_MAX;
+                continue;
+            }
+        }
         const T gx = (T)si.x + sg, gy = (T)si.y + sg * (T)0.015625;
         int dup = 0;
         for (int a = 0; a < k; a++) {
@@ -1150,8 +1189,11 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     const Star* gs = (const Star*)K.stars;
     if (x.resident)
         for (int j = tid; j < n; j += P) x.s_star[j] = gs[j];
-
-    seed_guesses<T>(x, 0);
+    __syncthreads();  // the guesses read the star tile
+    {
+        const double2 ph = K.phase[c];
+        seed_guesses<T>(x, 0, (T)ph.x, (T)ph.y);
+    }
     for (int k = lo + tid; k < hi; k += P) x.conv[nr + k] = 1;
     solve_rows<T, WIDE>(x, true, false, c, -1, K.max_iter_cold, true, true, s_count, &s_maxit);
 
@@ -1267,8 +1309,8 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             // row sits on a symmetric, non-converging configuration) restarts that row from
             // the star guesses.
             __syncthreads();
-            if (bad & 1) seed_guesses<T>(x, 0);
-            if (bad & 2) seed_guesses<T>(x, 1);
+            if (bad & 1) seed_guesses<T>(x, 0, (T)K.phase[r0].x, (T)K.phase[r0].y);
+            if (bad & 2) seed_guesses<T>(x, 1, (T)K.phase[r1].x, (T)K.phase[r1].y);
             solve_rows<T, WIDE>(x, bad & 1, (bad & 2) != 0, r0, r1, K.max_iter_cold, true, true, s_count, &s_maxit);
         }
         if (a0) {
