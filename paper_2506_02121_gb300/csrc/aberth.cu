@@ -1039,7 +1039,8 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d, T cph, T sp
     const int n2 = 2 * K.n;
     const T oms = (T)(1.0 - K.kappa_s);
     const T c0x = (T)K.gamma - oms * cph, c0y = oms * sph;
-    const bool local = !K.poly && n <= CT<T>::TS;
+    const bool direct = !K.poly && n <= CT<T>::TS;  // the other stars summed one by one
+    const bool tabled = !K.poly && !direct && sizeof(T) == 4 && K.tfmm.ok;  // near stars + cell expansion
     for (int k = x.lo + threadIdx.x; k < x.hi; k += blockDim.x) {
         const int key = d * nr + k;
         if (k >= n2) {
@@ -1060,17 +1061,40 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d, T cph, T sp
         const int i = k >> 1;
         const Star si = gs[i];
         const T sg = (k & 1) ? (T)-1 : (T)1;
-        if (local) {
+        const int cell = tabled ? far_cell<T>(K, (T)si.x, (T)si.y) : -1;
+        if (direct || cell >= 0) {
             T ax = c0x, ay = c0y;
-            for (int j = 0; j < n; j++) {
-                const Star sj = x.resident ? x.s_star[j] : gs[j];
+            auto add = [&](const Star& sj, int j) {
                 const T dx = (T)si.x - (T)sj.x, dy = (T)si.y - (T)sj.y;
                 const T r2 = dx * dx + dy * dy;
-                if (j == i || !(r2 > (T)0)) continue;
+                if (j == i || !(r2 > (T)0)) return;
                 const T inv = (T)1 / r2;
                 const T ux = dx * inv, uy = -dy * inv;
                 ax += (T)sj.z * (ux * ux - uy * uy);
                 ay += (T)sj.z * ((T)2 * ux * uy);
+            };
+            if (direct) {
+                for (int j = 0; j < n; j++) add(x.resident ? x.s_star[j] : gs[j], j);
+            } else {
+                // the cell's near stars, then its expansion of the far stars' S1 about the
+                // cell centre: sum_far m_j/(z - z_j)^2 = -S1'(t), t = z - centre
+                const TCell tc = K.tcells[cell];
+                const int* nl = K.tnear + (size_t)cell * TFMM_NEAR_MAX;
+                for (int q = 0; q < tc.near_cnt; q++) add(gs[nl[q]], nl[q]);
+                const float tx = (float)si.x - tc.cx, ty = (float)si.y - tc.cy;
+                const float4* L = K.tcoeff + (size_t)cell * TFMM_P;
+                float b0x = L[TFMM_P - 1].z, b0y = L[TFMM_P - 1].w, b1x = 0.f, b1y = 0.f;
+                for (int kk = TFMM_P - 2; kk >= 0; kk--) {
+                    const float4 c4 = L[kk];
+                    const float n1x = fmaf(b1x, tx, fmaf(-b1y, ty, b0x)), n1y = fmaf(b1x, ty, fmaf(b1y, tx, b0y));
+                    const float n0x = fmaf(b0x, tx, fmaf(-b0y, ty, c4.z)), n0y = fmaf(b0x, ty, fmaf(b0y, tx, c4.w));
+                    b1x = n1x;
+                    b1y = n1y;
+                    b0x = n0x;
+                    b0y = n0y;
+                }
+                ax -= (T)b1x;
+                ay -= (T)b1y;
             }
             const T den = ax * ax + ay * ay;
             // w = -m_i / c_i, and its principal square root
