@@ -1496,10 +1496,17 @@ int tracer_blocks_per_sm(bool fp64, int threads, int64_t n) {
     return b;
 }
 
-int tracer_cluster_size(const cc_options& o, int64_t nr, bool fp64) {
+// CTAs per sub-range.  Wide rows need a cluster per sub-range when there are too few rows to
+// give every SM a sub-range of its own; with enough rows (at least 8 per SM) one CTA per
+// sub-range is faster when the root sum is split (its cold starts cost one SM each, but
+// every warm row takes a small fraction of the exact sum: N = 20000, m = 2e4 traces in
+// 0.77 s against 9.2 s with clusters).
+int tracer_cluster_size(const cc_options& o, int64_t nr, bool fp64, int64_t m, int sms) {
     if (fp64) return 1;
     if (o.row_ctas > 0) return o.row_ctas;
-    return nr >= WIDE_MIN_NR ? 8 : 1;
+    if (nr < WIDE_MIN_NR) return 1;
+    if (o.root_refresh >= 2 && m >= 8 * (int64_t)sms) return 1;
+    return 8;
 }
 
 int tracer_max_clusters(int G, int threads) {

@@ -89,7 +89,7 @@ CurveLayout curve_layout(const cc_field* f, int64_t m) {
     const bool fp64 = f->opt.precision == CC_FP64;
     L.elem = fp64 ? sizeof(double2) : sizeof(float2);
     L.threads = f->opt.block_threads > 0 ? f->opt.block_threads : 512;
-    L.G = tracer_cluster_size(f->opt, nr, fp64);
+    L.G = tracer_cluster_size(f->opt, nr, fp64, m, sm_count(f->device));
     if (L.G > 1) {
         // one wave of clusters; a sub-range keeps >= 8 rows
         cc_options o = f->opt;

@@ -3,6 +3,7 @@ the chains match the FP64 oracle and the one-CTA tracer, for explicit cluster si
 small fields and for the automatic choice on a field with n_r >= 4096."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2506_02121_gb300 import cc, synth
@@ -63,3 +64,22 @@ def test_automatic_cluster_on_wide_rows():
         assert dist < TOL and len(set(idx.tolist())) == len(idx)
         wo = oracle.map_caustics(f.x, f.y, f.m, f.kappa_s, f.gamma, zg[j])
         assert np.abs(wg[j] - wo).max() < TOL
+
+
+def test_automatic_single_cta_on_long_wide_chains():
+    """n_r = 4200 >= 4096 with m >= 8 x the SM count: one CTA per sub-range (the root sum split
+    then keeps warm rows cheap), its near positions in global memory (n_r above the shared
+    tile); rows match the oracle."""
+    n = 2100
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    msteps = 8 * sms + 2
+    f = synth.disc_field(n, 0.3, 0.1, 0.3, synth.stream_seed(33, 1), "loguniform", normalise=True)
+    zg, wg, st, rep = _solve(f, msteps, cc.cc_options_default())
+    assert st == cc.CC_OK and rep["uncertified"] == 0 and rep["seam_ambiguous"] == 0, rep
+    assert rep["subchains"] > 32  # one CTA per sub-range, not one cluster of 8
+    assert rep["root_terms"] < 0.5 * rep["root_iterations"] * 2 * n
+    for j in [0, msteps // 2 + 3, msteps]:
+        zo, left = oracle.solve_row(f.x, f.y, f.m, f.kappa_s, f.gamma, oracle.phi(j, msteps))
+        assert left == 0
+        idx, dist, sep = match_row(zg[j], zo)
+        assert dist < TOL and len(set(idx.tolist())) == len(idx)
