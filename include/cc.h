@@ -111,7 +111,7 @@ typedef struct cc_options {
                               of a chain, where each root's sum is split into the roots of the 3 x 3
                               cells around it (summed exactly in every sweep) and the rest (kept
                               from the refresh row).  The roots found are the same zeros of F; only
-                              the Aberth iteration path changes.  At most 4096; default 32. */
+                              the Aberth iteration path changes.  At most 4096; default 64. */
 } cc_options;
 
 /* Solve statistics of the last cc_critical_curves on a field (host copy). */

@@ -184,7 +184,7 @@ int cc_options_default(cc_options* opt) {
     opt->rect_eps = 1e-9;
     opt->rect_s = 2.0;
     opt->row_ctas = 0;
-    opt->root_refresh = 32;
+    opt->root_refresh = 64;
     return CC_OK;
 }
 

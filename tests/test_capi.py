@@ -85,7 +85,7 @@ def test_root_refresh_default_and_range(lib):
     import numpy as np
     from paper_2506_02121_gb300 import cc
     o = cc.cc_options_default()
-    assert o.root_refresh == 32 and o.row_ctas == 0
+    assert o.root_refresh == 64 and o.row_ctas == 0
     x, y, m = np.zeros(1), np.zeros(1), np.ones(1)
     for bad in (-1, 4097):
         o = cc.cc_options_default()
