@@ -150,6 +150,31 @@ int fetch_host(double* dst, const double* src, int64_t n, const char* what) {
 
 bool finite3(double a, double b, double c) { return std::isfinite(a) && std::isfinite(b) && std::isfinite(c); }
 
+// A stream-ordered memory pool per device, owned by the library, for the fields' device
+// blocks: a field created and destroyed in a loop reuses cached memory instead of paying
+// cudaMalloc / cudaFree and their device-wide synchronisation each time.
+cudaError_t field_pool(int device, cudaMemPool_t* pool) {
+    static std::mutex mu;
+    static std::vector<cudaMemPool_t> pools;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)pools.size() <= device) pools.resize(device + 1, nullptr);
+    if (!pools[device]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t p;
+        cudaError_t e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = ~0ull;  // keep freed blocks for reuse
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) return e;
+        pools[device] = p;
+    }
+    *pool = pools[device];
+    return cudaSuccess;
+}
+
 }  // namespace
 
 int ccg::api_error(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -387,7 +412,9 @@ int cc_field_create(const double* x, const double* y, const double* mass, int64_
     f->dev.tfmm.ok = 0;
     f->solved = false;
     cudaGetDevice(&f->device);
-    cudaError_t e = cudaMalloc(&f->block, off);
+    cudaMemPool_t pool;
+    cudaError_t e = field_pool(f->device, &pool);
+    e = e ? e : cudaMallocFromPoolAsync(&f->block, off, pool, 0);
     e = e ? e : cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming);
     e = e ? e : cudaEventCreateWithFlags(&f->ready, cudaEventDisableTiming);
     for (int i = 0; i < 4; i++) e = e ? e : cudaEventCreate(&f->ev[i]);
@@ -429,7 +456,7 @@ int cc_field_destroy(cc_field* f) {
     if (!f) return CC_OK;
     if (f->done) cudaEventSynchronize(f->done);
     if (f->ready) cudaEventSynchronize(f->ready);
-    cudaFree(f->block);
+    if (f->block) cudaFreeAsync(f->block, 0);
     if (f->done) cudaEventDestroy(f->done);
     if (f->ready) cudaEventDestroy(f->ready);
     for (int i = 0; i < 4; i++)

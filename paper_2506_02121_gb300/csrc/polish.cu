@@ -33,6 +33,7 @@ struct PolishK {
     int64_t nr, m, points;
     int S;
     double kappa_s, gamma;
+    double wgx, wgy;      // 1 - kappa_s + gamma, 1 - kappa_s - gamma (the lens map's linear terms)
     const double2* phase;
     const float2* zrows;
     const int32_t* perm;
@@ -283,9 +284,8 @@ __device__ __forceinline__ bool polish_epilogue_df(const PolishK& K, int64_t poi
     const double ozx = tf_to_double(nzx), ozy = tf_to_double(nzy);
     K.z_out[point] = make_double2(ozx, ozy);
     if (K.w_out) {
-        const double oms = 1.0 - K.kappa_s;
-        double wx = fma(oms + K.gamma, ozx, -df_to_double(S1nx));
-        double wy = fma(oms - K.gamma, ozy, df_to_double(S1ny));
+        double wx = fma(K.wgx, ozx, -df_to_double(S1nx));
+        double wy = fma(K.wgy, ozy, df_to_double(S1ny));
         if (K.poly) {
             const double2 V = poly_V(K.poly, ozx, ozy);
             wx += V.x;
@@ -453,6 +453,8 @@ static PolishK make_polish_k(const PolishArgs& a) {
     K.S = a.S;
     K.kappa_s = a.f->kappa_s;
     K.gamma = a.f->gamma;
+    K.wgx = 1.0 - a.f->kappa_s + a.f->gamma;
+    K.wgy = 1.0 - a.f->kappa_s - a.f->gamma;
     K.phase = a.phase;
     K.zrows = a.zrows;
     K.perm = a.perm;
@@ -1007,7 +1009,7 @@ __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const
     const int64_t row0 = (wg / K.nr) * 32 + lane;
     const bool valid = wg < K.nr * ((K.m + 32) / 32) && row0 <= K.m;
     int passes = 0;
-    double est_max = 0.0;
+    float est_max = 0.f;  // certified estimates are FP32 values
     if (valid) {
     const int64_t row = row0;
     const int64_t point = row * K.nr + g;
@@ -1088,18 +1090,18 @@ __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const
         sm.a3 += 4.0f * (fabsf(b2x) + fabsf(b2y));
         double est = 0.0;
         if (polish_epilogue_df(K, point, row, sm, cxr, cyr, zxt, zyt, z0.x, z0.y, pass, it_in, est, bi.s2_err)) {
-            est_max = est;
+            est_max = (float)est;
             break;
         }
     }
     }  // valid
     for (int off = 16; off > 0; off >>= 1) {
         passes += __shfl_xor_sync(0xffffffffu, passes, off);
-        est_max = fmax(est_max, __shfl_xor_sync(0xffffffffu, est_max, off));
+        est_max = fmaxf(est_max, __shfl_xor_sync(0xffffffffu, est_max, off));
     }
     if (lane == 0) {
         if (passes) atomicAdd(&K.rep->polish_passes, (unsigned long long)passes);
-        if (est_max > 0.0) atomic_max_double_nonneg(&K.rep->max_err_est, est_max);
+        if (est_max > 0.f) atomic_max_double_nonneg(&K.rep->max_err_est, (double)est_max);
     }
 }
 
