@@ -1024,7 +1024,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
 // where an isolated star's critical points lie, far closer than the generic z_i +- 1
 // (Sec. 3.2), so the cold Aberth solve takes fewer sweeps; the roots it converges to are
 // the same.  A scale 1 + (i mod 64) 2^-12 keeps the guesses of coincident stars apart.
-// Fallback (rectangular field, N > CT<T>::TS, or |c_i| ~ 0): the star guesses
+// Fallback (rectangular field, no table and N > CT<T>::TS, or |c_i| ~ 0): the star guesses
 // z_i +- (1 + i/64), [2i] = z_i + (1 + i/64), [2i+1] = z_i - (1 + i/64).  The tilt breaks
 // the mirror symmetry about the line through a star parallel to the real axis, which FP32
 // arithmetic keeps exactly (an isolated star at phi = pi would otherwise never leave that
@@ -1039,8 +1039,10 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d, T cph, T sp
     const int n2 = 2 * K.n;
     const T oms = (T)(1.0 - K.kappa_s);
     const T c0x = (T)K.gamma - oms * cph, c0y = oms * sph;
-    const bool direct = !K.poly && n <= CT<T>::TS;  // the other stars summed one by one
-    const bool tabled = !K.poly && !direct && sizeof(T) == 4 && K.tfmm.ok;  // near stars + cell expansion
+    // the other stars' terms: near stars + the cell's expansion where the FP32 tables exist
+    // (a few dozen terms), else summed one by one from the shared star tile
+    const bool tabled = !K.poly && sizeof(T) == 4 && K.tfmm.ok;
+    const bool direct = !K.poly && !tabled && n <= CT<T>::TS;
     for (int k = x.lo + threadIdx.x; k < x.hi; k += blockDim.x) {
         const int key = d * nr + k;
         if (k >= n2) {
