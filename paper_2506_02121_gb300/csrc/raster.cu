@@ -358,14 +358,19 @@ __device__ __forceinline__ long long edt_key(const int32_t* f, int q) {
 // keeps a prefix of the left hull and a suffix of the right one, found by walking both
 // ends until neither end point can be dropped); then the warp fills the row 32 pixels at
 // a time, each lane walking the hull forward from the owner of the tile's first pixel.
-// Band position k of lane l is stored at [k * EDT_LS + l] (16-bit entries), so the lanes
-// of a warp stepping through their bands together never share a shared-memory bank word
-// they do not also share an address in.
+// Band position k of lane l is stored at [k * EDT_LS + l] (16-bit g values; 8- or 16-bit
+// stack entries), so the lanes of a warp stepping through their bands together never share
+// a shared-memory bank word they do not also share an address in.
 constexpr int EDT_BAND_MAX_W = 32768;
 constexpr int EDT_BAND_MAX_H = 65535;  // g < H fits 16 bits, 0xFFFF marks "no feature"
 constexpr int EDT_LS = 33;
 
-size_t edt_band_smem(int W) { return 2 * sizeof(uint16_t) * (size_t)((W + 31) / 32) * EDT_LS; }
+// g values (16 bits) and hull stacks of band positions (8 bits while a band holds at most
+// 256 columns, i.e. W <= 8192, else 16): the smaller stacks let more rows share an SM.
+size_t edt_band_smem(int W) {
+    const size_t Bw = (size_t)((W + 31) / 32);
+    return (sizeof(uint16_t) + (Bw <= 256 ? sizeof(uint8_t) : sizeof(uint16_t))) * Bw * EDT_LS;
+}
 
 __device__ __forceinline__ long long edt_lift(int q, int gq) { return (long long)q * q + (long long)gq * gq; }
 
@@ -383,6 +388,7 @@ __global__ void edt_sqrt_table_kernel(double* tab, int T) {
     if (k < T) tab[k] = sqrt((double)k);
 }
 
+template <typename ST>
 __global__ void __launch_bounds__(32) edt_row_band_kernel(const int32_t* g, int W, double pixel, double* d_out,
                                                           const double* sqtab, int T) {
     extern __shared__ uint16_t edt_sh[];
@@ -390,7 +396,7 @@ __global__ void __launch_bounds__(32) edt_row_band_kernel(const int32_t* g, int 
     const int r = blockIdx.x, lane = threadIdx.x;
     const int Bw = (W + 31) / 32;
     uint16_t* gs = edt_sh;                          // g by (band position, lane)
-    uint16_t* st = edt_sh + (size_t)Bw * EDT_LS;    // hull stacks: band positions
+    ST* st = (ST*)(edt_sh + (size_t)Bw * EDT_LS);   // hull stacks: band positions
     const int32_t* gr = g + (int64_t)r * W;
     {
         int l = lane / Bw, k = lane - l * Bw;  // column q = lane
@@ -425,7 +431,7 @@ __global__ void __launch_bounds__(32) edt_row_band_kernel(const int32_t* g, int 
                 cu = edt_lift(a + ku, site_g(lane, ku));
             }
         }
-        st[len * EDT_LS + lane] = (uint16_t)k;
+        st[len * EDT_LS + lane] = (ST)k;
         len++;
         ku = kv;
         cu = cv;
@@ -673,9 +679,17 @@ cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double
         double* sqtab = (double*)v;
         edt_sqrt_table_kernel<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(sqtab, T);
         const size_t smem = edt_band_smem(W);
-        e = cudaFuncSetAttribute(edt_row_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        edt_row_band_kernel<<<(unsigned)H, 32, smem, st>>>(g, W, pixel, d_out, sqtab, T);
+        if ((W + 31) / 32 <= 256) {
+            e = cudaFuncSetAttribute(edt_row_band_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+            edt_row_band_kernel<uint8_t><<<(unsigned)H, 32, smem, st>>>(g, W, pixel, d_out, sqtab, T);
+        } else {
+            e = cudaFuncSetAttribute(edt_row_band_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+            edt_row_band_kernel<uint16_t><<<(unsigned)H, 32, smem, st>>>(g, W, pixel, d_out, sqtab, T);
+        }
     } else {
         edt_row_kernel<<<(unsigned)((H + 63) / 64), 64, 0, st>>>(g, W, H, pixel, v, d_out);
     }
