@@ -998,6 +998,25 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
 
 // Points: warp = one chain (global column g), 32 consecutive rows, so that a warp's
 // points sit in one or two neighbouring cells.
+// a1 b1 + a2 b2 + c in double-float with one normalisation: the two high products and the
+// two sums are formed exactly (two_prod, two_sum), and their error terms, c's low part and
+// the four cross products of the low parts are gathered by FP32 adds and FMAs.  26 FP32
+// operations against 32 for two df_mul, a df_add and a df_sub, with the same ~2^-46
+// relative rounding (the final fast two-sum assumes, as df_add does, that the sum does not
+// cancel below its accumulated error).
+__device__ __forceinline__ df df_dot2_add(df a1, df b1, df a2, df b2, df c) {
+    const df p1 = two_prod(a1.hi, b1.hi), p2 = two_prod(a2.hi, b2.hi);
+    const df s1 = two_sum(p1.hi, p2.hi);
+    const df s2 = two_sum(s1.hi, c.hi);
+    float e = __fadd_rn(__fadd_rn(p1.lo, p2.lo), __fadd_rn(s1.lo, s2.lo));
+    e = __fadd_rn(e, c.lo);
+    e = __fmaf_rn(a1.hi, b1.lo, e);
+    e = __fmaf_rn(a1.lo, b1.hi, e);
+    e = __fmaf_rn(a2.hi, b2.lo, e);
+    e = __fmaf_rn(a2.lo, b2.hi, e);
+    return fast_two_sum(s2.hi, e);
+}
+
 template <bool UNIT>
 __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const FmmParams* Pm, const int* slot,
                                                                 const BoxInfo* info, const float4* coeff,
@@ -1068,11 +1087,11 @@ __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const
             b3y = n3y;
             b2x = n2x;
             b2y = n2y;
-            const df m1x = df_add(df_sub(df_mul(b1x, tx), df_mul(b1y, ty)), b0x);
-            const df m1y = df_add(df_add(df_mul(b1x, ty), df_mul(b1y, tx)), b0y);
+            const df m1x = df_dot2_add(b1x, tx, df_neg(b1y), ty, b0x);
+            const df m1y = df_dot2_add(b1x, ty, b1y, tx, b0y);
             const float4 Lk = L[kk];
-            const df m0x = df_add(df_sub(df_mul(b0x, tx), df_mul(b0y, ty)), df{Lk.x, Lk.y});
-            const df m0y = df_add(df_add(df_mul(b0x, ty), df_mul(b0y, tx)), df{Lk.z, Lk.w});
+            const df m0x = df_dot2_add(b0x, tx, df_neg(b0y), ty, df{Lk.x, Lk.y});
+            const df m0y = df_dot2_add(b0x, ty, b0y, tx, df{Lk.z, Lk.w});
             b1x = m1x;
             b1y = m1y;
             b0x = m0x;
