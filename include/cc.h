@@ -20,8 +20,16 @@
  *   - Calls taking a stream enqueue work on it and return without waiting; results are
  *     valid once the stream has reached that point.  A NULL stream is the legacy default
  *     stream.  cc_stream_t is binary-compatible with cudaStream_t.
- *   - The library allocates device memory only in cc_field_create (a few arrays of N
- *     entries, freed by cc_field_destroy); every other call works in caller memory.
+ *   - Device memory the library allocates itself: one block per field in cc_field_create
+ *     (its star layouts, report and far-field tables: O(N) plus a cell grid) from a
+ *     library-owned stream-ordered pool, returned to the pool by cc_field_destroy (the pool
+ *     keeps freed blocks for reuse), and the fixed static scratch of
+ *     cc_distance_map_static.  cc_field_create and cc_batch_create also create CUDA events.
+ *     Everything of size O(m N) or O(W H) (rows, tracer state, polish tables, batch tables,
+ *     map scratch) is caller memory: the workspaces whose sizes the *_workspace_bytes calls
+ *     return.
+ *   - No kernel spins on a flag or a lock, so no call waits on the device for anything but
+ *     its own work to finish.
  */
 #ifndef CC_H_
 #define CC_H_
@@ -42,14 +50,15 @@ typedef enum cc_status {
     CC_ENOMEM = 2,       /* device allocation failed (cc_field_create) or workspace too small */
     CC_ENOCONV = 3,      /* reported by cc_field_report: some roots did not converge */
     CC_EDEGENERATE = 4,  /* |1 - kappa_s - gamma| < 1e-12: a root runs to infinity at phi = 0 */
-    CC_ECUDA = 5,        /* a CUDA runtime call failed (message has the CUDA error string) */
-    CC_ETIMEOUT = 6      /* a device-side bounded wait gave up (status written, no hang) */
+    CC_ECUDA = 5         /* a CUDA runtime call failed (message has the CUDA error string) */
 } cc_status;
 
 /* Arithmetic of the root tracer (Sec. 3.2 iteration, Sec. 4.4 runtime). */
 typedef enum cc_precision {
-    /* Aberth-Ehrlich in FP32 (compensated, cascaded star sums), then a certified
-     * high-precision Newton polish on F fused with the caustic mapping. */
+    /* Aberth-Ehrlich in FP32 (plain FP32 star and root sums: the FP32 grid of positions,
+     * not the summation, sets the tracer's resolution), then a Newton polish on F with
+     * double-float or FP64 star sums (hp_arith), fused with the caustic mapping, that
+     * certifies every point to tol_cert (1e-10). */
     CC_MIXED = 0,
     /* Aberth-Ehrlich entirely in FP64 with the |dz| < tol_abs stop rule, as in the
      * paper's double-precision code; caustics by a separate FP64 lens-map pass. */
@@ -126,7 +135,6 @@ typedef struct cc_report {
     int64_t uncertified;       /* points whose final error estimate exceeds tol_cert */
     int64_t seam_ambiguous;    /* sub-range joins that were not a clean 1:1 match */
     int32_t max_iter_row;      /* largest per-root iteration count in any row */
-    int32_t timeout;           /* nonzero if a bounded device wait gave up */
     double max_err_est;        /* largest error estimate of a certified point (theta_*) */
     /* Device time of each stage of the last solve (CUDA events on the caller's stream):
      * tracing (Aberth), joining sub-ranges, polish + caustics (mixed form) or
@@ -168,10 +176,16 @@ int cc_critical_curves_workspace_bytes(const cc_field* field, int64_t m, size_t*
 
 /* Critical curves on the phi grid phi_j = 2 pi j / m, j = 0..m (Sec. 3.1, chain matrix of
  * Sec. 4.3; m even, >= 2).  Roots are found by simultaneous Aberth-Ehrlich iteration
- * (Sec. 3.2) from the z_i +- 1 guesses at the centre of each phi sub-range, then grown
- * row by row toward both ends of the sub-range, each row warm-started from its
- * neighbour (Secs. 3.2, 4.3).  Sub-ranges are joined so that column k of every row
- * follows one chain.
+ * (Sec. 3.2) at the centre row of each phi sub-range, then grown row by row toward both
+ * ends of the sub-range, each row warm-started from its neighbour (Secs. 3.2, 4.3).
+ * Sub-ranges are joined so that column k of every row follows one chain.
+ * Initial guesses at a centre row (the paper uses z_i +- 1): roots 2i and 2i+1 start at the
+ * two critical points of star i alone in the field of the others, z_i +- sqrt(-m_i / c_i)
+ * with c_i = gamma - (1 - kappa_s) e^{-i phi} + sum_{j != i} m_j / (z_i - z_j)^2 (the sum
+ * direct over a star tile, or through the FP32 far-field tables), scaled by
+ * 1 + (i mod 64) 2^-12 so that coincident stars keep distinct guesses; z_i +- (1 + 1i/64)
+ * for a rectangular field, a star outside the far-field grid, a field too large for one
+ * star tile without that grid, or c_i ~ 0.  Guesses do not change the roots found.
  *   z_out:     (m+1) x n_r complex128, row j holds the roots at phi_j (device).
  *   w_out:     optional (NULL to skip), same layout: the caustic point w(z) of each root
  *              (Sec. 5.1), computed in the same pass as the polish.
@@ -186,8 +200,7 @@ int cc_critical_curves(cc_field* field, int64_t m, double* z_out, double* w_out,
                        cc_stream_t stream);
 
 /* Wait for the field's last cc_critical_curves and copy its statistics.  Returns CC_OK,
- * CC_ENOCONV if any root-row hit the iteration cap or any point is uncertified, or
- * CC_ETIMEOUT if a device-side wait gave up. */
+ * or CC_ENOCONV if any root-row hit the iteration cap or any point is uncertified. */
 int cc_field_report(cc_field* field, cc_report* out);
 
 /* Caustic points (Sec. 3.1 lens equation, Sec. 5.1): w_out[p] = w(z[p]) for count points.
@@ -268,7 +281,7 @@ int cc_batch_bind(cc_batch* batch, double* const* z_out, double* const* w_out, v
 int cc_batch_launch(cc_batch* batch, int32_t use_graph, cc_stream_t stream);
 
 /* Wait for the last launch; per_field (count entries) and total may be NULL.  Stage times
- * are in total.  Returns CC_OK, CC_ENOCONV or CC_ETIMEOUT like cc_field_report. */
+ * are in total.  Returns CC_OK or CC_ENOCONV like cc_field_report. */
 int cc_batch_report(cc_batch* batch, cc_report* per_field, cc_report* total);
 
 /* Work items, persistent grid size and block size of the batch. */
@@ -288,13 +301,15 @@ int cc_batch_destroy(cc_batch* batch);
  * CC_DISTANCE_MAP_STATIC_MAX_PIXELS * 8 + 512 bytes in this library's device memory,
  * held by every GPU that loads the library until the process exits.
  *   ncc, d_out, W, H, pixel: as for cc_distance_map (caller-allocated device buffers).
- * The first call on each device looks up the array's device address (with that device
- * current); make that first call before any stream capture on the device.  All calls
- * share the one array and it keeps the last call's contents (nothing needs clearing:
- * every scratch entry is written before it is read); calls that overlap on the GPU race
- * on it, so order them on one stream or serialise them.
+ * The array is used on the current device, so stream must belong to that device.  The
+ * first call in each CUDA context looks up the array's device address (with that device
+ * current) and keeps it for that context; make that first call before any stream capture
+ * on the device.  After a reset of the device's primary context the next call looks the
+ * address up again.  All calls share the one array and it keeps the last call's contents
+ * (nothing needs clearing: every scratch entry is written before it is read); calls that
+ * overlap on the GPU race on it, so order them on one stream or serialise them.
  * Errors: CC_EINVAL (W * H > CC_DISTANCE_MAP_STATIC_MAX_PIXELS, NULL, bad size or
- *         pixel), CC_ECUDA. */
+ *         pixel, a stream of another device), CC_ECUDA. */
 int cc_distance_map_static(const int32_t* ncc, int32_t W, int32_t H, double pixel, double* d_out,
                            cc_stream_t stream);
 

@@ -19,13 +19,12 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libccgpu.so")
 
-CC_OK, CC_EINVAL, CC_ENOMEM, CC_ENOCONV, CC_EDEGENERATE, CC_ECUDA, CC_ETIMEOUT = range(7)
+CC_OK, CC_EINVAL, CC_ENOMEM, CC_ENOCONV, CC_EDEGENERATE, CC_ECUDA = range(6)
 CC_MIXED, CC_FP64 = 0, 1
 CC_HP_DFLOAT, CC_HP_FP64 = 0, 1
 CC_FIELD_DISC, CC_FIELD_RECT = 0, 1
 CC_RECT_MAX_T = 129
-_NAMES = {0: "CC_OK", 1: "CC_EINVAL", 2: "CC_ENOMEM", 3: "CC_ENOCONV", 4: "CC_EDEGENERATE", 5: "CC_ECUDA",
-          6: "CC_ETIMEOUT"}
+_NAMES = {0: "CC_OK", 1: "CC_EINVAL", 2: "CC_ENOMEM", 3: "CC_ENOCONV", 4: "CC_EDEGENERATE", 5: "CC_ECUDA"}
 
 
 class CCError(RuntimeError):
@@ -50,7 +49,7 @@ class Report(ctypes.Structure):
                 ("root_iterations", ctypes.c_int64), ("cold_root_iterations", ctypes.c_int64),
                 ("unconverged", ctypes.c_int64), ("polish_passes", ctypes.c_int64),
                 ("uncertified", ctypes.c_int64), ("seam_ambiguous", ctypes.c_int64),
-                ("max_iter_row", ctypes.c_int32), ("timeout", ctypes.c_int32), ("max_err_est", ctypes.c_double),
+                ("max_iter_row", ctypes.c_int32), ("max_err_est", ctypes.c_double),
                 ("trace_ms", ctypes.c_float), ("join_ms", ctypes.c_float), ("polish_ms", ctypes.c_float),
                 ("rescued_points", ctypes.c_int64), ("jumped", ctypes.c_int64),
                 ("star_terms", ctypes.c_int64), ("far_evals", ctypes.c_int64),
@@ -225,9 +224,9 @@ def cc_critical_curves(field: Field, m: int, z_out, w_out=None, iters_out=None, 
 
 
 def cc_field_report(field: Field):
-    """Returns (status, report dict); status is CC_OK or CC_ENOCONV / CC_ETIMEOUT."""
+    """Returns (status, report dict); status is CC_OK or CC_ENOCONV."""
     r = Report()
-    st = _check(_lib.cc_field_report(field.handle, ctypes.byref(r)), allow=(CC_ENOCONV, CC_ETIMEOUT))
+    st = _check(_lib.cc_field_report(field.handle, ctypes.byref(r)), allow=(CC_ENOCONV,))
     return st, r.as_dict()
 
 
@@ -346,7 +345,7 @@ def cc_batch_report(batch: Batch):
     n = len(batch.fields)
     per = (Report * n)()
     tot = Report()
-    st = _check(_lib.cc_batch_report(batch.handle, per, ctypes.byref(tot)), allow=(CC_ENOCONV, CC_ETIMEOUT))
+    st = _check(_lib.cc_batch_report(batch.handle, per, ctypes.byref(tot)), allow=(CC_ENOCONV,))
     return st, [p.as_dict() for p in per], tot.as_dict()
 
 

@@ -448,7 +448,6 @@ int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
         q.uncertified = (int64_t)r[f].uncertified;
         q.seam_ambiguous = (int64_t)r[f].seam_ambiguous;
         q.max_iter_row = r[f].max_iter_row;
-        q.timeout = r[f].timeout;
         q.max_err_est = r[f].max_err_est;
         q.rescued_points = (int64_t)r[f].rescued_points;
         q.jumped = (int64_t)r[f].jumped;
@@ -467,7 +466,6 @@ int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
         tot.uncertified += q.uncertified;
         tot.seam_ambiguous += q.seam_ambiguous;
         tot.max_iter_row = std::max(tot.max_iter_row, q.max_iter_row);
-        tot.timeout |= q.timeout;
         tot.max_err_est = std::max(tot.max_err_est, q.max_err_est);
         tot.rescued_points += q.rescued_points;
         tot.jumped += q.jumped;
@@ -481,7 +479,6 @@ int cc_batch_report(cc_batch* b, cc_report* per_field, cc_report* total) {
     tot.join_ms = t12;
     tot.polish_ms = t23;
     if (total) *total = tot;
-    if (tot.timeout) return berr(CC_ETIMEOUT, "a device-side wait gave up");
     if (bad) return berr(CC_ENOCONV, "some fields have unconverged or uncertified points");
     return CC_OK;
 }

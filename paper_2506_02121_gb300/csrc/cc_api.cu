@@ -614,7 +614,6 @@ int cc_field_report(cc_field* f, cc_report* out) {
     out->uncertified = (int64_t)r.uncertified;
     out->seam_ambiguous = (int64_t)r.seam_ambiguous;
     out->max_iter_row = r.max_iter_row;
-    out->timeout = r.timeout;
     out->max_err_est = r.max_err_est;
     out->rescued_points = (int64_t)r.rescued_points;
     out->jumped = (int64_t)r.jumped;
@@ -625,7 +624,6 @@ int cc_field_report(cc_field* f, cc_report* out) {
     CC_CUDA(cudaEventElapsedTime(&out->trace_ms, f->ev[0], f->ev[1]), "stage time");
     CC_CUDA(cudaEventElapsedTime(&out->join_ms, f->ev[1], f->ev[2]), "stage time");
     CC_CUDA(cudaEventElapsedTime(&out->polish_ms, f->ev[2], f->ev[3]), "stage time");
-    if (r.timeout) return fail(CC_ETIMEOUT, "a device-side wait gave up");
     if (r.unconverged || r.uncertified)
         return fail(CC_ENOCONV, "%lld root-rows hit the iteration cap, %lld points uncertified",
                     (long long)r.unconverged, (long long)r.uncertified);

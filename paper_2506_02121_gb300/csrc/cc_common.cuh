@@ -162,7 +162,6 @@ struct DevReport {
     unsigned long long root_terms;      // tracer: root-root terms summed
     unsigned long long split_redone_rows;  // tracer: rows solved again with the exact root sum
     int max_iter_row;
-    int timeout;
     double max_err_est;          // stored as the bit pattern of a non-negative double
 };
 

@@ -37,6 +37,22 @@ def test_static_scratch_matches_workspace_version_on_consecutive_calls():
         assert torch.equal(out, ref)  # bit-exact, as every distance-map comparison here
 
 
+def test_static_scratch_call_allocates_no_device_memory():
+    H, W = 777, 1301
+    ncc = _ncc_map(13, H, W)
+    out = torch.empty((H, W), dtype=torch.float64, device="cuda")
+    pixel = 20.0 / 1024
+    cc.cc_distance_map_static(ncc, pixel, out)  # warm-up: per-context set-up, module load
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    cc.cc_distance_map_static(ncc, pixel, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert torch.cuda.memory_reserved() == reserved0
+    assert free1 == free0
+
+
 def test_static_scratch_rejects_maps_beyond_its_limit():
     H, W = 1025, 1024
     ncc = torch.zeros((H, W), dtype=torch.int32, device="cuda")
