@@ -76,6 +76,10 @@ def _load():
         lib.orc_winding_at.restype = i64
         lib.orc_crossing_map.argtypes = [_DP, i64, i64, dbl, dbl, dbl, dbl, i32, i32, _I32P]
         lib.orc_crossing_map.restype = None
+        lib.orc_crossing_rows.argtypes = [_DP, i64, i64, dbl, dbl, dbl, dbl, i32, i32, i32, i32, _I32P]
+        lib.orc_crossing_rows.restype = None
+        lib.orc_newton_check.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, i64, i64, i64, i64, _DP, _DP, _DP]
+        lib.orc_newton_check.restype = None
         lib.orc_feature_mask.argtypes = [_I32P, i32, i32, _U8P]
         lib.orc_feature_mask.restype = None
         lib.orc_distance_map_brute.argtypes = [_I32P, i32, i32, dbl, _DP]
@@ -295,6 +299,36 @@ def crossing_map(w, x0, x1, y0, y1, W, H):
     _load().orc_crossing_map(ww.view(np.float64).ctypes.data_as(_DP), rows, nr, x0, x1, y0, y1,
                              int(W), int(H), out.ctypes.data_as(_I32P))
     return out
+
+
+def crossing_rows(w, x0, x1, y0, y1, W, H, r0, r1):
+    """Pixel rows [r0, r1) of crossing_map(w, x0, x1, y0, y1, W, H): the same pixel centres
+    and decisions, int32 [r1 - r0, W]."""
+    if not (0 <= r0 <= r1 <= H):
+        raise ValueError("need 0 <= r0 <= r1 <= H")
+    ww = np.ascontiguousarray(w, dtype=np.complex128)
+    rows, nr = ww.shape
+    out = np.zeros((r1 - r0, W), dtype=np.int32)
+    _load().orc_crossing_rows(ww.view(np.float64).ctypes.data_as(_DP), rows, nr, x0, x1, y0, y1,
+                              int(W), int(H), int(r0), int(r1), out.ctypes.data_as(_I32P))
+    return out
+
+
+def newton_check(x, y, m, kappa_s, gamma, msteps, z, row0=0):
+    """Per point of the rows x n_r array z (row r at phi_j, j = row0 + r): the FP64 Newton
+    correction |F/F'| (Sec. 3.2; to first order the distance to the zero of F) and the lens
+    map w (Sec. 3.1).  Disc field.  Returns (step [rows, n_r] float64, w like z)."""
+    x, y, m = _stars(x, y, m)
+    zz = np.ascontiguousarray(z, dtype=np.complex128)
+    if zz.ndim != 2:
+        raise ValueError("z must be rows x n_r")
+    rows, nr = zz.shape
+    step = np.zeros((rows, nr), dtype=np.float64)
+    w = np.zeros_like(zz)
+    _load().orc_newton_check(_d(x), _d(y), _d(m), len(x), float(kappa_s), float(gamma), int(msteps), int(row0),
+                             rows, nr, zz.view(np.float64).ctypes.data_as(_DP), _d(step),
+                             w.view(np.float64).ctypes.data_as(_DP))
+    return step, w
 
 
 def feature_mask(ncc):

@@ -486,6 +486,42 @@ void orc_rect_map_caustics(const double* x, const double* y, const double* m, in
     map_caustics(&L, z, count, w_out);
 }
 
+/* Newton correction and caustic point of given points of a disc field (Sec. 3.1 for F and
+ * w, Sec. 3.2 for the Newton correction inside Aberth's step).  Point p = r * nr + k lies on
+ * row j = row0 + r, phi_j = 2 pi j / m (orc_phi).  step[p] = |F(z_p, phi_j)| / |F'(z_p)|,
+ * the length of the Newton correction: for a simple zero of F it is the distance from z_p
+ * to that zero up to a second-order term.  w_out[p] = w(z_p), the lens map.
+ * One pass over the stars per point: with u = 1/(z - z_i) = conj(z - z_i)/|z - z_i|^2,
+ *   F  = gamma + sum m_i u^2 - (1 - kappa_s) e^{-i phi},   F' = -2 sum m_i u^3,
+ *   w  = (1 - kappa_s) z + gamma conj(z) - sum m_i conj(u). */
+void orc_newton_check(const double* x, const double* y, const double* m, int64_t n, double kappa_s,
+                      double gamma, int64_t msteps, int64_t row0, int64_t rows, int64_t nr, const double* z,
+                      double* step, double* w_out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < rows * nr; p++) {
+        const int64_t j = row0 + p / nr;
+        const double phi = orc_phi(j, msteps);
+        const cplx e_mphi = cos(phi) - I * sin(phi);
+        const cplx zz = z[2 * p] + I * z[2 * p + 1];
+        cplx sF = 0.0, sdF = 0.0, sW = 0.0;
+        for (int64_t i = 0; i < n; i++) {
+            const double dx = creal(zz) - x[i], dy = cimag(zz) - y[i];
+            const double r2 = dx * dx + dy * dy;
+            const cplx u = dx / r2 - I * (dy / r2);
+            const cplx u2 = u * u;
+            sF += m[i] * u2;
+            sdF += m[i] * (u2 * u);
+            sW += m[i] * conj(u);
+        }
+        const cplx F = gamma + sF - (1.0 - kappa_s) * e_mphi;
+        const cplx dF = -2.0 * sdF;
+        const cplx w = (1.0 - kappa_s) * zz + gamma * conj(zz) - sW;
+        step[p] = cabs(F) / cabs(dF);
+        w_out[2 * p] = creal(w);
+        w_out[2 * p + 1] = cimag(w);
+    }
+}
+
 /* Smallest pairwise distance among the n_r roots of one row (distinctness check). */
 double orc_min_separation(const double* z, int64_t nr) {
     double best = INFINITY;
@@ -600,21 +636,19 @@ int64_t orc_winding_at(const double* w, int64_t rows, int64_t nr, double px, dou
     return wn;
 }
 
-/* Full N_cc map (row 0 = y0 side, column 0 = x0 side).  Same decisions as evaluating
- * orc_winding_at at every pixel centre: a segment can only change the count of pixel
- * rows whose centre satisfies min(a.y,b.y) <= y < max(a.y,b.y), so other rows are
- * skipped for that segment. */
-void orc_crossing_map(const double* w, int64_t rows, int64_t nr, double x0, double x1,
-                      double y0, double y1, int32_t W, int32_t H, int32_t* ncc) {
-    int64_t npx = (int64_t)W * H;
+/* Pixel rows [r0, r1) of the N_cc map of a W x H grid (row 0 = y0 side, column 0 = x0
+ * side) into ncc[(r - r0) * W + i].  Same decisions as evaluating orc_winding_at at every
+ * pixel centre: a segment can only change the count of pixel rows whose centre satisfies
+ * min(a.y,b.y) <= y < max(a.y,b.y), so other rows are skipped for that segment. */
+static void crossing_rows(const double* w, int64_t rows, int64_t nr, double x0, double x1, double y0,
+                          double y1, int32_t W, int32_t H, int32_t r0, int32_t r1, int32_t* ncc) {
+    int64_t npx = (int64_t)W * (r1 - r0);
     int64_t* wn = (int64_t*)calloc((size_t)npx, sizeof(int64_t));
-    double* pyc = (double*)malloc(sizeof(double) * (size_t)H);
     double* pxc = (double*)malloc(sizeof(double) * (size_t)W);
-    for (int32_t r = 0; r < H; r++) pyc[r] = orc_pixel_center(y0, y1, H, r);
     for (int32_t i = 0; i < W; i++) pxc[i] = orc_pixel_center(x0, x1, W, i);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int32_t r = 0; r < H; r++) {
-        double py = pyc[r];
+    for (int32_t r = r0; r < r1; r++) {
+        double py = orc_pixel_center(y0, y1, H, r);
         for (int64_t k = 0; k < nr; k++)
             for (int64_t j = 0; j + 1 < rows; j++) {
                 const double* a = w + 2 * (j * nr + k);
@@ -623,13 +657,25 @@ void orc_crossing_map(const double* w, int64_t rows, int64_t nr, double x0, doub
                 double hi = a[1] < b[1] ? b[1] : a[1];
                 if (!(lo <= py && py < hi)) continue;
                 for (int32_t i = 0; i < W; i++)
-                    wn[(int64_t)r * W + i] += sunday_edge(a[0], a[1], b[0], b[1], pxc[i], py);
+                    wn[(int64_t)(r - r0) * W + i] += sunday_edge(a[0], a[1], b[0], b[1], pxc[i], py);
             }
     }
     for (int64_t p = 0; p < npx; p++) ncc[p] = (int32_t)(-wn[p]);
     free(wn);
-    free(pyc);
     free(pxc);
+}
+
+/* Full N_cc map (row 0 = y0 side, column 0 = x0 side). */
+void orc_crossing_map(const double* w, int64_t rows, int64_t nr, double x0, double x1,
+                      double y0, double y1, int32_t W, int32_t H, int32_t* ncc) {
+    crossing_rows(w, rows, nr, x0, x1, y0, y1, W, H, 0, H, ncc);
+}
+
+/* Rows [r0, r1) of the N_cc map of the W x H grid (a horizontal slab of orc_crossing_map,
+ * same pixel centres), into an (r1 - r0) x W array. */
+void orc_crossing_rows(const double* w, int64_t rows, int64_t nr, double x0, double x1, double y0,
+                       double y1, int32_t W, int32_t H, int32_t r0, int32_t r1, int32_t* ncc) {
+    crossing_rows(w, rows, nr, x0, x1, y0, y1, W, H, r0, r1, ncc);
 }
 
 /* ------------------------------------------------------------------------------------

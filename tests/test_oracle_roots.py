@@ -181,3 +181,43 @@ def test_F_equals_lens_map_wirtinger_form():
         # dF/dz by central differences of F itself
         dref = (oracle.F(f.x, f.y, f.m, f.kappa_s, f.gamma, ph, p + h) - oracle.F(f.x, f.y, f.m, f.kappa_s, f.gamma, ph, p - h)) / (2 * h)
         assert abs(oracle.dF(f.x, f.y, f.m, p) - dref) < 1e-5 * (1 + abs(dref))
+
+
+@pytest.mark.parametrize("kappa_s,gamma", [(0.0, 0.2), (0.3, 0.5), (0.0, 1.3)])
+def test_newton_check_at_and_near_chang_refsdal_roots(kappa_s, gamma):
+    """At the closed-form roots the Newton correction vanishes and w is the closed-form
+    caustic; a root moved by delta gets a correction of length |delta| (to first order), so a
+    wrong factor in F' or a wrong phase row would show."""
+    x, y, m = np.array([0.7]), np.array([-0.4]), np.array([0.6])
+    msteps, row0 = 64, 5
+    rows = [lm.chang_refsdal_roots(complex(x[0], y[0]), m[0], kappa_s, gamma, oracle.phi(row0 + r, msteps))
+            for r in range(4)]
+    z = np.array(rows)
+    step, w = oracle.newton_check(x, y, m, kappa_s, gamma, msteps, z, row0=row0)
+    assert step.max() < 1e-13
+    for r in range(4):
+        wc = lm.chang_refsdal_caustic(complex(x[0], y[0]), m[0], kappa_s, gamma, oracle.phi(row0 + r, msteps))
+        assert np.abs(w[r] - wc).max() < 1e-12
+    delta = 1e-6 * np.exp(1j * np.array([[0.3, 2.0], [4.1, 1.1], [5.5, 0.2], [3.3, 2.8]]))
+    step2, _ = oracle.newton_check(x, y, m, kappa_s, gamma, msteps, z + delta, row0=row0)
+    assert np.abs(step2 / np.abs(delta) - 1).max() < 1e-4
+    # the same points attributed to other rows are not roots there
+    step3, _ = oracle.newton_check(x, y, m, kappa_s, gamma, msteps, z, row0=row0 + 1)
+    assert step3.min() > 1e-4
+
+
+def test_newton_check_matches_oracle_sums_on_a_field():
+    """On a random 25-star field the per-point values equal the oracle's own F, F' and lens
+    map (written separately, with complex division) at every point and phase row."""
+    x, y, m = _random_field(25, 31, mass="var")
+    kappa_s, gamma, msteps, row0 = 0.15, 0.45, 40, 7
+    u = synth.uniform(32, 2 * 3 * 6)
+    z = ((u[0::2] - 0.5) * 8 + 1j * (u[1::2] - 0.5) * 8).reshape(3, 6)
+    step, w = oracle.newton_check(x, y, m, kappa_s, gamma, msteps, z, row0=row0)
+    wo = oracle.map_caustics(x, y, m, kappa_s, gamma, z)
+    assert np.abs(w - wo).max() < 1e-12 * (1 + np.abs(wo).max())
+    for r in range(3):
+        for k in range(6):
+            F = oracle.F(x, y, m, kappa_s, gamma, oracle.phi(row0 + r, msteps), z[r, k])
+            dF = oracle.dF(x, y, m, z[r, k])
+            assert abs(step[r, k] - abs(F) / abs(dF)) < 1e-12 * step[r, k]
