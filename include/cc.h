@@ -111,10 +111,11 @@ typedef struct cc_options {
     double rect_c1, rect_c2; /* CC_FIELD_RECT: corner c = c1 + i c2 of the field (half-width,
                               half-height, both > 0) */
     double rect_eps, rect_s; /* CC_FIELD_RECT, rect_t == 0: error target (1e-9) and ratio s > 1 (2) */
-    int32_t row_ctas;      /* CTAs (one thread-block cluster) that share each phi sub-range of the FP32
-                              tracer, each updating a slice of the roots: 0 = automatic (8 when
-                              n_r >= 4096 and, with root_refresh >= 2, m < 8 x the SM count;
-                              else 1), 1 = one CTA per sub-range, 2..16 = that many */
+    int32_t row_ctas;      /* CTAs (one thread-block cluster) that share each phi sub-range of the
+                              tracer (either precision), each updating a slice of the roots:
+                              0 = automatic (1 when n_r < 4096, or when m >= 8 x the SM count and
+                              the form is CC_FP64 or root_refresh >= 2; else 8), 1 = one CTA per
+                              sub-range, 2..16 = that many */
     int32_t root_refresh;  /* Aberth root sum of the FP32 tracer's warm rows (one CTA per sub-range):
                               0 or 1 = exact in every sweep (Sec. 3.2); K >= 2 = exact every K-th row
                               of a chain, where each root's sum is split into the roots of the 3 x 3

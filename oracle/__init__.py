@@ -76,7 +76,7 @@ def _load():
         lib.orc_winding_at.restype = i64
         lib.orc_crossing_map.argtypes = [_DP, i64, i64, dbl, dbl, dbl, dbl, i32, i32, _I32P]
         lib.orc_crossing_map.restype = None
-        lib.orc_crossing_rows.argtypes = [_DP, i64, i64, dbl, dbl, dbl, dbl, i32, i32, i32, i32, _I32P]
+        lib.orc_crossing_rows.argtypes = [_DP, i64, i64, dbl, dbl, dbl, dbl, i32, i32, _I32P, i32, _I32P]
         lib.orc_crossing_rows.restype = None
         lib.orc_newton_check.argtypes = [_DP, _DP, _DP, i64, dbl, dbl, i64, i64, i64, i64, _DP, _DP, _DP]
         lib.orc_newton_check.restype = None
@@ -109,6 +109,8 @@ def _load():
         lib.orc_rect_map_caustics.restype = None
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_num_threads.restype = None
         _lib = lib
         return lib
 
@@ -167,6 +169,11 @@ def rect_dalpha_dzb(kappa_star, c1, c2, t, z):
 def num_threads() -> int:
     """OpenMP threads the oracle uses (1 when built without OpenMP)."""
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (for timing runs)."""
+    _load().orc_set_num_threads(int(n))
 
 
 def phi(j: int, msteps: int) -> float:
@@ -301,16 +308,17 @@ def crossing_map(w, x0, x1, y0, y1, W, H):
     return out
 
 
-def crossing_rows(w, x0, x1, y0, y1, W, H, r0, r1):
-    """Pixel rows [r0, r1) of crossing_map(w, x0, x1, y0, y1, W, H): the same pixel centres
-    and decisions, int32 [r1 - r0, W]."""
-    if not (0 <= r0 <= r1 <= H):
-        raise ValueError("need 0 <= r0 <= r1 <= H")
+def crossing_rows(w, x0, x1, y0, y1, W, H, rows):
+    """The listed pixel rows of crossing_map(w, x0, x1, y0, y1, W, H): the same pixel
+    centres and decisions, int32 [len(rows), W]."""
+    rl = np.ascontiguousarray(rows, dtype=np.int32)
+    if rl.ndim != 1 or (rl.size and (rl.min() < 0 or rl.max() >= H)):
+        raise ValueError("rows must be indices in [0, H)")
     ww = np.ascontiguousarray(w, dtype=np.complex128)
-    rows, nr = ww.shape
-    out = np.zeros((r1 - r0, W), dtype=np.int32)
-    _load().orc_crossing_rows(ww.view(np.float64).ctypes.data_as(_DP), rows, nr, x0, x1, y0, y1,
-                              int(W), int(H), int(r0), int(r1), out.ctypes.data_as(_I32P))
+    nrows, nr = ww.shape
+    out = np.zeros((rl.size, W), dtype=np.int32)
+    _load().orc_crossing_rows(ww.view(np.float64).ctypes.data_as(_DP), nrows, nr, x0, x1, y0, y1,
+                              int(W), int(H), rl.ctypes.data_as(_I32P), int(rl.size), out.ctypes.data_as(_I32P))
     return out
 
 

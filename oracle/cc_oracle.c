@@ -636,19 +636,20 @@ int64_t orc_winding_at(const double* w, int64_t rows, int64_t nr, double px, dou
     return wn;
 }
 
-/* Pixel rows [r0, r1) of the N_cc map of a W x H grid (row 0 = y0 side, column 0 = x0
- * side) into ncc[(r - r0) * W + i].  Same decisions as evaluating orc_winding_at at every
- * pixel centre: a segment can only change the count of pixel rows whose centre satisfies
- * min(a.y,b.y) <= y < max(a.y,b.y), so other rows are skipped for that segment. */
+/* Pixel rows rlist[0..count) of the N_cc map of a W x H grid (row 0 = y0 side, column 0 =
+ * x0 side) into ncc[t * W + i] for row rlist[t].  Same decisions as evaluating
+ * orc_winding_at at every pixel centre: a segment can only change the count of pixel rows
+ * whose centre satisfies min(a.y,b.y) <= y < max(a.y,b.y), so other rows are skipped for
+ * that segment. */
 static void crossing_rows(const double* w, int64_t rows, int64_t nr, double x0, double x1, double y0,
-                          double y1, int32_t W, int32_t H, int32_t r0, int32_t r1, int32_t* ncc) {
-    int64_t npx = (int64_t)W * (r1 - r0);
+                          double y1, int32_t W, int32_t H, const int32_t* rlist, int32_t count, int32_t* ncc) {
+    int64_t npx = (int64_t)W * count;
     int64_t* wn = (int64_t*)calloc((size_t)npx, sizeof(int64_t));
     double* pxc = (double*)malloc(sizeof(double) * (size_t)W);
     for (int32_t i = 0; i < W; i++) pxc[i] = orc_pixel_center(x0, x1, W, i);
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int32_t r = r0; r < r1; r++) {
-        double py = orc_pixel_center(y0, y1, H, r);
+    for (int32_t t = 0; t < count; t++) {
+        double py = orc_pixel_center(y0, y1, H, rlist[t]);
         for (int64_t k = 0; k < nr; k++)
             for (int64_t j = 0; j + 1 < rows; j++) {
                 const double* a = w + 2 * (j * nr + k);
@@ -657,7 +658,7 @@ static void crossing_rows(const double* w, int64_t rows, int64_t nr, double x0, 
                 double hi = a[1] < b[1] ? b[1] : a[1];
                 if (!(lo <= py && py < hi)) continue;
                 for (int32_t i = 0; i < W; i++)
-                    wn[(int64_t)(r - r0) * W + i] += sunday_edge(a[0], a[1], b[0], b[1], pxc[i], py);
+                    wn[(int64_t)t * W + i] += sunday_edge(a[0], a[1], b[0], b[1], pxc[i], py);
             }
     }
     for (int64_t p = 0; p < npx; p++) ncc[p] = (int32_t)(-wn[p]);
@@ -668,14 +669,17 @@ static void crossing_rows(const double* w, int64_t rows, int64_t nr, double x0, 
 /* Full N_cc map (row 0 = y0 side, column 0 = x0 side). */
 void orc_crossing_map(const double* w, int64_t rows, int64_t nr, double x0, double x1,
                       double y0, double y1, int32_t W, int32_t H, int32_t* ncc) {
-    crossing_rows(w, rows, nr, x0, x1, y0, y1, W, H, 0, H, ncc);
+    int32_t* rlist = (int32_t*)malloc(sizeof(int32_t) * (size_t)H);
+    for (int32_t r = 0; r < H; r++) rlist[r] = r;
+    crossing_rows(w, rows, nr, x0, x1, y0, y1, W, H, rlist, H, ncc);
+    free(rlist);
 }
 
-/* Rows [r0, r1) of the N_cc map of the W x H grid (a horizontal slab of orc_crossing_map,
- * same pixel centres), into an (r1 - r0) x W array. */
+/* The listed pixel rows of the N_cc map of the W x H grid (rows of orc_crossing_map, same
+ * pixel centres), into a count x W array. */
 void orc_crossing_rows(const double* w, int64_t rows, int64_t nr, double x0, double x1, double y0,
-                       double y1, int32_t W, int32_t H, int32_t r0, int32_t r1, int32_t* ncc) {
-    crossing_rows(w, rows, nr, x0, x1, y0, y1, W, H, r0, r1, ncc);
+                       double y1, int32_t W, int32_t H, const int32_t* rlist, int32_t count, int32_t* ncc) {
+    crossing_rows(w, rows, nr, x0, x1, y0, y1, W, H, rlist, count, ncc);
 }
 
 /* ------------------------------------------------------------------------------------
@@ -868,6 +872,16 @@ void orc_moving_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pi
             }
             d_out[(int64_t)r * W + i] = d;
         }
+}
+
+/* Threads of the oracle's parallel loops from now on (timing runs; n >= 1). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
 }
 
 int orc_num_threads(void) {

@@ -16,6 +16,9 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 ROOT = os.path.dirname(PKG)
 LIB = os.path.join(PKG, "libccgpu.so")
+# FMA-rate probes for the roofline denominators (a measurement tool, not part of the method)
+PROBE_LIB = os.path.join(PKG, "libccprobe.so")
+PROBE_SRC = "probe_peaks.cu"
 BUILD_DIR = os.path.join(ROOT, "_build")
 SOURCES = ["cc_api.cu", "aberth.cu", "polish.cu", "raster.cu", "static_scratch.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,13 +39,27 @@ def nvcc() -> str:
 
 
 def _deps_mtime() -> float:
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "cc.h"),
-                                                                 os.path.abspath(__file__)]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f != PROBE_SRC] + [
+        os.path.join(ROOT, "include", "cc.h"), os.path.abspath(__file__)]
     return max(os.path.getmtime(f) for f in files if os.path.isfile(f))
+
+
+def build_probe(force: bool = False) -> str:
+    src = os.path.join(CSRC, PROBE_SRC)
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(src):
+        return PROBE_LIB
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc(), *ARCH, *FLAGS, "-shared", "-cudart", "shared", src, "-o", tmp],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PROBE_SRC}:\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+        build_probe(force)
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
     cc = nvcc()
@@ -57,8 +74,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        probe = ex.submit(build_probe, force)
         objs = list(ex.map(compile_one, SOURCES))
+        probe.result()
     tmp = LIB + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:

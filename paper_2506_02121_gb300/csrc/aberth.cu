@@ -1385,7 +1385,9 @@ __global__ void __launch_bounds__(512, 1) trace_kernel(TK K) {
 }
 
 // One phi sub-range per thread-block cluster (grid = S clusters of G CTAs): for rows so wide
-// (many roots) that one SM per sub-range would leave most of the GPU idle on a small m.
+// (many roots) that one SM per sub-range would leave most of the GPU idle on a small m.  Both
+// arithmetics: the FP32 tracer and the plain FP64 form.
+template <typename T>
 __global__ void __launch_bounds__(512, 1) trace_wide_kernel(TK K) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_count[2], s_maxit, s_red[8], s_tot[4], s_parity;
@@ -1397,8 +1399,8 @@ __global__ void __launch_bounds__(512, 1) trace_wide_kernel(TK K) {
     const int s = (int)blockIdx.x / G;
     unsigned long long n_terms = 0, n_far = 0, n_root = 0;
     __syncthreads();
-    run_subchain<float, true>(K, s, K.work + (size_t)s * K.work_stride, smem, s_count, &s_maxit, &n_terms, &n_far,
-                              &n_root, s_red, s_tot, &s_parity, rank, G);
+    run_subchain<T, true>(K, s, K.work + (size_t)s * K.work_stride, smem, s_count, &s_maxit, &n_terms, &n_far,
+                          &n_root, s_red, s_tot, &s_parity, rank, G);
     add_work_counters(K.rep, n_terms, n_far, n_root);
     if (threadIdx.x == 0) atomicMax(&K.rep->max_iter_row, s_maxit);
     cluster_sync();  // no CTA leaves while another may still read its shared memory
@@ -1504,18 +1506,26 @@ int tracer_blocks_per_sm(bool fp64, int threads, int64_t n) {
 // every warm row takes a small fraction of the exact sum: N = 20000, m = 2e4 traces in
 // 0.77 s against 9.2 s with clusters).
 int tracer_cluster_size(const cc_options& o, int64_t nr, bool fp64, int64_t m, int sms) {
-    if (fp64) return 1;
     if (o.row_ctas > 0) return o.row_ctas;
     if (nr < WIDE_MIN_NR) return 1;
-    if (o.root_refresh >= 2 && m >= 8 * (int64_t)sms) return 1;
+    // with enough rows one CTA per sub-range wins: the FP32 tracer's root-sum split makes
+    // warm rows cheap, and the FP64 form's rows then already fill every SM
+    if ((fp64 || o.root_refresh >= 2) && m >= 8 * (int64_t)sms) return 1;
     return 8;
 }
 
-int tracer_max_clusters(int G, int threads) {
-    const size_t smem = tracer_smem_bytes(false, (int64_t)CT<float>::TS);
-    cudaError_t e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename T>
+static cudaError_t wide_attributes(int G, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(trace_wide_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && G > 8)
-        e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(trace_wide_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+int tracer_max_clusters(int G, int threads, bool fp64) {
+    const size_t smem =
+        fp64 ? tracer_smem_bytes(true, (int64_t)CT<double>::TS) : tracer_smem_bytes(false, (int64_t)CT<float>::TS);
+    cudaError_t e = fp64 ? wide_attributes<double>(G, smem) : wide_attributes<float>(G, smem);
     int n = 0;
     if (e == cudaSuccess) {
         cudaLaunchConfig_t cfg = {};
@@ -1529,7 +1539,8 @@ int tracer_max_clusters(int G, int threads) {
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaOccupancyMaxActiveClusters(&n, trace_wide_kernel, &cfg);
+        e = fp64 ? cudaOccupancyMaxActiveClusters(&n, trace_wide_kernel<double>, &cfg)
+                 : cudaOccupancyMaxActiveClusters(&n, trace_wide_kernel<float>, &cfg);
     }
     if (e != cudaSuccess) cudaGetLastError();
     return n > 0 ? n : 1;
@@ -1579,10 +1590,8 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
     K.near_cap = (!fp64 && a.cluster <= 1 && a.root_refresh >= 2 && a.f->nr <= NEAR_SMEM_NR) ? (int)a.f->nr : 0;
     const size_t smem = tracer_smem_bytes(fp64, a.f->n, K.near_cap);
     cudaError_t e;
-    if (!fp64 && a.cluster > 1) {
-        e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess && a.cluster > 8)
-            e = cudaFuncSetAttribute(trace_wide_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (a.cluster > 1) {
+        e = fp64 ? wide_attributes<double>(a.cluster, smem) : wide_attributes<float>(a.cluster, smem);
         if (e != cudaSuccess) return e;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(a.S * a.cluster));
@@ -1596,7 +1605,7 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, trace_wide_kernel, K);
+        e = fp64 ? cudaLaunchKernelEx(&cfg, trace_wide_kernel<double>, K) : cudaLaunchKernelEx(&cfg, trace_wide_kernel<float>, K);
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }

@@ -93,7 +93,7 @@ CurveLayout curve_layout(const cc_field* f, int64_t m) {
     if (L.G > 1) {
         // one wave of clusters; a sub-range keeps >= 8 rows
         cc_options o = f->opt;
-        o.subchains = f->opt.subchains > 0 ? f->opt.subchains : std::max(1, tracer_max_clusters(L.G, L.threads));
+        o.subchains = f->opt.subchains > 0 ? f->opt.subchains : std::max(1, tracer_max_clusters(L.G, L.threads, fp64));
         L.S = subchain_count(m, nr, o, 1, 1);
     } else {
         L.S = subchain_count(m, nr, f->opt, sm_count(f->device), tracer_occupancy(f->device, fp64, L.threads, f->dev.n));

@@ -289,7 +289,7 @@ int tracer_blocks_per_sm(bool fp64, int threads, int64_t n);
 int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms, int blocks_per_sm);
 constexpr int WIDE_MIN_NR = 4096;   // automatic cluster tracing from this many roots per row
 int tracer_cluster_size(const cc_options& o, int64_t nr, bool fp64, int64_t m, int sms);
-int tracer_max_clusters(int G, int threads);  // co-resident clusters of G tracing CTAs
+int tracer_max_clusters(int G, int threads, bool fp64);  // co-resident clusters of G tracing CTAs
 
 cudaError_t launch_phase_table(double2* phase, int64_t m, cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st);

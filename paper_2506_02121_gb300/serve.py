@@ -204,10 +204,14 @@ def summarize(results, wall: float):
 
 
 class GpuExecutor:
-    """Runs requests through the C ABI on one CUDA stream per slot."""
+    """Runs requests through the C ABI on one CUDA stream per slot.
+
+    precision selects the solver form: "mixed" (FP32 Aberth tracer + certified polish, the
+    library default) or "fp64" (the paper's plain FP64 Aberth form with FP64 caustics), so
+    that one request trace can be served by both."""
 
     def __init__(self, slots: int, block_threads: int = 256, subchains: int = 0, device: int = 0,
-                 cache_bytes: int = 8 << 30):
+                 cache_bytes: int = 8 << 30, precision: str = "mixed"):
         import torch
 
         from . import cc
@@ -220,19 +224,26 @@ class GpuExecutor:
         self.cache = collections.OrderedDict()  # key -> (field, m, z, w, bytes)
         self.cache_bytes = cache_bytes
         self.cache_used = 0
+        if precision not in ("mixed", "fp64"):
+            raise ValueError("precision must be 'mixed' or 'fp64'")
+        self.precision = precision
 
     def _opts(self):
         o = self.cc.cc_options_default()
         o.block_threads = self.block_threads
         o.subchains = self.subchains
+        if self.precision == "fp64":
+            o.precision = self.cc.CC_FP64
+            o.hp_arith = self.cc.CC_HP_FP64
         return o
 
     def estimate_bytes(self, req: Request) -> int:
         rows, nr = req.msteps + 1, 2 * req.n
         zw = 2 * 16 * rows * nr
-        # tracer rows + iteration counts, plus joins and per-CTA Jacobi state for at most
-        # 320 sub-ranges (about 100 bytes per root each)
-        ws = rows * nr * (8 + 4) + 320 * 100 * nr
+        # tracer rows (complex64, or complex128 in the FP64 form) + iteration counts, plus
+        # joins and per-CTA Jacobi state for at most 320 sub-ranges (about 100 bytes per
+        # root each)
+        ws = rows * nr * ((16 if self.precision == "fp64" else 8) + 4) + 320 * 100 * nr
         return zw + ws + 4 * req.map_pixels ** 2
 
     def start(self, req: Request, slot: int):

@@ -2,9 +2,15 @@
 N = 1000 stars (log-uniform masses), m = 10^4 phi steps, 4096^2 maps over +-10.
 
 The oracle cannot trace all 10^4 rows in test time, so it is compared on what it can
-compute one by one (cold-solved sampled rows, per-pixel winding numbers at sampled pixel
-centres, the full distance map from the GPU's N_cc), and properties that hold at any size
-are checked on every row (Vieta sums of the rationalised polynomial, 2N distinct roots)."""
+compute one by one:
+- every one of the 2*10^7 critical points: the oracle's FP64 Newton correction |F/F'| at
+  the GPU's point (the distance to the zero of F, to first order) and the oracle's lens
+  map w at that point, against the GPU's caustic point; every row's points pairwise
+  farther apart than their corrections (2N distinct zeros: the whole row's multiset);
+- cold-solved sampled rows, matched root by root;
+- whole pixel rows of the 4096^2 N_cc map, per-pixel winding numbers at sampled pixel
+  centres, and the full distance map from the GPU's N_cc;
+and Vieta's sums of the rationalised polynomial on every row."""
 import numpy as np
 import pytest
 import torch
@@ -69,6 +75,38 @@ def test_every_row_vieta_and_distinct(solved):
     for j in range(0, m + 1, 997):
         row = np.sort_complex(z[j])
         assert oracle.min_separation(z[j]) > 1e-7
+
+
+def test_every_point_newton_step_and_caustic(solved):
+    """All (m+1) x 2N points at the library defaults (root_refresh = 64): the FP64 Newton
+    correction is below 1e-9 everywhere, the caustic point is within 1e-9 of the oracle's
+    lens map at the GPU's point, and within each row the points are pairwise farther apart
+    than the sum of their corrections, so they are 2N distinct zeros (Sec. 3.2)."""
+    from scipy.spatial import cKDTree
+    f, m, z, w = solved["f"], solved["m"], solved["z"], solved["w"]
+    step, wo = oracle.newton_check(f.x, f.y, f.m, f.kappa_s, f.gamma, m, z)
+    worst = float(step.max())
+    assert worst < TOL, f"largest Newton correction {worst:.3e} at {np.unravel_index(step.argmax(), step.shape)}"
+    dw = float(np.abs(w - wo).max())
+    assert dw < TOL, f"largest caustic difference {dw:.3e}"
+    for j in range(m + 1):
+        pts = np.stack([z[j].real, z[j].imag], axis=1)
+        d, k = cKDTree(pts).query(pts, k=2)
+        assert (d[:, 1] > 2 * TOL + step[j] + step[j][k[:, 1]]).all(), f"row {j}: two points share a zero"
+    print(f"every point: max Newton correction {worst:.3e}, max caustic difference {dw:.3e}")
+
+
+def test_whole_pixel_rows_match_oracle(solved):
+    """16 whole rows of the 4096^2 N_cc map, bit for bit against the oracle's winding rule
+    evaluated over all 2*10^7 GPU caustic segments (Sec. 5.1)."""
+    w, ncc, ext, px = solved["w"], solved["ncc"], solved["ext"], solved["px"]
+    u = synth.uniform(78, 16)
+    rows = sorted({int((k + u[k]) * px / 16) for k in range(16)})
+    ref = oracle.crossing_rows(w, -ext, ext, -ext, ext, px, px, rows)
+    for t, r in enumerate(rows):
+        bad = np.flatnonzero(ncc[r] != ref[t])
+        assert bad.size == 0, f"row {r}: {bad.size} pixels differ, first at column {bad[:5]}"
+    assert sum(int(np.abs(np.diff(ncc[r])).sum()) for r in rows) > 0  # the rows do cross caustics
 
 
 def test_sampled_pixels_match_oracle_winding(solved):

@@ -22,7 +22,9 @@ def _opt(k, base=None):
     return o
 
 
-@pytest.mark.parametrize("n,m,k", [(300, 400, 8), (500, 300, 4), (40, 300, 16), (800, 160, 2)])
+# (400, 1024, 64): the library's default refresh period with 256 rows per sub-range, so
+# every sub-range crosses three refreshes
+@pytest.mark.parametrize("n,m,k", [(300, 400, 8), (500, 300, 4), (40, 300, 16), (800, 160, 2), (400, 1024, 64)])
 def test_split_matches_oracle_and_exact_sum(n, m, k):
     f = synth.disc_field(n, 0.45, 0.05, 0.35, synth.stream_seed(11, n), "loguniform", 0.08, 1.0)
     zo, _, bad = oracle.critical_curves(f.x, f.y, f.m, f.kappa_s, f.gamma, m)

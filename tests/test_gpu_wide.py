@@ -83,3 +83,45 @@ def test_automatic_single_cta_on_long_wide_chains():
         assert left == 0
         idx, dist, sep = match_row(zg[j], zo)
         assert dist < TOL and len(set(idx.tolist())) == len(idx)
+
+
+def _fp64_opt(G):
+    o = cc.cc_options_default()
+    o.precision = cc.CC_FP64
+    o.hp_arith = cc.CC_HP_FP64
+    o.row_ctas = G
+    return o
+
+
+@pytest.mark.parametrize("G", [2, 8])
+def test_fp64_cluster_tracer_matches_oracle(G):
+    """The plain FP64 form traced by clusters of G CTAs per sub-range: chains and caustics
+    match the oracle and the one-CTA FP64 form."""
+    f = synth.disc_field(60, 0.4, 0.0, 0.4, synth.stream_seed(34, G), "loguniform", normalise=True)
+    zg, wg, st, rep = _solve(f, 200, _fp64_opt(G))
+    assert st == cc.CC_OK and rep["unconverged"] == 0 and rep["seam_ambiguous"] == 0, rep
+    zo, _, bad = oracle.critical_curves(f.x, f.y, f.m, f.kappa_s, f.gamma, 200)
+    assert bad == 0
+    compare_chain(zg, zo, TOL)
+    wo = oracle.map_caustics(f.x, f.y, f.m, f.kappa_s, f.gamma, zg)
+    assert np.abs(wg - wo).max() < 1e-12 * (1 + np.abs(wo).max())
+    z1, w1, st1, _ = _solve(f, 200, _fp64_opt(1))
+    assert st1 == cc.CC_OK
+    compare_chain(zg, z1, 2e-9)
+
+
+def test_fp64_automatic_cluster_on_wide_rows():
+    """The FP64 form on n_r = 4200 >= 4096 with few rows takes clusters of 8 CTAs by default;
+    sampled rows pass the oracle's FP64 Newton check, points distinct."""
+    from scipy.spatial import cKDTree
+    n, msteps = 2100, 40
+    f = synth.disc_field(n, 0.3, 0.1, 0.3, synth.stream_seed(33, 2), "loguniform", normalise=True)
+    zg, wg, st, rep = _solve(f, msteps, _fp64_opt(0))
+    assert st == cc.CC_OK and rep["unconverged"] == 0 and rep["seam_ambiguous"] == 0, rep
+    step, wo = oracle.newton_check(f.x, f.y, f.m, f.kappa_s, f.gamma, msteps, zg)
+    assert step.max() < TOL
+    assert np.abs(wg - wo).max() < 1e-12 * (1 + np.abs(wo).max())
+    for j in range(msteps + 1):
+        pts = np.stack([zg[j].real, zg[j].imag], axis=1)
+        d, nb = cKDTree(pts).query(pts, k=2)
+        assert (d[:, 1] > 2 * TOL + step[j] + step[j][nb[:, 1]]).all(), j
