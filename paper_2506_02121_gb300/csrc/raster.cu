@@ -115,35 +115,97 @@ struct CrossK {
     double x0, sx, y0, sy;
     int W, H;
     int* D;
-    float x0f, inv_sxf, y0f, inv_syf;  // FP32 copies for estimates (exactness comes from FP64 checks)
+    float x0f, inv_sxf, y0f, inv_syf, syf;  // FP32 copies (host round-to-nearest) for the fast path
 };
 
 constexpr int XS_THREADS = 256;
 
-// One thread per segment finds, in FP32 with a margin that covers its rounding, the pixel
-// rows its half-open y-range may contain.  The (segment, candidate row) pairs of a warp
-// are then laid out by a warp prefix sum and processed by all 32 lanes together, so the
-// exact FP64 work (row test, prefix length settled by the exact orientation predicate)
-// runs without divergence however unevenly crossings are spread over segments.
+// A double as a float by truncating its significand, with integer instructions only (no
+// FP64 pipe): |f - v| <= 2^-23 |v|, and 0 for |v| < 2^-100 (|f - v| < 2^-100).  ok turns
+// false for a non-finite v or |v| >= 2^100, which the fast path does not take.
+__device__ __forceinline__ float f32_trunc(double v, bool& ok) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FF);
+    if (e >= 1023 + 100) {
+        ok = false;
+        return 0.f;
+    }
+    if (e < 1023 - 100) return 0.f;
+    return __uint_as_float((unsigned)(b >> 63) << 31 | (unsigned)(e - 1023 + 127) << 23 |
+                           (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+
+// Integer key ordering finite doubles like their values (-0 below +0), so that comparing two
+// doubles takes no FP64 instruction.
+__device__ __forceinline__ long long dkey(double v) {
+    const long long k = __double_as_longlong(v);
+    return k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+
+// Segment flags in the scatter kernel's shared memory.
+constexpr int XS_FAST = 1;  // coordinates within the fast path's range
+
+// One thread per segment finds the pixel rows its half-open y-range may contain, in FP32
+// with a margin (1e-3 row plus 8x the rounding bound) that covers the rounding.  The
+// (segment, candidate row) pairs of a warp are then laid out by a warp prefix sum and
+// processed by all 32 lanes together:
+//  - a row more than the margin inside the candidate range is in the segment's half-open
+//    y-range for certain; only a row within the margin of either end takes the exact FP64
+//    test on its FP64 pixel centre;
+//  - the count c of pixel centres left of the crossing abscissa (c = ceil(u) for
+//    u = (x_c - x0)/sx - 1/2) comes from an FP32 evaluation of u with a rigorous bound E on
+//    its error, propagated term by term from the inputs' truncation (2^-23 relative) and
+//    each FP32 rounding (2^-24); when an integer lies within E of u the exact orientation
+//    predicate settles c in FP64.
+// FP32 carries all but a few pairs per thousand, so the counts equal a per-pixel
+// evaluation of Sunday's rule bit for bit while the FP64 pipe (1/64 of the FP32 rate on
+// this part) stays off the critical path.
 __global__ void __launch_bounds__(XS_THREADS) crossing_scatter_kernel(CrossK K) {
     __shared__ double2 s_a[XS_THREADS], s_b[XS_THREADS];
-    __shared__ int s_r0[XS_THREADS], s_excl[XS_THREADS];
+    __shared__ float4 s_f[XS_THREADS];   // a.x, a.y, b.x, b.y truncated to FP32
+    __shared__ float2 s_t[XS_THREADS];   // candidate range ends tl, th (row units, FP32)
+    __shared__ float s_eps[XS_THREADS];  // their error margin
+    __shared__ int s_r0[XS_THREADS], s_excl[XS_THREADS], s_flag[XS_THREADS];
     const int lane = threadIdx.x & 31;
     const int wbase = threadIdx.x & ~31;
     const int64_t t = blockIdx.x * (int64_t)XS_THREADS + threadIdx.x;
     const int64_t nseg = (K.rows - 1) * K.nr;
-    int r0 = 0, cnt = 0;
+    int r0 = 0, cnt = 0, flag = 0;
     double2 a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+    float4 fv = make_float4(0.f, 0.f, 0.f, 0.f);
+    float tl = 0.f, th = 0.f, eps = 0.f;
     if (t < nseg) {
         a = K.w[t];
         b = K.w[t + K.nr];
-        if (isfinite(a.x) && isfinite(a.y) && isfinite(b.x) && isfinite(b.y) && a.y != b.y) {
-            const float lo = (float)fmin(a.y, b.y), hi = (float)fmax(a.y, b.y);
-            const float tl = (lo - K.y0f) * K.inv_syf - 0.5f;
-            const float th = (hi - K.y0f) * K.inv_syf - 0.5f;
-            const float eps = 1e-3f + 1e-6f * ((fabsf(lo) + fabsf(K.y0f)) * fabsf(K.inv_syf) + fabsf(tl) + fabsf(th));
-            const float fr0 = fmaxf(ceilf(tl - eps), 0.0f);
-            const float fr1 = fminf(floorf(th + eps) + 1.0f, (float)K.H);  // candidates [fr0, fr1)
+        const unsigned long long ya = (unsigned long long)__double_as_longlong(a.y);
+        const unsigned long long yb = (unsigned long long)__double_as_longlong(b.y);
+        const bool finite = ((((unsigned long long)__double_as_longlong(a.x) >> 52) & 0x7FF) != 0x7FF) &&
+                            ((((unsigned long long)__double_as_longlong(b.x) >> 52) & 0x7FF) != 0x7FF) &&
+                            (((ya >> 52) & 0x7FF) != 0x7FF) && (((yb >> 52) & 0x7FF) != 0x7FF);
+        // a.y == b.y (equal bits, or +0 and -0): no pixel centre can satisfy a.y <= y < b.y
+        if (finite && ((ya ^ yb) << 1) != 0ull) {
+            bool ok = true;
+            fv.x = f32_trunc(a.x, ok);
+            fv.y = f32_trunc(a.y, ok);
+            fv.z = f32_trunc(b.x, ok);
+            fv.w = f32_trunc(b.y, ok);
+            float fr0, fr1;
+            if (ok) {
+                flag = XS_FAST;
+                const float lo = fminf(fv.y, fv.w), hi = fmaxf(fv.y, fv.w);
+                tl = (lo - K.y0f) * K.inv_syf - 0.5f;
+                th = (hi - K.y0f) * K.inv_syf - 0.5f;
+                eps = 1e-3f + 1e-6f * ((fmaxf(fabsf(lo), fabsf(hi)) + fabsf(K.y0f)) * fabsf(K.inv_syf) + fabsf(tl) +
+                                       fabsf(th));
+                fr0 = fmaxf(ceilf(tl - eps), 0.0f);
+                fr1 = fminf(floorf(th + eps) + 1.0f, (float)K.H);
+            } else {
+                // coordinates beyond 2^100: candidate rows in FP64 (every row is tested exactly)
+                const double lo = fmin(a.y, b.y), hi = fmax(a.y, b.y);
+                const double tld = (lo - K.y0) / K.sy - 0.5, thd = (hi - K.y0) / K.sy - 0.5;
+                fr0 = (float)fmax(ceil(tld - 1e-3 - 1e-9 * fabs(tld)), 0.0);
+                fr1 = (float)fmin(floor(thd + 1e-3 + 1e-9 * fabs(thd)) + 1.0, (double)K.H);
+            }
             if (fr1 > fr0) {
                 r0 = (int)fr0;
                 cnt = (int)fr1 - r0;
@@ -161,8 +223,12 @@ __global__ void __launch_bounds__(XS_THREADS) crossing_scatter_kernel(CrossK K) 
     if (total == 0) return;  // whole warp: nothing to do
     s_a[threadIdx.x] = a;
     s_b[threadIdx.x] = b;
+    s_f[threadIdx.x] = fv;
+    s_t[threadIdx.x] = make_float2(tl, th);
+    s_eps[threadIdx.x] = eps;
     s_r0[threadIdx.x] = r0;
     s_excl[threadIdx.x] = incl - cnt;
+    s_flag[threadIdx.x] = flag;
     __syncwarp();
     for (int base = 0; base < total; base += 32) {
         const int item = base + lane;
@@ -175,37 +241,74 @@ __global__ void __launch_bounds__(XS_THREADS) crossing_scatter_kernel(CrossK K) 
             else hi = mid - 1;
         }
         const int j = wbase + lo;
+        const int r = s_r0[j] + (item - s_excl[j]);
+        const bool fast = s_flag[j] & XS_FAST;
         const double2 sa = s_a[j], sb = s_b[j];
-        const int64_t r = s_r0[j] + (item - s_excl[j]);
-        const bool up = sa.y < sb.y;
-        const double ylo = up ? sa.y : sb.y, yhi = up ? sb.y : sa.y;
-        const double py = pix(K.y0, K.sy, r);
-        if (!(ylo <= py && py < yhi)) continue;  // exact half-open row test
+        const bool up = dkey(sa.y) < dkey(sb.y);  // exact: a.y != b.y here
         const int sgn = up ? 1 : -1;
-        // prefix length c: the centres with orient(a, b, P) == sgn are those left of the
-        // crossing abscissa xc, i.e. with index i < u = (xc - x0)/sx - 0.5, so c = ceil(u).
-        // u in FP32 from FP64 differences; its error is at most
-        //   (2.4e-7 |x_a - x0| + 5e-7 |x_b - x_a|) / sx + 6e-8 (|u| + 0.5)
-        // (each difference rounded once to FP32, |t| <= 1, IEEE division and products); with
-        // no centre index within 4x that bound of u the count is settled, else the exact
-        // orientation predicate settles it.
-        const float sxr = (float)(sa.x - K.x0);
-        const float exf = (float)(sb.x - sa.x), eyf = (float)(sb.y - sa.y);
-        const float tf = __fdiv_rn((float)(py - sa.y), eyf);
-        const float u = __fsub_rn(__fmul_rn(__fadd_rn(sxr, __fmul_rn(exf, tf)), K.inv_sxf), 0.5f);
-        const float err = 4.0f * ((4e-7f * (fabsf(sxr) + fabsf(exf))) * K.inv_sxf + 2.4e-7f * fabsf(u) + 1e-6f);
-        int64_t c;
-        if (isfinite(u) && isfinite(err) && ceilf(u - err) == ceilf(u + err)) {
-            c = (int64_t)fminf(fmaxf(ceilf(u), 0.0f), (float)K.W);
-        } else {
-            float ce = ceilf(u);
-            ce = fminf(fmaxf(ce, 0.0f), (float)K.W);
-            if (!(ce == ce)) ce = 0.0f;  // NaN guard
+        const float rf = (float)r;
+        bool sure = false;
+        if (fast) {
+            const float2 tt = s_t[j];
+            const float e = s_eps[j];
+            sure = rf > tt.x + e && rf < tt.y - e;
+        }
+        double py = 0.0;
+        if (!sure) {  // exact half-open row test on the FP64 pixel centre
+            const bool upx = sa.y < sb.y;
+            const double ylo = upx ? sa.y : sb.y, yhi = upx ? sb.y : sa.y;
+            py = pix(K.y0, K.sy, r);
+            if (!(ylo <= py && py < yhi)) continue;
+        }
+        int64_t c = -1;
+        float u = 0.f;
+        if (fast) {
+            // u = (x_c - x0)/sx - 1/2 in FP32 and a bound E on its error (EPS >= 2^-23 (1 + 2^-23):
+            // truncation of the inputs; the host-rounded constants and each operation add
+            // 2^-24 relative)
+            const float EPS = 1.2e-7f;
+            const float4 f = s_f[j];
+            const float sxr = f.x - K.x0f, e1 = EPS * (fabsf(f.x) + fabsf(K.x0f) + fabsf(sxr));
+            const float exf = f.z - f.x, e2 = EPS * (fabsf(f.x) + fabsf(f.z) + fabsf(exf));
+            const float eyf = f.w - f.y, e3 = EPS * (fabsf(f.y) + fabsf(f.w) + fabsf(eyf));
+            const float ayr = f.y - K.y0f, e4 = EPS * (fabsf(f.y) + fabsf(K.y0f) + fabsf(ayr));
+            const float den = fabsf(eyf) - e3;
+            if (den > 0.f) {
+                // py - y0 = (r + 1/2) sy: syf and the product each round once; the FP64 pixel
+                // centre itself is within 2^-52 (|y0| + |py|) of its real value
+                const float pr = (rf + 0.5f) * K.syf;
+                const float e5 = 2.0f * EPS * fabsf(pr) + 1e-12f * (fabsf(K.y0f) + fabsf(pr));
+                const float ty = pr - ayr, e6 = e5 + e4 + EPS * fabsf(ty);
+                const float tf = __fdiv_rn(ty, eyf);
+                const float dT = __fdiv_rn(e6 + fabsf(tf) * e3, den) + EPS * fabsf(tf);
+                const float p = exf * tf, e7 = fabsf(exf) * dT + (fabsf(tf) + dT) * e2 + EPS * fabsf(p);
+                const float sm = sxr + p, e8 = e1 + e7 + EPS * fabsf(sm);
+                const float v = sm * K.inv_sxf, e9 = e8 * fabsf(K.inv_sxf) * 1.0001f + 2.0f * EPS * fabsf(v);
+                u = v - 0.5f;
+                const float E = 1.01f * (e9 + EPS * fabsf(u)) + 1e-6f;
+                if (isfinite(u) && isfinite(E)) {
+                    if (u - E >= (float)K.W) c = K.W;
+                    else if (u + E <= 0.f) c = 0;
+                    else if (ceilf(u - E) == ceilf(u + E)) c = (int64_t)fminf(fmaxf(ceilf(u), 0.0f), (float)K.W);
+                }
+            }
+        }
+        if (c < 0) {
+            // exact: walk from an estimate with the orientation predicate
+            if (sure) py = pix(K.y0, K.sy, r);
+            double ue = u;
+            if (!fast || !isfinite(u)) {
+                const double ey = sb.y - sa.y;
+                ue = ((sa.x - K.x0) + (sb.x - sa.x) * ((py - sa.y) / ey)) / K.sx - 0.5;
+            }
+            double ce = ceil(ue);
+            ce = fmin(fmax(ce, 0.0), (double)K.W);
+            if (!(ce == ce)) ce = 0.0;  // NaN guard
             c = (int64_t)ce;
             while (c > 0 && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c - 1), py) != sgn) c--;
             while (c < K.W && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c), py) == sgn) c++;
         }
-        if (c > 0) atomicAdd(&K.D[r * K.W + (c - 1)], sgn);
+        if (c > 0) atomicAdd(&K.D[(int64_t)r * K.W + (c - 1)], sgn);
     }
 }
 
@@ -274,6 +377,7 @@ cudaError_t launch_crossing_map(const double2* w, int64_t rows, int64_t nr, doub
         K.inv_sxf = (float)(1.0 / K.sx);
         K.y0f = (float)y0;
         K.inv_syf = (float)(1.0 / K.sy);
+        K.syf = (float)K.sy;
         const int64_t segs = (rows - 1) * nr;
         crossing_scatter_kernel<<<(unsigned)((segs + XS_THREADS - 1) / XS_THREADS), XS_THREADS, 0, st>>>(K);
         e = cudaGetLastError();
@@ -350,27 +454,14 @@ __device__ __forceinline__ long long edt_key(const int32_t* f, int q) {
     return (long long)f[q] * f[q] + (long long)q * q;
 }
 
-// Row pass, one warp per row, exact integer arithmetic.  D(i) = min_q (i - q)^2 + g[q]^2 is
-// the lower envelope of the parabolas of the columns with a feature; its owners are the
-// vertices of the lower convex hull of the lifted points (q, q^2 + g[q]^2).  Lane l takes
-// the band of columns [l Bw, (l + 1) Bw) and builds the hull of its band with a stack; five
-// rounds of bridge merges join neighbouring bands (the hull of two column-separated sets
-// keeps a prefix of the left hull and a suffix of the right one, found by walking both
-// ends until neither end point can be dropped); then the warp fills the row 32 pixels at
-// a time, each lane walking the hull forward from the owner of the tile's first pixel.
-// Band position k of lane l is stored at [k * EDT_LS + l] (16-bit g values; 8- or 16-bit
-// stack entries), so the lanes of a warp stepping through their bands together never share
-// a shared-memory bank word they do not also share an address in.
+// Band layout of the row pass: band position k of lane l at [k * EDT_LS + l], so that the
+// lanes of a warp stepping through their bands together never share a shared-memory bank
+// word they do not also share an address in.  g values are 16-bit (0xFFFF: no feature in
+// the column), hull stacks 8-bit band positions while a band holds at most 256 columns
+// (W <= 8192), else 16-bit.
 constexpr int EDT_BAND_MAX_W = 32768;
 constexpr int EDT_BAND_MAX_H = 65535;  // g < H fits 16 bits, 0xFFFF marks "no feature"
 constexpr int EDT_LS = 33;
-
-// g values (16 bits) and hull stacks of band positions (8 bits while a band holds at most
-// 256 columns, i.e. W <= 8192, else 16): the smaller stacks let more rows share an SM.
-size_t edt_band_smem(int W) {
-    const size_t Bw = (size_t)((W + 31) / 32);
-    return (sizeof(uint16_t) + (Bw <= 256 ? sizeof(uint8_t) : sizeof(uint16_t))) * Bw * EDT_LS;
-}
 
 __device__ __forceinline__ long long edt_lift(int q, int gq) { return (long long)q * q + (long long)gq * gq; }
 
@@ -386,156 +477,6 @@ constexpr int EDT_SQRT_T = 65536;
 __global__ void edt_sqrt_table_kernel(double* tab, int T) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < T) tab[k] = sqrt((double)k);
-}
-
-template <typename ST>
-__global__ void __launch_bounds__(32) edt_row_band_kernel(const int32_t* g, int W, double pixel, double* d_out,
-                                                          const double* sqtab, int T) {
-    extern __shared__ uint16_t edt_sh[];
-    __shared__ int s_lo[32], s_hi[32];
-    const int r = blockIdx.x, lane = threadIdx.x;
-    const int Bw = (W + 31) / 32;
-    uint16_t* gs = edt_sh;                          // g by (band position, lane)
-    ST* st = (ST*)(edt_sh + (size_t)Bw * EDT_LS);   // hull stacks: band positions
-    const int32_t* gr = g + (int64_t)r * W;
-    {
-        int l = lane / Bw, k = lane - l * Bw;  // column q = lane
-        for (int q = lane; q < W; q += 32) {
-            const int32_t v = gr[q];
-            gs[k * EDT_LS + l] = v >= 0xFFFF ? (uint16_t)0xFFFF : (uint16_t)v;
-            k += 32;
-            while (k >= Bw) {
-                k -= Bw;
-                l++;
-            }
-        }
-    }
-    __syncwarp();
-    auto site_g = [&](int l, int k) -> int { return gs[k * EDT_LS + l]; };
-    // 1. hull of the own band
-    const int a = lane * Bw;
-    const int bl = max(0, min(Bw, W - a));
-    int len = 0;
-    int ku = 0, kv = 0;             // band positions of the two top stack entries
-    long long cu = 0, cv = 0;       // and their lifted values
-    for (int k = 0; k < bl; k++) {
-        const int gq = site_g(lane, k);
-        if (gq == 0xFFFF) continue;
-        const long long cq = edt_lift(a + k, gq);
-        while (len >= 2 && !edt_keep(ku, cu, kv, cv, k, cq)) {
-            len--;
-            kv = ku;
-            cv = cu;
-            if (len >= 2) {
-                ku = st[(len - 2) * EDT_LS + lane];
-                cu = edt_lift(a + ku, site_g(lane, ku));
-            }
-        }
-        st[len * EDT_LS + lane] = (ST)k;
-        len++;
-        ku = kv;
-        cu = cv;
-        kv = k;
-        cv = cq;
-    }
-    s_lo[lane] = 0;
-    s_hi[lane] = len;
-    __syncwarp();
-    // 2. bridge merges of the hulls of lane groups [b, b + h) and [b + h, b + 2h)
-    for (int h = 1; h < 32; h <<= 1) {
-        if ((lane & (2 * h - 1)) == 0) {
-            const int b = lane, e = lane + 2 * h;
-            int la = b + h - 1, lb = b + h;
-            while (la >= b && s_lo[la] == s_hi[la]) la--;
-            while (lb < e && s_lo[lb] == s_hi[lb]) lb++;
-            if (la >= b && lb < e) {
-                int pa = s_hi[la] - 1, pb = s_lo[lb];
-                int ka = st[pa * EDT_LS + la], kb = st[pb * EDT_LS + lb];
-                int qa = la * Bw + ka, qb = lb * Bw + kb;
-                long long ca = edt_lift(qa, site_g(la, ka)), cb = edt_lift(qb, site_g(lb, kb));
-                for (bool changed = true; changed;) {
-                    changed = false;
-                    for (;;) {  // drop the left end point while it is not below chord(pred, B)
-                        int lp = la, pp = pa - 1;
-                        if (pp < s_lo[la]) {
-                            lp = la - 1;
-                            while (lp >= b && s_lo[lp] == s_hi[lp]) lp--;
-                            if (lp < b) break;
-                            pp = s_hi[lp] - 1;
-                        }
-                        const int kp = st[pp * EDT_LS + lp], qp = lp * Bw + kp;
-                        const long long cp = edt_lift(qp, site_g(lp, kp));
-                        if (edt_keep(qp, cp, qa, ca, qb, cb)) break;
-                        s_hi[la] = pa;
-                        la = lp;
-                        pa = pp;
-                        qa = qp;
-                        ca = cp;
-                        changed = true;
-                    }
-                    for (;;) {  // drop the right end point while it is not below chord(A, succ)
-                        int ln = lb, pn = pb + 1;
-                        if (pn >= s_hi[lb]) {
-                            ln = lb + 1;
-                            while (ln < e && s_lo[ln] == s_hi[ln]) ln++;
-                            if (ln >= e) break;
-                            pn = s_lo[ln];
-                        }
-                        const int kn = st[pn * EDT_LS + ln], qn = ln * Bw + kn;
-                        const long long cn = edt_lift(qn, site_g(ln, kn));
-                        if (edt_keep(qa, ca, qb, cb, qn, cn)) break;
-                        s_lo[lb] = pb + 1;
-                        lb = ln;
-                        pb = pn;
-                        qb = qn;
-                        cb = cn;
-                        changed = true;
-                    }
-                }
-            }
-        }
-        __syncwarp();
-    }
-    // 3. fill, 32 pixels at a time
-    double* out = d_out + (int64_t)r * W;
-    const unsigned live = __ballot_sync(0xffffffffu, s_lo[lane] < s_hi[lane]);
-    if (live == 0) {
-        for (int i = lane; i < W; i += 32) out[i] = __longlong_as_double(0x7ff0000000000000LL);
-        return;
-    }
-    int cl = __ffs(live) - 1, cp = s_lo[cl];
-    for (int t0 = 0; t0 < W; t0 += 32) {
-        const int i = t0 + lane;
-        int L = cl, p = cp;
-        int k = st[p * EDT_LS + L];
-        int q = L * Bw + k, gq = site_g(L, k);
-        long long cq = edt_lift(q, gq);
-        if (i < W) {
-            for (;;) {
-                int L2 = L, p2 = p + 1;
-                if (p2 >= s_hi[L]) {
-                    const unsigned rest = live & ~((2u << L) - 1u);
-                    if (rest == 0) break;
-                    L2 = __ffs(rest) - 1;
-                    p2 = s_lo[L2];
-                }
-                const int k2 = st[p2 * EDT_LS + L2];
-                const int q2 = L2 * Bw + k2, g2 = site_g(L2, k2);
-                const long long c2 = edt_lift(q2, g2);
-                if (c2 - cq > 2LL * i * (q2 - q)) break;  // the next owner starts right of i
-                L = L2;
-                p = p2;
-                q = q2;
-                gq = g2;
-                cq = c2;
-            }
-            const long long d2 = (long long)(i - q) * (i - q) + (long long)gq * gq;
-            out[i] = pixel * (d2 < T ? sqtab[d2] : sqrt((double)d2));
-        }
-        const int last = min(31, W - 1 - t0);
-        cl = __shfl_sync(0xffffffffu, L, last);
-        cp = __shfl_sync(0xffffffffu, p, last);
-    }
 }
 
 // Row pass for very wide maps: one thread per row, envelope stack in global memory.
@@ -647,17 +588,363 @@ cudaError_t launch_moving_distance_map(const int32_t* ncc, int32_t W, int32_t H,
     return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------------
+// Distance map, banded path (W <= EDT_BAND_MAX_W, H <= EDT_BAND_MAX_H).  The column pass is
+// never written out: one read of N_cc gives every pixel's feature bit, packed 64 rows to a
+// word per column (W H / 8 bytes), with each 64-row chunk's first and last feature row; a
+// scan over the chunks gives, per (chunk, column), the nearest feature row above and below
+// the chunk.  The row pass then takes each column distance g from the column's word (the
+// nearest set bit on either side of the row, by count-leading/trailing-zeros) or the
+// chunk's neighbours, all read from L2, builds the lower envelope, and fills the row.
+// ----------------------------------------------------------------------------------
+constexpr int EDT_BITS = 64;  // rows per feature word
+
+// Feature word of (chunk c, column i): bit b set when pixel (c * 64 + b, i) is a feature;
+// and the chunk's first and last feature row (-1 when none).  One thread per (chunk,
+// column); a warp covers 32 adjacent columns and passes the row values to its neighbours
+// by shuffles (lanes past the map's edge take part with no loads).
+__global__ void __launch_bounds__(128) edt_bits_kernel(const int32_t* ncc, int W, int H, unsigned long long* bits,
+                                                         int2* summ) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    const int r0 = c * EDT_BITS, r1 = min(H, r0 + EDT_BITS);
+    const bool in = i < W;
+    auto at = [&](int r, int col) -> int32_t { return ncc[(int64_t)r * W + col]; };
+    int32_t up = 0, cur = 0, dn = 0;
+    const bool has_up = r0 > 0;
+    if (in) {
+        if (has_up) up = at(r0 - 1, i);
+        cur = at(r0, i);
+    }
+    unsigned long long word = 0ull;
+    int first = -1, last = -1;
+    for (int r = r0; r < r1; r++) {
+        const bool has_dn = r + 1 < H;
+        if (in && has_dn) dn = at(r + 1, i);
+        int32_t left = __shfl_up_sync(0xffffffffu, cur, 1);
+        int32_t right = __shfl_down_sync(0xffffffffu, cur, 1);
+        if (in && lane == 0 && i > 0) left = at(r, i - 1);
+        if (in && lane == 31 && i + 1 < W) right = at(r, i + 1);
+        const bool f = in && ((i > 0 && left != cur) || (i + 1 < W && right != cur) || (r > 0 && up != cur) ||
+                              (has_dn && dn != cur));
+        if (f) {
+            word |= 1ull << (r - r0);
+            if (first < 0) first = r;
+            last = r;
+        }
+        up = cur;
+        cur = dn;
+    }
+    if (in) {
+        bits[(int64_t)c * W + i] = word;
+        summ[(int64_t)c * W + i] = make_int2(first, last);
+    }
+}
+
+// Per column: nearest feature row above chunk c (in chunks < c) and below it (in chunks > c),
+// -1 when none.
+__global__ void edt_chunk_scan_kernel(const int2* summ, int W, int nchunk, int2* ab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W) return;
+    int above = -1;
+    for (int c = 0; c < nchunk; c++) {
+        ab[(int64_t)c * W + i].x = above;
+        const int l = summ[(int64_t)c * W + i].y;
+        if (l >= 0) above = l;
+    }
+    int below = -1;
+    for (int c = nchunk - 1; c >= 0; c--) {
+        ab[(int64_t)c * W + i].y = below;
+        const int f = summ[(int64_t)c * W + i].x;
+        if (f >= 0) below = f;
+    }
+}
+
+// Distance in rows from row r to the nearest feature of column q (0xFFFF when the column has
+// none): the nearest set bit of the column's word on either side of bit b = r mod 64, else
+// the nearest feature of the chunks above or below.
+__device__ __forceinline__ int edt_col_dist(unsigned long long w, int2 ab, int r, int b) {
+    int d = 0xFFFF;
+    const unsigned long long lo = b == 63 ? w : (w & ((2ull << b) - 1ull));  // rows <= r in the chunk
+    if (lo) d = b - (63 - __clzll(lo));
+    else if (ab.x >= 0) d = r - ab.x;
+    const unsigned long long hi = w >> b;  // rows >= r in the chunk
+    if (hi) d = min(d, __ffsll(hi) - 1);
+    else if (ab.y >= 0) d = min(d, ab.y - r);
+    return d;
+}
+
+// First pixel owned by envelope vertex v = (qv, cv) after its predecessor u = (qu, cu),
+// qu < qv: the smallest integer t with (t - qv)^2 + gv^2 <= (t - qu)^2 + gu^2, i.e.
+// t (2 (qv - qu)) >= cv - cu (c = q^2 + g^2), clamped to [0, W + 1].  An FP32 quotient lands
+// within one of it, and exact int64 products settle it.
+__device__ __forceinline__ int edt_start(int qu, long long cu, int qv, long long cv, int W) {
+    const long long num = cv - cu;
+    const long long den = 2LL * (qv - qu);
+    const float est = (float)num / (float)den;
+    if (!(est < (float)W + 2.0f)) return W + 1;
+    if (est < -2.0f) return 0;
+    int t = (int)ceilf(est);
+    while ((long long)(t - 1) * den >= num) t--;
+    while ((long long)t * den < num) t++;
+    return max(0, min(t, W + 1));
+}
+
+// Row pass, one warp per row.  g of the row from the feature words (band layout of the
+// hull build: column q = l Bw + k at [k EDT_LS + l]), the hull of each lane's band, five
+// rounds of bridge merges, then every surviving vertex writes its
+// column at the first pixel it owns (own[]; a vertex whose range is empty writes nothing),
+// and the fill takes, 32 pixels at a time, the running maximum of own[] by a warp scan:
+// the owner's column (envelope columns increase with the pixel).
+template <typename ST>
+__global__ void __launch_bounds__(32) edt_row_env_kernel(const unsigned long long* bits, const int2* ab, int W,
+                                                         double pixel, double* d_out, const double* sqtab, int T) {
+    extern __shared__ uint16_t edt_sh[];
+    __shared__ int s_lo[32], s_hi[32];
+    const int r = blockIdx.x, lane = threadIdx.x;
+    const int Bw = (W + 31) / 32;
+    uint16_t* gs = edt_sh;                              // g by (band position, lane)
+    ST* st = (ST*)(edt_sh + (size_t)Bw * EDT_LS);       // hull stacks: band positions
+    uint16_t* own = (uint16_t*)((char*)st + ((sizeof(ST) * (size_t)Bw * EDT_LS + 15) & ~(size_t)15));
+    const int c = r / EDT_BITS, b = r - c * EDT_BITS;
+    {
+        const unsigned long long* wr = bits + (int64_t)c * W;
+        const int2* abr = ab + (int64_t)c * W;
+        int l = lane / Bw, k = lane - l * Bw;  // column q = lane
+        for (int q = lane; q < W; q += 32) {
+            gs[k * EDT_LS + l] = (uint16_t)edt_col_dist(__ldg(wr + q), __ldg(abr + q), r, b);
+            k += 32;
+            while (k >= Bw) {
+                k -= Bw;
+                l++;
+            }
+        }
+        for (int i = lane; i < W; i += 32) own[i] = 0;
+    }
+    __syncwarp();
+    auto site_g = [&](int l, int k) -> int { return gs[k * EDT_LS + l]; };
+    // 1. hull of the own band
+    const int a = lane * Bw;
+    const int bl = max(0, min(Bw, W - a));
+    int len = 0;
+    int ku = 0, kv = 0;
+    long long cu = 0, cv = 0;
+    for (int k = 0; k < bl; k++) {
+        const int gq = site_g(lane, k);
+        if (gq == 0xFFFF) continue;
+        const long long cq = edt_lift(a + k, gq);
+        while (len >= 2 && !edt_keep(ku, cu, kv, cv, k, cq)) {
+            len--;
+            kv = ku;
+            cv = cu;
+            if (len >= 2) {
+                ku = st[(len - 2) * EDT_LS + lane];
+                cu = edt_lift(a + ku, site_g(lane, ku));
+            }
+        }
+        st[len * EDT_LS + lane] = (ST)k;
+        len++;
+        ku = kv;
+        cu = cv;
+        kv = k;
+        cv = cq;
+    }
+    s_lo[lane] = 0;
+    s_hi[lane] = len;
+    __syncwarp();
+    // 2. bridge merges of the hulls of lane groups [b0, b0 + h) and [b0 + h, b0 + 2h)
+    for (int h = 1; h < 32; h <<= 1) {
+        if ((lane & (2 * h - 1)) == 0) {
+            const int b0 = lane, e = lane + 2 * h;
+            int la = b0 + h - 1, lb = b0 + h;
+            while (la >= b0 && s_lo[la] == s_hi[la]) la--;
+            while (lb < e && s_lo[lb] == s_hi[lb]) lb++;
+            if (la >= b0 && lb < e) {
+                int pa = s_hi[la] - 1, pb = s_lo[lb];
+                int ka = st[pa * EDT_LS + la], kb = st[pb * EDT_LS + lb];
+                int qa = la * Bw + ka, qb = lb * Bw + kb;
+                long long ca = edt_lift(qa, site_g(la, ka)), cb = edt_lift(qb, site_g(lb, kb));
+                for (bool changed = true; changed;) {
+                    changed = false;
+                    for (;;) {  // drop the left end point while it is not below chord(pred, B)
+                        int lp = la, pp = pa - 1;
+                        if (pp < s_lo[la]) {
+                            lp = la - 1;
+                            while (lp >= b0 && s_lo[lp] == s_hi[lp]) lp--;
+                            if (lp < b0) break;
+                            pp = s_hi[lp] - 1;
+                        }
+                        const int kp = st[pp * EDT_LS + lp], qp = lp * Bw + kp;
+                        const long long cp = edt_lift(qp, site_g(lp, kp));
+                        if (edt_keep(qp, cp, qa, ca, qb, cb)) break;
+                        s_hi[la] = pa;
+                        la = lp;
+                        pa = pp;
+                        qa = qp;
+                        ca = cp;
+                        changed = true;
+                    }
+                    for (;;) {  // drop the right end point while it is not below chord(A, succ)
+                        int ln = lb, pn = pb + 1;
+                        if (pn >= s_hi[lb]) {
+                            ln = lb + 1;
+                            while (ln < e && s_lo[ln] == s_hi[ln]) ln++;
+                            if (ln >= e) break;
+                            pn = s_lo[ln];
+                        }
+                        const int kn = st[pn * EDT_LS + ln], qn = ln * Bw + kn;
+                        const long long cn = edt_lift(qn, site_g(ln, kn));
+                        if (edt_keep(qa, ca, qb, cb, qn, cn)) break;
+                        s_lo[lb] = pb + 1;
+                        lb = ln;
+                        pb = pn;
+                        qb = qn;
+                        cb = cn;
+                        changed = true;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    double* out = d_out + (int64_t)r * W;
+    const unsigned live = __ballot_sync(0xffffffffu, s_lo[lane] < s_hi[lane]);
+    if (live == 0) {
+        for (int i = lane; i < W; i += 32) out[i] = __longlong_as_double(0x7ff0000000000000LL);
+        return;
+    }
+    // 3. start pixel of every surviving vertex; a vertex with a non-empty range [s, s_next)
+    // inside the row writes its column at own[s]
+    if (s_lo[lane] < s_hi[lane]) {
+        const unsigned before = live & ((1u << lane) - 1u);
+        int qu = -1;
+        long long cu2 = 0;
+        if (before) {
+            const int lp = 31 - __clz(before);
+            const int kp = st[(s_hi[lp] - 1) * EDT_LS + lp];
+            qu = lp * Bw + kp;
+            cu2 = edt_lift(qu, site_g(lp, kp));
+        }
+        int qv = lane * Bw + st[s_lo[lane] * EDT_LS + lane];
+        long long cv2 = edt_lift(qv, site_g(lane, qv - lane * Bw));
+        int sv = qu < 0 ? 0 : edt_start(qu, cu2, qv, cv2, W);
+        for (int p = s_lo[lane]; p < s_hi[lane]; p++) {
+            // successor of entry p: the next entry of this lane, or the first of the next live lane
+            int qn = -1;
+            long long cn = 0;
+            if (p + 1 < s_hi[lane]) {
+                const int kn = st[(p + 1) * EDT_LS + lane];
+                qn = lane * Bw + kn;
+                cn = edt_lift(qn, site_g(lane, kn));
+            } else {
+                const unsigned after = live & ~((2u << lane) - 1u);
+                if (after) {
+                    const int ln = __ffs(after) - 1;
+                    const int kn = st[s_lo[ln] * EDT_LS + ln];
+                    qn = ln * Bw + kn;
+                    cn = edt_lift(qn, site_g(ln, kn));
+                }
+            }
+            const int sn = qn < 0 ? W : edt_start(qv, cv2, qn, cn, W);
+            if (sv < sn && sv < W) own[sv] = (uint16_t)qv;
+            qv = qn;
+            cv2 = cn;
+            sv = sn;
+        }
+    }
+    __syncwarp();
+    // 4. fill, 32 pixels at a time: owner = running maximum of own[]
+    const float inv_bw = 1.0f / (float)Bw;
+    int carry = 0;
+    for (int t0 = 0; t0 < W; t0 += 32) {
+        const int i = t0 + lane;
+        int q = i < W ? own[i] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, q, off);
+            if (lane >= off) q = max(q, y);
+        }
+        q = max(q, carry);
+        carry = __shfl_sync(0xffffffffu, q, 31);
+        if (i < W) {
+            // band of column q: (q + 1/2) / Bw in FP32 is within 4e-6 of the exact quotient, whose
+            // fractional part stays >= 1/(2 Bw) >= 4.9e-4 away from an integer (q < 2^15)
+            const int l = (int)(((float)q + 0.5f) * inv_bw), k = q - l * Bw;
+            const int gq = site_g(l, k);
+            const long long d2 = (long long)(i - q) * (i - q) + (long long)gq * gq;
+            out[i] = pixel * (d2 < T ? sqtab[d2] : sqrt((double)d2));
+        }
+    }
+}
+
+size_t edt_env_smem(int W, bool byte_stacks) {
+    const size_t Bw = (size_t)((W + 31) / 32);
+    const size_t stb = ((byte_stacks ? 1 : 2) * Bw * EDT_LS + 15) & ~(size_t)15;
+    return sizeof(uint16_t) * Bw * EDT_LS + stb + sizeof(uint16_t) * (size_t)((W + 31) / 32 * 32);
+}
+
+// Workspace of the banded path: feature words, chunk summaries, chunk neighbours, square
+// roots.
+struct EdtEnvLayout {
+    size_t bits, summ, ab, sq, total;
+};
+
+EdtEnvLayout edt_env_layout(int32_t W, int32_t H) {
+    const size_t nchunk = (size_t)((H + EDT_BITS - 1) / EDT_BITS);
+    auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+    EdtEnvLayout L;
+    L.bits = 0;
+    L.summ = L.bits + al(nchunk * W * sizeof(unsigned long long));
+    L.ab = L.summ + al(nchunk * W * sizeof(int2));
+    L.sq = L.ab + al(nchunk * W * sizeof(int2));
+    L.total = L.sq + al(sizeof(double) * EDT_SQRT_T);
+    return L;
+}
+
+bool edt_banded(int32_t W, int32_t H) { return W <= EDT_BAND_MAX_W && H <= EDT_BAND_MAX_H; }
+
 size_t distance_workspace_bytes(int32_t W, int32_t H) {
+    if (edt_banded(W, H)) return edt_env_layout(W, H).total;
     const size_t plane = ((size_t)W * H * sizeof(int32_t) + 255) / 256 * 256;
     return 2 * plane;
 }
 
-// Scratch: plane 0 = g (int32 per pixel); plane 1 = feature flags (bytes) during the
-// column pass, then the square-root table of the band row pass (or the envelope stacks of
-// the global-memory row pass).  The chunk summaries of the column pass live in d_out, which
-// the row pass overwrites entirely.
+// Scratch of the wide-map path (W > EDT_BAND_MAX_W or H > EDT_BAND_MAX_H): plane 0 = g (int32
+// per pixel); plane 1 = feature flags (bytes) during the column pass, then the envelope
+// stacks of the global-memory row pass.  The chunk summaries of the column pass live in
+// d_out, which the row pass overwrites entirely.
 cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double pixel,
                                 double* d_out, void* ws, cudaStream_t st) {
+    cudaError_t e;
+    if (edt_banded(W, H)) {
+        const EdtEnvLayout L = edt_env_layout(W, H);
+        char* base = (char*)ws;
+        unsigned long long* bits = (unsigned long long*)(base + L.bits);
+        int2* summ = (int2*)(base + L.summ);
+        int2* ab = (int2*)(base + L.ab);
+        double* sqtab = (double*)(base + L.sq);
+        const int nchunk = (H + EDT_BITS - 1) / EDT_BITS;
+        edt_bits_kernel<<<dim3((unsigned)((W + 127) / 128), (unsigned)nchunk), 128, 0, st>>>(ncc, W, H, bits, summ);
+        edt_chunk_scan_kernel<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(summ, W, nchunk, ab);
+        edt_sqrt_table_kernel<<<(unsigned)((EDT_SQRT_T + 255) / 256), 256, 0, st>>>(sqtab, EDT_SQRT_T);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const bool byte_stacks = (W + 31) / 32 <= 256;
+        const size_t smem = edt_env_smem(W, byte_stacks);
+        if (byte_stacks) {
+            e = cudaFuncSetAttribute(edt_row_env_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+            edt_row_env_kernel<uint8_t><<<(unsigned)H, 32, smem, st>>>(bits, ab, W, pixel, d_out, sqtab, EDT_SQRT_T);
+        } else {
+            e = cudaFuncSetAttribute(edt_row_env_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+            if (e != cudaSuccess) return e;
+            edt_row_env_kernel<uint16_t><<<(unsigned)H, 32, smem, st>>>(bits, ab, W, pixel, d_out, sqtab, EDT_SQRT_T);
+        }
+        return cudaGetLastError();
+    }
     const size_t plane = ((size_t)W * H * sizeof(int32_t) + 255) / 256 * 256;
     int32_t* g = (int32_t*)ws;
     int32_t* v = (int32_t*)((char*)ws + plane);
@@ -666,33 +953,14 @@ cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double
     const int nchunk = (H + EDT_CHUNK - 1) / EDT_CHUNK;
     const int64_t npx = (int64_t)W * H;
     edt_feature_kernel<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(ncc, W, H, feat);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 cg((unsigned)((W + 127) / 128), (unsigned)nchunk);
     edt_chunk_kernel<<<cg, 128, 0, st>>>(feat, W, H, summ);
     edt_column_kernel<<<cg, 128, 0, st>>>(feat, summ, W, H, nchunk, g);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (W <= EDT_BAND_MAX_W && H <= EDT_BAND_MAX_H) {
-        // square-root table in plane 1 (the row pass needs no stacks there)
-        const int T = (int)std::min<size_t>((size_t)EDT_SQRT_T, plane / sizeof(double));
-        double* sqtab = (double*)v;
-        edt_sqrt_table_kernel<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(sqtab, T);
-        const size_t smem = edt_band_smem(W);
-        if ((W + 31) / 32 <= 256) {
-            e = cudaFuncSetAttribute(edt_row_band_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            if (e != cudaSuccess) return e;
-            edt_row_band_kernel<uint8_t><<<(unsigned)H, 32, smem, st>>>(g, W, pixel, d_out, sqtab, T);
-        } else {
-            e = cudaFuncSetAttribute(edt_row_band_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            if (e != cudaSuccess) return e;
-            edt_row_band_kernel<uint16_t><<<(unsigned)H, 32, smem, st>>>(g, W, pixel, d_out, sqtab, T);
-        }
-    } else {
-        edt_row_kernel<<<(unsigned)((H + 63) / 64), 64, 0, st>>>(g, W, H, pixel, v, d_out);
-    }
+    edt_row_kernel<<<(unsigned)((H + 63) / 64), 64, 0, st>>>(g, W, H, pixel, v, d_out);
     return cudaGetLastError();
 }
 

@@ -43,7 +43,11 @@ def test_host_only_calls(lib):
     o = cc.cc_options_default()
     assert o.tol_abs == 1e-9 and o.precision == cc.CC_MIXED
     assert cc.cc_version().startswith("ccgpu")
-    assert cc.cc_distance_map_workspace_bytes(4096, 4096) >= 2 * 4096 * 4096 * 4
+    # banded maps: 64-row feature words, chunk summaries and neighbours (8 B each per chunk and
+    # column) and a 2^16-entry square-root table; wider maps keep two int32 planes
+    assert cc.cc_distance_map_workspace_bytes(4096, 4096) >= 64 * 4096 * 24 + 65536 * 8
+    assert cc.cc_distance_map_workspace_bytes(4096, 4096) < 4096 * 4096
+    assert cc.cc_distance_map_workspace_bytes(33000, 3) >= 2 * 33000 * 3 * 4
     with pytest.raises(cc.CCError) as e:
         cc.cc_distance_map_workspace_bytes(0, 5)
     assert e.value.status == cc.CC_EINVAL

@@ -160,8 +160,48 @@ def test_crossing_map_long_and_outside_segments():
     assert int(cc.crossing_map(empty, -1, 1, -1, 1, 8, 8).abs().sum()) == 0
 
 
+def test_crossing_map_near_ties_tiny_and_huge_segments():
+    """Segments whose crossings fall within 1e-12 to 1e-3 pixel of pixel centres, segments far
+    shorter than FP32 can resolve at |w| ~ 10, vertices with +0 and -0 ordinates, and
+    coordinates beyond 2^100: the FP32 fast path must hand every undecidable pair to the
+    exact predicate, and the counts stay equal to the oracle's."""
+    W = H = 512
+    x0, x1, y0, y1 = -10.0, 10.0, -10.0, 10.0
+    u = synth.uniform(4711, 6 * 3000)
+    cols = []
+    for t in range(3000):
+        r = int(u[6 * t] * H)
+        i = int(u[6 * t + 1] * W)
+        px = oracle.pixel_center(x0, x1, W, i)
+        py = oracle.pixel_center(y0, y1, H, r)
+        off = (u[6 * t + 2] - 0.5) * 10 ** (-12 + 9 * u[6 * t + 3]) * (x1 - x0) / W
+        length = 10 ** (-9 + 7 * u[6 * t + 4])
+        ang = 0.05 + 3.0 * u[6 * t + 5]
+        d = length * np.exp(1j * ang)
+        c = complex(px + off, py)
+        cols.append([c - 0.37 * d, c + 0.63 * d, c + 0.63 * d + 0.5 * length, c - 0.37 * d])
+    w = np.array(cols).T.copy()
+    ref = oracle.crossing_map(w, x0, x1, y0, y1, W, H)
+    got = cc.crossing_map(torch.from_numpy(w).cuda(), x0, x1, y0, y1, W, H).cpu().numpy()
+    assert np.array_equal(got, ref)
+    # +0 / -0 ordinates, a vertical edge through pixel centres, and huge coordinates
+    z0 = np.array([complex(0.0, 0.0), complex(0.3, -0.0), complex(0.3, 0.7), complex(0.0, 0.0)])
+    big = np.array([complex(-3e30, -0.25), complex(4e30, 0.75), complex(1e300, -1e300), complex(-3e30, -0.25)])
+    for ww in (z0[:, None], big[:, None], np.stack([z0, big], axis=1)):
+        ww = np.ascontiguousarray(ww)
+        ref = oracle.crossing_map(ww, -1, 1, -1, 1, 64, 48)
+        got = cc.crossing_map(torch.from_numpy(ww).cuda(), -1, 1, -1, 1, 64, 48).cpu().numpy()
+        assert np.array_equal(got, ref)
+
+
 @pytest.mark.parametrize("W,H,density", [(1, 1, 0.0), (1, 50, 0.05), (50, 1, 0.05), (64, 48, 0.01),
-                                         (200, 130, 0.001), (97, 101, 0.0)])
+                                         (200, 130, 0.001), (97, 101, 0.0),
+                                         # several 64-row feature words per column, ragged last word
+                                         (333, 321, 0.0005), (64, 64, 0.3), (31, 257, 0.002),
+                                         # distances beyond the square-root table (d^2 >= 2^16)
+                                         (700, 650, 0.000004),
+                                         # 16-bit hull stacks (W > 8192), and the wide-map path (W > 32768)
+                                         (9000, 5, 0.001), (33000, 3, 0.0005)])
 def test_distance_map_bit_exact(W, H, density):
     u = synth.uniform(77 + W * H, W * H).reshape(H, W)
     ncc = (u < density).astype(np.int32)
@@ -169,6 +209,20 @@ def test_distance_map_bit_exact(W, H, density):
     ref = oracle.distance_map(ncc, 0.0123)
     got = cc.distance_map(torch.from_numpy(ncc).cuda(), 0.0123).cpu().numpy()
     assert np.array_equal(got, ref)
+
+
+def test_distance_map_single_feature_and_checkerboard():
+    """A lone feature (distances up to the far corner, every column's nearest feature in
+    another 64-row word) and a map where every pixel is a feature."""
+    H, W = 517, 389
+    ncc = np.zeros((H, W), dtype=np.int32)
+    ncc[200, 100] = 1
+    ref = oracle.distance_map(ncc, 0.5)
+    got = cc.distance_map(torch.from_numpy(ncc).cuda(), 0.5).cpu().numpy()
+    assert np.array_equal(got, ref)
+    cb = (np.add.outer(np.arange(70), np.arange(90)) % 2).astype(np.int32)
+    got = cc.distance_map(torch.from_numpy(cb).cuda(), 0.25).cpu().numpy()
+    assert np.array_equal(got, oracle.distance_map(cb, 0.25)) and got.max() == 0.0
 
 
 def test_degenerate_and_invalid_arguments():
