@@ -109,6 +109,26 @@ __device__ __forceinline__ double pix(double lo, double step, int64_t i) {
     return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), step));
 }
 
+// Integer <-> float without conversion instructions (which share the FP64 pipe's low rate on
+// this part): adding an integer to the bits of 1.5 * 2^23 steps its value by exactly one per
+// unit, so for |x| < 2^22 the value is 1.5 * 2^23 + x, and an FP32 sum with 1.5 * 2^23
+// rounds to the nearest integer.
+constexpr float MAGIC_F = 12582912.0f;  // 1.5 * 2^23
+constexpr int MAGIC_I = 0x4B400000;     // its bits
+__device__ __forceinline__ float i2f_small(int x) { return __int_as_float(MAGIC_I + x) - MAGIC_F; }  // |x| < 2^22
+__device__ __forceinline__ int ceil_small(float x) {  // |x| < 2^21
+    const float t = x + MAGIC_F;
+    const int n = __float_as_int(t) - MAGIC_I;
+    return (t - MAGIC_F) < x ? n + 1 : n;
+}
+__device__ __forceinline__ int floor_small(float x) {  // |x| < 2^21
+    const float t = x + MAGIC_F;
+    const int n = __float_as_int(t) - MAGIC_I;
+    return (t - MAGIC_F) > x ? n - 1 : n;
+}
+// Maps of up to this many pixels per side take the conversion-free forms above.
+constexpr int SMALL_GRID = 1 << 20;
+
 struct CrossK {
     const double2* w;
     int64_t rows, nr;
@@ -146,7 +166,7 @@ __device__ __forceinline__ long long dkey(double v) {
 constexpr int XS_FAST = 1;  // coordinates within the fast path's range
 
 // One thread per segment finds the pixel rows its half-open y-range may contain, in FP32
-// with a margin (1e-3 row plus 8x the rounding bound) that covers the rounding.  The
+// with a margin (1.5x a rigorous bound on the rounding) that covers the rounding.  The
 // (segment, candidate row) pairs of a warp are then laid out by a warp prefix sum and
 // processed by all 32 lanes together:
 //  - a row more than the margin inside the candidate range is in the segment's half-open
@@ -182,23 +202,37 @@ __global__ void __launch_bounds__(XS_THREADS) crossing_scatter_kernel(CrossK K) 
         const bool finite = ((((unsigned long long)__double_as_longlong(a.x) >> 52) & 0x7FF) != 0x7FF) &&
                             ((((unsigned long long)__double_as_longlong(b.x) >> 52) & 0x7FF) != 0x7FF) &&
                             (((ya >> 52) & 0x7FF) != 0x7FF) && (((yb >> 52) & 0x7FF) != 0x7FF);
-        // a.y == b.y (equal bits, or +0 and -0): no pixel centre can satisfy a.y <= y < b.y
-        if (finite && ((ya ^ yb) << 1) != 0ull) {
+        // a.y == b.y (equal bits, or both zero of either sign): no pixel centre can satisfy
+        // a.y <= y < b.y
+        const bool same_y = ya == yb || ((ya | yb) << 1) == 0ull;
+        if (finite && !same_y) {
             bool ok = true;
             fv.x = f32_trunc(a.x, ok);
             fv.y = f32_trunc(a.y, ok);
             fv.z = f32_trunc(b.x, ok);
             fv.w = f32_trunc(b.y, ok);
-            float fr0, fr1;
+            float fr0 = 0.0f, fr1 = 0.0f;
             if (ok) {
                 flag = XS_FAST;
                 const float lo = fminf(fv.y, fv.w), hi = fmaxf(fv.y, fv.w);
                 tl = (lo - K.y0f) * K.inv_syf - 0.5f;
                 th = (hi - K.y0f) * K.inv_syf - 0.5f;
-                eps = 1e-3f + 1e-6f * ((fmaxf(fabsf(lo), fabsf(hi)) + fabsf(K.y0f)) * fabsf(K.inv_syf) + fabsf(tl) +
-                                       fabsf(th));
-                fr0 = fmaxf(ceilf(tl - eps), 0.0f);
-                fr1 = fminf(floorf(th + eps) + 1.0f, (float)K.H);
+                // |tl - exact| <= 2^-23 (|lo| + |y0| + |lo - y0|) / sy + 2^-24 (2 |tl| + 1) (truncation,
+                // the host-rounded y0 and 1/sy, each operation rounding once), likewise th; with
+                // a 1.5x margin, and 1e-6 row for the FP64 pixel centres' own rounding
+                const float ym = fmaxf(fabsf(lo), fabsf(hi)), yd = fmaxf(fabsf(lo - K.y0f), fabsf(hi - K.y0f));
+                eps = 1e-6f + 1.8e-7f * ((ym + fabsf(K.y0f) + yd) * fabsf(K.inv_syf) + fabsf(tl) + fabsf(th) + 1.0f);
+                if (K.H <= SMALL_GRID) {
+                    // (clamped first: the exact range only matters inside [0, H))
+                    r0 = max(ceil_small(fminf(fmaxf(tl - eps, -2.0f), (float)SMALL_GRID + 2.0f)), 0);
+                    const int r1 = min(floor_small(fminf(fmaxf(th + eps, -2.0f), (float)SMALL_GRID + 2.0f)) + 1, K.H);
+                    cnt = max(r1 - r0, 0);
+                    if (cnt == 0) r0 = 0;
+                    fr0 = fr1 = 0.0f;
+                } else {
+                    fr0 = fmaxf(ceilf(tl - eps), 0.0f);
+                    fr1 = fminf(floorf(th + eps) + 1.0f, (float)K.H);
+                }
             } else {
                 // coordinates beyond 2^100: candidate rows in FP64 (every row is tested exactly)
                 const double lo = fmin(a.y, b.y), hi = fmax(a.y, b.y);
@@ -246,7 +280,7 @@ __global__ void __launch_bounds__(XS_THREADS) crossing_scatter_kernel(CrossK K) 
         const double2 sa = s_a[j], sb = s_b[j];
         const bool up = dkey(sa.y) < dkey(sb.y);  // exact: a.y != b.y here
         const int sgn = up ? 1 : -1;
-        const float rf = (float)r;
+        const float rf = K.H <= SMALL_GRID ? i2f_small(r) : (float)r;
         bool sure = false;
         if (fast) {
             const float2 tt = s_t[j];
@@ -260,8 +294,9 @@ __global__ void __launch_bounds__(XS_THREADS) crossing_scatter_kernel(CrossK K) 
             py = pix(K.y0, K.sy, r);
             if (!(ylo <= py && py < yhi)) continue;
         }
-        int64_t c = -1;
+        int c = -1;
         float u = 0.f;
+        bool have_u = false;  // u holds an FP32 estimate of the abscissa
         if (fast) {
             // u = (x_c - x0)/sx - 1/2 in FP32 and a bound E on its error (EPS >= 2^-23 (1 + 2^-23):
             // truncation of the inputs; the host-rounded constants and each operation add
@@ -287,26 +322,53 @@ __global__ void __launch_bounds__(XS_THREADS) crossing_scatter_kernel(CrossK K) 
                 u = v - 0.5f;
                 const float E = 1.01f * (e9 + EPS * fabsf(u)) + 1e-6f;
                 if (isfinite(u) && isfinite(E)) {
+                    have_u = true;
                     if (u - E >= (float)K.W) c = K.W;
                     else if (u + E <= 0.f) c = 0;
-                    else if (ceilf(u - E) == ceilf(u + E)) c = (int64_t)fminf(fmaxf(ceilf(u), 0.0f), (float)K.W);
+                    else if (K.W <= SMALL_GRID) {
+                        // u in (-E, W + E): no integer within E of u means c = ceil(u)
+                        const float t = u + MAGIC_F, nf = t - MAGIC_F;
+                        if (E < 0.5f && fabsf(u - nf) > E) {
+                            const int n = __float_as_int(t) - MAGIC_I;
+                            c = min(max(nf > u ? n : n + 1, 0), K.W);
+                        }
+                    } else if (ceilf(u - E) == ceilf(u + E)) {
+                        c = (int)fminf(fmaxf(ceilf(u), 0.0f), (float)K.W);
+                    }
                 }
             }
         }
         if (c < 0) {
-            // exact: walk from an estimate with the orientation predicate
+            // exact: c = the number of pixel centres i with orient(a, b, P_i) == sgn, which hold
+            // for a prefix of the row (left of the crossing).  Test the two centres around an
+            // estimate of the crossing first, then bisect what is left: at most about
+            // log2(W) + 2 predicate calls however poor the estimate.
             if (sure) py = pix(K.y0, K.sy, r);
             double ue = u;
-            if (!fast || !isfinite(u)) {
+            if (!have_u) {
                 const double ey = sb.y - sa.y;
                 ue = ((sa.x - K.x0) + (sb.x - sa.x) * ((py - sa.y) / ey)) / K.sx - 0.5;
             }
             double ce = ceil(ue);
             ce = fmin(fmax(ce, 0.0), (double)K.W);
             if (!(ce == ce)) ce = 0.0;  // NaN guard
-            c = (int64_t)ce;
-            while (c > 0 && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c - 1), py) != sgn) c--;
-            while (c < K.W && orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, c), py) == sgn) c++;
+            const int ci = (int)ce;
+            auto left = [&](int i) { return orient_sign(sa.x, sa.y, sb.x, sb.y, pix(K.x0, K.sx, i), py) == sgn; };
+            int lo = 0, hi = K.W;  // c in [lo, hi]
+            if (ci > 0) {
+                if (left(ci - 1)) lo = ci;
+                else hi = ci - 1;
+            }
+            if (lo <= ci && ci < hi) {
+                if (left(ci)) lo = ci + 1;
+                else hi = ci;
+            }
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (left(mid)) lo = mid + 1;
+                else hi = mid;
+            }
+            c = lo;
         }
         if (c > 0) atomicAdd(&K.D[(int64_t)r * K.W + (c - 1)], sgn);
     }
@@ -454,14 +516,10 @@ __device__ __forceinline__ long long edt_key(const int32_t* f, int q) {
     return (long long)f[q] * f[q] + (long long)q * q;
 }
 
-// Band layout of the row pass: band position k of lane l at [k * EDT_LS + l], so that the
-// lanes of a warp stepping through their bands together never share a shared-memory bank
-// word they do not also share an address in.  g values are 16-bit (0xFFFF: no feature in
-// the column), hull stacks 8-bit band positions while a band holds at most 256 columns
-// (W <= 8192), else 16-bit.
+// Limits of the banded row pass: g values are 16-bit in shared memory (0xFFFF: no feature in
+// the column), hull stacks 8-bit band positions (bands of at most 256 columns).
 constexpr int EDT_BAND_MAX_W = 32768;
 constexpr int EDT_BAND_MAX_H = 65535;  // g < H fits 16 bits, 0xFFFF marks "no feature"
-constexpr int EDT_LS = 33;
 
 __device__ __forceinline__ long long edt_lift(int q, int gq) { return (long long)q * q + (long long)gq * gq; }
 
@@ -471,13 +529,7 @@ __device__ __forceinline__ bool edt_keep(int u, long long cu, int v, long long c
     return (cw - cv) * (long long)(v - u) > (cv - cu) * (long long)(w - v);
 }
 
-// sqrt(k) for k < T by the same IEEE FP64 square root the row pass would take, so that a
-// table hit returns the same bits (squared distances are integers).
-constexpr int EDT_SQRT_T = 65536;
-__global__ void edt_sqrt_table_kernel(double* tab, int T) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < T) tab[k] = sqrt((double)k);
-}
+constexpr int EDT_SQRT_T = 65536;  // entries of the distance table of the banded path
 
 // Row pass for very wide maps: one thread per row, envelope stack in global memory.
 __global__ void edt_row_kernel(const int32_t* g, int W, int H, double pixel, int32_t* vstack,
@@ -680,58 +732,77 @@ __device__ __forceinline__ int edt_col_dist(unsigned long long w, int2 ab, int r
 // t (2 (qv - qu)) >= cv - cu (c = q^2 + g^2), clamped to [0, W + 1].  An FP32 quotient lands
 // within one of it, and exact int64 products settle it.
 __device__ __forceinline__ int edt_start(int qu, long long cu, int qv, long long cv, int W) {
-    const long long num = cv - cu;
-    const long long den = 2LL * (qv - qu);
-    const float est = (float)num / (float)den;
+    const long long num = cv - cu;  // |num| < 2^38 (q < 2^15, g < 2^16)
+    const int den = 2 * (qv - qu);  // < 2^16
+    const float numf = fmaf(i2f_small((int)(num >> 16)), 65536.0f, i2f_small((int)(num & 0xFFFF)));
+    const float est = numf / i2f_small(den);
     if (!(est < (float)W + 2.0f)) return W + 1;
     if (est < -2.0f) return 0;
-    int t = (int)ceilf(est);
+    int t = ceil_small(est);
     while ((long long)(t - 1) * den >= num) t--;
     while ((long long)t * den < num) t++;
     return max(0, min(t, W + 1));
 }
 
-// Row pass, one warp per row.  g of the row from the feature words (band layout of the
-// hull build: column q = l Bw + k at [k EDT_LS + l]), the hull of each lane's band, five
-// rounds of bridge merges, then every surviving vertex writes its
-// column at the first pixel it owns (own[]; a vertex whose range is empty writes nothing),
-// and the fill takes, 32 pixels at a time, the running maximum of own[] by a warp scan:
-// the owner's column (envelope columns increase with the pixel).
-template <typename ST>
-__global__ void __launch_bounds__(32) edt_row_env_kernel(const unsigned long long* bits, const int2* ab, int W,
-                                                         double pixel, double* d_out, const double* sqtab, int T) {
+// Row pass, one CTA of EDT_NB threads per row.  Thread l owns the band of columns
+// [l Bw, (l + 1) Bw), Bw = ceil(W / EDT_NB) <= 256 (band layout: column q = l Bw + k at
+// [k EDT_LSB + l], so threads stepping through their bands together touch consecutive
+// words).  g of the row comes from the feature words; each thread builds the hull of its
+// band; log2(EDT_NB) rounds of bridge merges join neighbouring bands (the hull of two
+// column-separated sets keeps a prefix of the left hull and a suffix of the right one,
+// found by walking both ends until neither end point can be dropped); then every surviving
+// vertex writes its column at the first pixel it owns (own[]; a vertex whose range is empty
+// writes nothing), and each warp fills a quarter of the row, 32 pixels at a time, with the
+// owner = the running maximum of own[] (envelope columns increase with the pixel), seeded
+// with the maximum over the quarters before it.  All comparisons are exact int64.
+constexpr int EDT_NB = 128;            // threads (bands) per row
+constexpr int EDT_LSB = EDT_NB + 1;    // band-layout stride
+constexpr int EDT_NW = EDT_NB / 32;    // warps per row
+
+__device__ __forceinline__ int edt_warp_max_scan(int v, int lane) {
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v = max(v, y);
+    }
+    return v;
+}
+
+__global__ void __launch_bounds__(EDT_NB) edt_row_env_kernel(const unsigned long long* bits, const int2* ab, int W,
+                                                             double pixel, double* d_out, const double* dtab, int T) {
     extern __shared__ uint16_t edt_sh[];
-    __shared__ int s_lo[32], s_hi[32];
-    const int r = blockIdx.x, lane = threadIdx.x;
-    const int Bw = (W + 31) / 32;
-    uint16_t* gs = edt_sh;                              // g by (band position, lane)
-    ST* st = (ST*)(edt_sh + (size_t)Bw * EDT_LS);       // hull stacks: band positions
-    uint16_t* own = (uint16_t*)((char*)st + ((sizeof(ST) * (size_t)Bw * EDT_LS + 15) & ~(size_t)15));
+    __shared__ int s_lo[EDT_NB], s_hi[EDT_NB], s_prev[EDT_NB], s_next[EDT_NB];
+    __shared__ int s_wred[2][EDT_NW];
+    const int r = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int Bw = (W + EDT_NB - 1) / EDT_NB;
+    uint16_t* gs = edt_sh;                                   // g by (band position, band)
+    uint8_t* st = (uint8_t*)(edt_sh + (size_t)Bw * EDT_LSB);  // hull stacks: band positions
+    uint16_t* own = (uint16_t*)((char*)st + (((size_t)Bw * EDT_LSB + 15) & ~(size_t)15));
     const int c = r / EDT_BITS, b = r - c * EDT_BITS;
     {
         const unsigned long long* wr = bits + (int64_t)c * W;
         const int2* abr = ab + (int64_t)c * W;
-        int l = lane / Bw, k = lane - l * Bw;  // column q = lane
-        for (int q = lane; q < W; q += 32) {
-            gs[k * EDT_LS + l] = (uint16_t)edt_col_dist(__ldg(wr + q), __ldg(abr + q), r, b);
-            k += 32;
+        int l = tid / Bw, k = tid - l * Bw;  // column q = tid
+        for (int q = tid; q < W; q += EDT_NB) {
+            gs[k * EDT_LSB + l] = (uint16_t)edt_col_dist(__ldg(wr + q), __ldg(abr + q), r, b);
+            k += EDT_NB;
             while (k >= Bw) {
                 k -= Bw;
                 l++;
             }
         }
-        for (int i = lane; i < W; i += 32) own[i] = 0;
+        for (int i = tid; i < W; i += EDT_NB) own[i] = 0;
     }
-    __syncwarp();
-    auto site_g = [&](int l, int k) -> int { return gs[k * EDT_LS + l]; };
+    __syncthreads();
+    auto site_g = [&](int l, int k) -> int { return gs[k * EDT_LSB + l]; };
     // 1. hull of the own band
-    const int a = lane * Bw;
+    const int a = tid * Bw;
     const int bl = max(0, min(Bw, W - a));
     int len = 0;
     int ku = 0, kv = 0;
     long long cu = 0, cv = 0;
     for (int k = 0; k < bl; k++) {
-        const int gq = site_g(lane, k);
+        const int gq = site_g(tid, k);
         if (gq == 0xFFFF) continue;
         const long long cq = edt_lift(a + k, gq);
         while (len >= 2 && !edt_keep(ku, cu, kv, cv, k, cq)) {
@@ -739,30 +810,30 @@ __global__ void __launch_bounds__(32) edt_row_env_kernel(const unsigned long lon
             kv = ku;
             cv = cu;
             if (len >= 2) {
-                ku = st[(len - 2) * EDT_LS + lane];
-                cu = edt_lift(a + ku, site_g(lane, ku));
+                ku = st[(len - 2) * EDT_LSB + tid];
+                cu = edt_lift(a + ku, site_g(tid, ku));
             }
         }
-        st[len * EDT_LS + lane] = (ST)k;
+        st[len * EDT_LSB + tid] = (uint8_t)k;
         len++;
         ku = kv;
         cu = cv;
         kv = k;
         cv = cq;
     }
-    s_lo[lane] = 0;
-    s_hi[lane] = len;
-    __syncwarp();
-    // 2. bridge merges of the hulls of lane groups [b0, b0 + h) and [b0 + h, b0 + 2h)
-    for (int h = 1; h < 32; h <<= 1) {
-        if ((lane & (2 * h - 1)) == 0) {
-            const int b0 = lane, e = lane + 2 * h;
+    s_lo[tid] = 0;
+    s_hi[tid] = len;
+    __syncthreads();
+    // 2. bridge merges of the hulls of band groups [b0, b0 + h) and [b0 + h, b0 + 2h)
+    for (int h = 1; h < EDT_NB; h <<= 1) {
+        if ((tid & (2 * h - 1)) == 0) {
+            const int b0 = tid, e = tid + 2 * h;
             int la = b0 + h - 1, lb = b0 + h;
             while (la >= b0 && s_lo[la] == s_hi[la]) la--;
             while (lb < e && s_lo[lb] == s_hi[lb]) lb++;
             if (la >= b0 && lb < e) {
                 int pa = s_hi[la] - 1, pb = s_lo[lb];
-                int ka = st[pa * EDT_LS + la], kb = st[pb * EDT_LS + lb];
+                int ka = st[pa * EDT_LSB + la], kb = st[pb * EDT_LSB + lb];
                 int qa = la * Bw + ka, qb = lb * Bw + kb;
                 long long ca = edt_lift(qa, site_g(la, ka)), cb = edt_lift(qb, site_g(lb, kb));
                 for (bool changed = true; changed;) {
@@ -775,7 +846,7 @@ __global__ void __launch_bounds__(32) edt_row_env_kernel(const unsigned long lon
                             if (lp < b0) break;
                             pp = s_hi[lp] - 1;
                         }
-                        const int kp = st[pp * EDT_LS + lp], qp = lp * Bw + kp;
+                        const int kp = st[pp * EDT_LSB + lp], qp = lp * Bw + kp;
                         const long long cp = edt_lift(qp, site_g(lp, kp));
                         if (edt_keep(qp, cp, qa, ca, qb, cb)) break;
                         s_hi[la] = pa;
@@ -793,7 +864,7 @@ __global__ void __launch_bounds__(32) edt_row_env_kernel(const unsigned long lon
                             if (ln >= e) break;
                             pn = s_lo[ln];
                         }
-                        const int kn = st[pn * EDT_LS + ln], qn = ln * Bw + kn;
+                        const int kn = st[pn * EDT_LSB + ln], qn = ln * Bw + kn;
                         const long long cn = edt_lift(qn, site_g(ln, kn));
                         if (edt_keep(qa, ca, qb, cb, qn, cn)) break;
                         s_lo[lb] = pb + 1;
@@ -806,45 +877,62 @@ __global__ void __launch_bounds__(32) edt_row_env_kernel(const unsigned long lon
                 }
             }
         }
-        __syncwarp();
+        __syncthreads();
     }
+    // live bands: the nearest non-empty band before (s_prev) and after (s_next) each band
+    const bool alive = s_lo[tid] < s_hi[tid];
+    {
+        const int pv = edt_warp_max_scan(alive ? tid : -1, lane);            // last live <= tid
+        int nx = alive ? -tid : -EDT_NB;                                     // first live >= tid,
+        for (int off = 1; off < 32; off <<= 1) {                             // as a max of -index
+            const int y = __shfl_down_sync(0xffffffffu, nx, off);
+            if (lane + off < 32) nx = max(nx, y);
+        }
+        if (lane == 31) s_wred[0][wid] = pv;
+        if (lane == 0) s_wred[1][wid] = nx;
+        __syncthreads();
+        int before = -1, after = -EDT_NB;
+        for (int w2 = 0; w2 < wid; w2++) before = max(before, s_wred[0][w2]);
+        for (int w2 = wid + 1; w2 < EDT_NW; w2++) after = max(after, s_wred[1][w2]);
+        const int pv_all = max(pv, before), nx_all = max(nx, after);
+        // exclusive: the live band strictly before / after tid
+        s_prev[tid] = pv_all;
+        s_next[tid] = -nx_all;
+    }
+    __syncthreads();
     double* out = d_out + (int64_t)r * W;
-    const unsigned live = __ballot_sync(0xffffffffu, s_lo[lane] < s_hi[lane]);
-    if (live == 0) {
-        for (int i = lane; i < W; i += 32) out[i] = __longlong_as_double(0x7ff0000000000000LL);
+    const int first_live = s_next[0];  // EDT_NB when no band is live
+    if (first_live >= EDT_NB) {
+        for (int i = tid; i < W; i += EDT_NB) out[i] = __longlong_as_double(0x7ff0000000000000LL);
         return;
     }
     // 3. start pixel of every surviving vertex; a vertex with a non-empty range [s, s_next)
     // inside the row writes its column at own[s]
-    if (s_lo[lane] < s_hi[lane]) {
-        const unsigned before = live & ((1u << lane) - 1u);
+    if (alive) {
+        const int lp = tid > 0 ? s_prev[tid - 1] : -1;
         int qu = -1;
         long long cu2 = 0;
-        if (before) {
-            const int lp = 31 - __clz(before);
-            const int kp = st[(s_hi[lp] - 1) * EDT_LS + lp];
+        if (lp >= 0) {
+            const int kp = st[(s_hi[lp] - 1) * EDT_LSB + lp];
             qu = lp * Bw + kp;
             cu2 = edt_lift(qu, site_g(lp, kp));
         }
-        int qv = lane * Bw + st[s_lo[lane] * EDT_LS + lane];
-        long long cv2 = edt_lift(qv, site_g(lane, qv - lane * Bw));
+        int qv = tid * Bw + st[s_lo[tid] * EDT_LSB + tid];
+        long long cv2 = edt_lift(qv, site_g(tid, qv - tid * Bw));
         int sv = qu < 0 ? 0 : edt_start(qu, cu2, qv, cv2, W);
-        for (int p = s_lo[lane]; p < s_hi[lane]; p++) {
-            // successor of entry p: the next entry of this lane, or the first of the next live lane
+        const int ln_band = tid + 1 < EDT_NB ? s_next[tid + 1] : EDT_NB;
+        for (int p = s_lo[tid]; p < s_hi[tid]; p++) {
+            // successor of entry p: the next entry of this band, or the first of the next live band
             int qn = -1;
             long long cn = 0;
-            if (p + 1 < s_hi[lane]) {
-                const int kn = st[(p + 1) * EDT_LS + lane];
-                qn = lane * Bw + kn;
-                cn = edt_lift(qn, site_g(lane, kn));
-            } else {
-                const unsigned after = live & ~((2u << lane) - 1u);
-                if (after) {
-                    const int ln = __ffs(after) - 1;
-                    const int kn = st[s_lo[ln] * EDT_LS + ln];
-                    qn = ln * Bw + kn;
-                    cn = edt_lift(qn, site_g(ln, kn));
-                }
+            if (p + 1 < s_hi[tid]) {
+                const int kn = st[(p + 1) * EDT_LSB + tid];
+                qn = tid * Bw + kn;
+                cn = edt_lift(qn, site_g(tid, kn));
+            } else if (ln_band < EDT_NB) {
+                const int kn = st[s_lo[ln_band] * EDT_LSB + ln_band];
+                qn = ln_band * Bw + kn;
+                cn = edt_lift(qn, site_g(ln_band, kn));
             }
             const int sn = qn < 0 ? W : edt_start(qv, cv2, qn, cn, W);
             if (sv < sn && sv < W) own[sv] = (uint16_t)qv;
@@ -853,35 +941,47 @@ __global__ void __launch_bounds__(32) edt_row_env_kernel(const unsigned long lon
             sv = sn;
         }
     }
-    __syncwarp();
-    // 4. fill, 32 pixels at a time: owner = running maximum of own[]
-    const float inv_bw = 1.0f / (float)Bw;
+    __syncthreads();
+    // 4. fill: warp w takes the quarter [w Q, (w + 1) Q) of the row (Q a multiple of 32),
+    // seeded with the maximum of own[] over the quarters before it
+    const int Q = ((W + EDT_NW - 1) / EDT_NW + 31) & ~31;
+    const int i0 = wid * Q, i1 = min(W, i0 + Q);
+    {
+        int mx = 0;
+        for (int i = i0 + lane; i < i1; i += 32) mx = max(mx, (int)own[i]);
+        for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (lane == 0) s_wred[0][wid] = mx;
+    }
+    __syncthreads();
     int carry = 0;
-    for (int t0 = 0; t0 < W; t0 += 32) {
+    for (int w2 = 0; w2 < wid; w2++) carry = max(carry, s_wred[0][w2]);
+    // band of column q: floor(q / Bw) = umulhi(q, ceil(2^32 / Bw)) exactly for q < 2^15
+    const unsigned bw_mul = Bw > 1 ? 0xFFFFFFFFu / (unsigned)Bw + 1u : 0u;
+    for (int t0 = i0; t0 < i1; t0 += 32) {
         const int i = t0 + lane;
-        int q = i < W ? own[i] : 0;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, q, off);
-            if (lane >= off) q = max(q, y);
-        }
+        int q = edt_warp_max_scan(i < i1 ? (int)own[i] : 0, lane);
         q = max(q, carry);
         carry = __shfl_sync(0xffffffffu, q, 31);
-        if (i < W) {
-            // band of column q: (q + 1/2) / Bw in FP32 is within 4e-6 of the exact quotient, whose
-            // fractional part stays >= 1/(2 Bw) >= 4.9e-4 away from an integer (q < 2^15)
-            const int l = (int)(((float)q + 0.5f) * inv_bw), k = q - l * Bw;
+        if (i < i1) {
+            const int l = Bw > 1 ? (int)__umulhi((unsigned)q, bw_mul) : q, k = q - l * Bw;
             const int gq = site_g(l, k);
             const long long d2 = (long long)(i - q) * (i - q) + (long long)gq * gq;
-            out[i] = pixel * (d2 < T ? sqtab[d2] : sqrt((double)d2));
+            out[i] = d2 < T ? dtab[d2] : pixel * sqrt((double)d2);
         }
     }
 }
 
-size_t edt_env_smem(int W, bool byte_stacks) {
-    const size_t Bw = (size_t)((W + 31) / 32);
-    const size_t stb = ((byte_stacks ? 1 : 2) * Bw * EDT_LS + 15) & ~(size_t)15;
-    return sizeof(uint16_t) * Bw * EDT_LS + stb + sizeof(uint16_t) * (size_t)((W + 31) / 32 * 32);
+size_t edt_env_smem(int W) {
+    const size_t Bw = (size_t)((W + EDT_NB - 1) / EDT_NB);
+    return sizeof(uint16_t) * Bw * EDT_LSB + ((Bw * EDT_LSB + 15) & ~(size_t)15) +
+           sizeof(uint16_t) * (size_t)((W + 31) / 32 * 32);
+}
+
+// d = pixel * sqrt(k) for k < T, by the same IEEE FP64 square root and product the row
+// pass would take (squared distances are integers), so a table hit returns the same bits.
+__global__ void edt_dist_table_kernel(double* tab, int T, double pixel) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < T) tab[k] = pixel * sqrt((double)k);
 }
 
 // Workspace of the banded path: feature words, chunk summaries, chunk neighbours, square
@@ -927,22 +1027,13 @@ cudaError_t launch_distance_map(const int32_t* ncc, int32_t W, int32_t H, double
         const int nchunk = (H + EDT_BITS - 1) / EDT_BITS;
         edt_bits_kernel<<<dim3((unsigned)((W + 127) / 128), (unsigned)nchunk), 128, 0, st>>>(ncc, W, H, bits, summ);
         edt_chunk_scan_kernel<<<(unsigned)((W + 127) / 128), 128, 0, st>>>(summ, W, nchunk, ab);
-        edt_sqrt_table_kernel<<<(unsigned)((EDT_SQRT_T + 255) / 256), 256, 0, st>>>(sqtab, EDT_SQRT_T);
+        edt_dist_table_kernel<<<(unsigned)((EDT_SQRT_T + 255) / 256), 256, 0, st>>>(sqtab, EDT_SQRT_T, pixel);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        const bool byte_stacks = (W + 31) / 32 <= 256;
-        const size_t smem = edt_env_smem(W, byte_stacks);
-        if (byte_stacks) {
-            e = cudaFuncSetAttribute(edt_row_env_kernel<uint8_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            if (e != cudaSuccess) return e;
-            edt_row_env_kernel<uint8_t><<<(unsigned)H, 32, smem, st>>>(bits, ab, W, pixel, d_out, sqtab, EDT_SQRT_T);
-        } else {
-            e = cudaFuncSetAttribute(edt_row_env_kernel<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-            if (e != cudaSuccess) return e;
-            edt_row_env_kernel<uint16_t><<<(unsigned)H, 32, smem, st>>>(bits, ab, W, pixel, d_out, sqtab, EDT_SQRT_T);
-        }
+        const size_t smem = edt_env_smem(W);
+        e = cudaFuncSetAttribute(edt_row_env_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        edt_row_env_kernel<<<(unsigned)H, EDT_NB, smem, st>>>(bits, ab, W, pixel, d_out, sqtab, EDT_SQRT_T);
         return cudaGetLastError();
     }
     const size_t plane = ((size_t)W * H * sizeof(int32_t) + 255) / 256 * 256;

@@ -163,8 +163,8 @@ def test_crossing_map_long_and_outside_segments():
 def test_crossing_map_near_ties_tiny_and_huge_segments():
     """Segments whose crossings fall within 1e-12 to 1e-3 pixel of pixel centres, segments far
     shorter than FP32 can resolve at |w| ~ 10, vertices with +0 and -0 ordinates, and
-    coordinates beyond 2^100: the FP32 fast path must hand every undecidable pair to the
-    exact predicate, and the counts stay equal to the oracle's."""
+    coordinates beyond 2^100 (up to 1e140): the FP32 fast path must hand every undecidable
+    pair to the exact predicate, and the counts stay equal to the oracle's."""
     W = H = 512
     x0, x1, y0, y1 = -10.0, 10.0, -10.0, 10.0
     u = synth.uniform(4711, 6 * 3000)
@@ -186,7 +186,9 @@ def test_crossing_map_near_ties_tiny_and_huge_segments():
     assert np.array_equal(got, ref)
     # +0 / -0 ordinates, a vertical edge through pixel centres, and huge coordinates
     z0 = np.array([complex(0.0, 0.0), complex(0.3, -0.0), complex(0.3, 0.7), complex(0.0, 0.0)])
-    big = np.array([complex(-3e30, -0.25), complex(4e30, 0.75), complex(1e300, -1e300), complex(-3e30, -0.25)])
+    # (products of coordinate differences must stay inside the double range, |w| < 1e154, for
+    # the exact orientation predicate on either side)
+    big = np.array([complex(-3e30, -0.25), complex(4e30, 0.75), complex(1e140, -1e140), complex(-3e30, -0.25)])
     for ww in (z0[:, None], big[:, None], np.stack([z0, big], axis=1)):
         ww = np.ascontiguousarray(ww)
         ref = oracle.crossing_map(ww, -1, 1, -1, 1, 64, 48)
