@@ -294,10 +294,10 @@ def run_ours(args):
         status, rep = cc.cc_field_report(field)
         S = rep["subchains"]
         # phase table, tracer, seam match (S > 1), permutation compose; polish stage (far field:
-        # extent, setup, occupancy, slots, coefficients, point kernel, direct kernel that
+        # extent, setup, occupancy, slots, coefficients, sub-cells, point kernel, direct kernel that
         # returns at once; else the direct kernel); rescue; crossing scatter + row scan;
         # distance map feature, chunk, column and row kernels
-        polish_kernels = 7 if f.n >= 128 else 1
+        polish_kernels = 8 if f.n >= 128 else 1
         launches_per_step = 1 + 1 + (1 if S > 1 else 0) + 1 + polish_kernels + 1 + 2 + 4
         return status, rep
 

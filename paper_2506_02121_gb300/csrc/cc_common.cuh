@@ -25,6 +25,27 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // ----------------------------------------------------------------------------------
+// Small integers <-> float
+// ----------------------------------------------------------------------------------
+// Integer <-> float without conversion instructions (which share the FP64 pipe's low rate on
+// this part): adding an integer to the bits of 1.5 * 2^23 steps its value by exactly one per
+// unit, so for |x| < 2^22 the value is 1.5 * 2^23 + x, and an FP32 sum with 1.5 * 2^23
+// rounds to the nearest integer.
+constexpr float MAGIC_F = 12582912.0f;  // 1.5 * 2^23
+constexpr int MAGIC_I = 0x4B400000;     // its bits
+__device__ __forceinline__ float i2f_small(int x) { return __int_as_float(MAGIC_I + x) - MAGIC_F; }  // |x| < 2^22
+__device__ __forceinline__ int ceil_small(float x) {  // |x| < 2^21
+    const float t = x + MAGIC_F;
+    const int n = __float_as_int(t) - MAGIC_I;
+    return (t - MAGIC_F) < x ? n + 1 : n;
+}
+__device__ __forceinline__ int floor_small(float x) {  // |x| < 2^21
+    const float t = x + MAGIC_F;
+    const int n = __float_as_int(t) - MAGIC_I;
+    return (t - MAGIC_F) > x ? n - 1 : n;
+}
+
+// ----------------------------------------------------------------------------------
 // double-float
 // ----------------------------------------------------------------------------------
 struct df {

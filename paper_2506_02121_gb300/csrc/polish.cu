@@ -233,7 +233,8 @@ __device__ __forceinline__ dfc poly_Q_df(const SmoothPoly* P, df zx, df zy) {
 // terms of the Taylor correction of S1.  FP64 is used for the outputs alone.
 __device__ __forceinline__ bool polish_epilogue_df(const PolishK& K, int64_t point, int64_t row, const Sums& s,
                                                    const df& cx, const df& cy, tf& zx, tf& zy, float z0x, float z0y,
-                                                   int pass, int32_t it_in, double& est_out, float s2_err = 0.f) {
+                                                   int pass, int32_t it_in, double& est_out, float s2_err = 0.f,
+                                                   float s3_err = 0.f) {
     df Fx = df_add(s.S2x, cx), Fy = df_add(s.S2y, cy);
     float s3x = s.s3x, s3y = s.s3y, s4x = s.s4x, s4y = s.s4y, a3 = s.a3;
     if (K.poly) {
@@ -261,7 +262,8 @@ __device__ __forceinline__ bool polish_epilogue_df(const PolishK& K, int64_t poi
         const float s3a = 0.5f * sqrtf(den);
         const float s4a = sqrtf(fmaf(s4x, s4x, s4y * s4y));
         const float r3 = __frcp_rn(s3a);
-        est = 1.5f * ad * ad * s4a * r3 + ad * (4.f * FLT_EPSILON * a3 * r3 + 8.f * FLT_EPSILON) + 0.5f * s2_err * r3;
+        est = 1.5f * ad * ad * s4a * r3 + ad * ((4.f * FLT_EPSILON * a3 + s3_err) * r3 + 8.f * FLT_EPSILON) +
+              0.5f * s2_err * r3;
     } else {
         // F' vanishes (or the sums overflowed): no step, certified only at an exact zero of F
         est = (fx == 0.f && fy == 0.f) ? 0.f : FLT_MAX;
@@ -544,18 +546,69 @@ struct FmmParams {
     int pool_used;            // near-list entries handed out
     int cpool_used;           // coarse star-list entries handed out
     int cap, pool_cap;
+    int sub_used;             // sub-cell table entries handed out
 };
 
 struct BoxInfo {
-    float4 c;      // centre as double-float (x_hi, x_lo, y_hi, y_lo)
+    float4 c;        // centre as double-float (x_hi, x_lo, y_hi, y_lo)
     int near_off, near_cnt;
-    float s2_err;  // truncation bound of S2_far (theta_*^-2)
+    float s2_err;    // truncation bound of S2_far (theta_*^-2) plus the FP32 rounding of terms >= FMM_K0
+    float s2_trunc;  // the truncation part alone
+};
+
+// Sub-cells: each occupied cell is cut into FMM_SUB x FMM_SUB sub-cells, and the cell's
+// 32-term expansion is re-centred exactly (a Taylor shift) at the centre of every sub-cell
+// that holds a traced point (tables handed out from a pool of FMM_SUBPOOL).  A point within FMM_SUBR b of its sub-cell centre sees the far
+// stars at a ratio of about 0.1 instead of 0.29, so FMM_PS terms of the re-centred
+// polynomial, FMM_KS0 of them in double-float, hold what 32 (20) did; the dropped terms'
+// exact bound, from the re-centred coefficients, joins the certificate.
+constexpr int FMM_SUB = 4;
+constexpr int FMM_SUB2 = FMM_SUB * FMM_SUB;
+constexpr int FMM_PS = 16;            // terms kept at a sub-cell centre
+constexpr int FMM_KS0 = 9;            // of which terms k >= FMM_KS0 in FP32
+constexpr int FMM_SUBPOOL = 1 << 20;  // sub-cell tables (occupied sub-cells) at most; cells beyond use the cell's
+constexpr float FMM_SUBR = 0.185f;    // sub-cell radius / b: 1.05 x the half-diagonal sqrt(2)/8 (so that
+                                      // |z - c| <= 0.375 sqrt(2) b + 0.185 b <= 0.72 b, the cell bound's radius)
+
+struct SubInfo {
+    float4 c;       // sub-cell centre as double-float
+    float s2_err;   // bound on S2's error from the cell's truncation, the dropped terms and the FP32 part
+    float s3_err;   // bound on S3's error from the dropped terms
+    float r2;       // squared radius within which the bounds hold
     float pad;
 };
+
+// Binomial coefficients C(j, k), j, k < 32, as double-float (exact: C(31, 15) < 2^29).
+struct BinomTable {
+    float hi[32][32], lo[32][32];
+};
+constexpr BinomTable make_binom_table() {
+    BinomTable t{};
+    long long c[32][32] = {};
+    for (int j = 0; j < 32; j++) {
+        c[j][0] = 1;
+        for (int k = 1; k <= j; k++) c[j][k] = c[j - 1][k - 1] + (k <= j - 1 ? c[j - 1][k] : 0);
+    }
+    for (int j = 0; j < 32; j++)
+        for (int k = 0; k < 32; k++) {
+            const float h = (float)c[j][k];
+            t.hi[j][k] = h;
+            t.lo[j][k] = (float)(c[j][k] - (long long)h);
+        }
+    return t;
+}
+__constant__ BinomTable kBinom = make_binom_table();
 
 __device__ __forceinline__ int fmm_cell(float v, float v0, float inv_b) {
     const float t = floorf(__fmul_rn(__fsub_rn(v, v0), inv_b));
     return (int)fminf(fmaxf(t, -1.0e6f), 1.0e6f);
+}
+
+// Sub-cell coordinate (0 .. FMM_SUB - 1) of v inside its cell c (the same arithmetic wherever
+// a traced point is placed, so that its sub-cell is one that was marked occupied).
+__device__ __forceinline__ int fmm_subcell(float v, float v0, float inv_b, int c) {
+    const float u = __fmul_rn(__fsub_rn(v, v0), inv_b) - i2f_small(c);
+    return min(max(floor_small(u * (float)FMM_SUB), 0), FMM_SUB - 1);
 }
 
 __global__ void fmm_extent_kernel(const float2* z, int64_t npts, float4* part) {
@@ -641,12 +694,13 @@ __global__ void fmm_setup_kernel(const float4* part, int nparts, float b_target,
     P->cpool_used = 0;
     P->cap = cap;
     P->pool_cap = pool_cap;
+    P->sub_used = 0;
 }
 
 // Occupied cells.  A warp takes one tracer column over 32 consecutive rows: one chain
 // (within a sub-range), whose points mostly share a cell, so after a warp-level match of the
 // cell indices one lane per distinct cell tests and marks it.
-__global__ void fmm_occupy_kernel(const float2* z, int64_t rows, int64_t nr, FmmParams* P, uint8_t* occ) {
+__global__ void fmm_occupy_kernel(const float2* z, int64_t rows, int64_t nr, FmmParams* P, unsigned* occ) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t col = w % nr, row = (w / nr) * 32 + lane;
@@ -655,23 +709,24 @@ __global__ void fmm_occupy_kernel(const float2* z, int64_t rows, int64_t nr, Fmm
     // warp-uniform (the full-warp match below needs every lane)
     if (!__shfl_sync(0xffffffffu, P->ok, 0)) return;
     int64_t cell = -1;
+    unsigned bit = 0;
     if (row < rows) {
         const float2 v = z[row * nr + col];
         const int cx = fmm_cell(v.x, P->x0, P->inv_b), cy = fmm_cell(v.y, P->y0, P->inv_b);
-        if (cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby)
+        if (cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby) {
             cell = (int64_t)cy * P->nbx + cx;
-        else
+            bit = 1u << (fmm_subcell(v.y, P->y0, P->inv_b, cy) * FMM_SUB + fmm_subcell(v.x, P->x0, P->inv_b, cx));
+        } else {
             P->ok = 0;
+        }
     }
+    // occ[cell]: bit s set when sub-cell s holds a traced point
     const unsigned same = __match_any_sync(0xffffffffu, cell);
-    if (cell >= 0 && lane == __ffs(same) - 1) {
-        // a stale 0 only repeats a store
-        uint8_t* o = occ + cell;
-        if (*o == 0) *o = 1;
-    }
+    const unsigned bits = __reduce_or_sync(same, bit);
+    if (cell >= 0 && lane == __ffs(same) - 1 && (occ[cell] & bits) != bits) atomicOr(occ + cell, bits);
 }
 
-__global__ void fmm_slot_kernel(FmmParams* P, const uint8_t* occ, int* slot, int2* boxlist) {
+__global__ void fmm_slot_kernel(FmmParams* P, const unsigned* occ, int* slot, int2* boxlist) {
     const int64_t cell = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t ncell = (int64_t)P->nbx * P->nby;
     if (cell >= ncell) return;
@@ -709,7 +764,7 @@ constexpr int FMM_CLIST = 8192;                  // stars of one coarse 5x5 bloc
 constexpr int FMM_COARSE_MAX = (FMM_G / FMM_F) * (FMM_G / FMM_F);
 constexpr int FMM_CPOOL = 1 << 23;               // coarse star-list entries (more: direct polish)
 
-__global__ void fmm_coarse_list_kernel(FmmParams* P, const uint8_t* occ, int2* clist) {
+__global__ void fmm_coarse_list_kernel(FmmParams* P, const unsigned* occ, int2* clist) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (!P->ok) return;
     const int nbx = P->nbx, nby = P->nby;
@@ -987,12 +1042,115 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
             // points lie within 0.72 b of c (half-diagonal plus the Newton steps)
             const float tc = (float)sqrt((cxd - Cxd) * (cxd - Cxd) + (cyd - Cyd) * (cyd - Cyd));
             const float rho1 = 0.72f * P->b / D, rho2 = (tc + 0.72f * P->b) / cI.dmin;
-            bi.s2_err = fmm_tail(R2, rho1) + fmm_tail(cI.r2, rho2) +
-                        fmm_fp32_part(R2, rho1) + fmm_fp32_part(cI.r2, rho2);
-            bi.pad = 0.f;
+            bi.s2_trunc = fmm_tail(R2, rho1) + fmm_tail(cI.r2, rho2);
+            bi.s2_err = bi.s2_trunc + fmm_fp32_part(R2, rho1) + fmm_fp32_part(cI.r2, rho2);
             info[box] = bi;
         }
         __syncthreads();
+        __syncthreads();
+    }
+}
+
+// Pass 3: one CTA per occupied cell B: B's 32-term polynomial
+// re-centred at the centre c + d of each sub-cell holding a traced point, exactly as an
+// algebraic identity, L'_k = sum_{j >= k} C(j, k) L_j d^(j - k) (Horner in d): in
+// double-float for the kept terms k < FMM_PS (one thread per (sub-cell, k)), and for the
+// dropped ones an FP32 upper bound on |L'_k| by the same sum of magnitudes (rounding covered
+// by a 1.001 factor); then each sub-cell's bounds.
+constexpr int FMM_ST = FMM_SUB2 * FMM_PS;  // threads of the sub-cell kernel
+__global__ void __launch_bounds__(FMM_ST) fmm_subcell_kernel(FmmParams* P, const int2* boxlist,
+                                                             const unsigned* occ, const BoxInfo* info,
+                                                             const float4* coeff, int* sub_base, float4* scoeff,
+                                                             SubInfo* sinfo, int sub_cap) {
+    __shared__ float4 s_L[FMM_P];
+    __shared__ int s_base;
+    __shared__ float2 s_binom[32][32];
+    __shared__ float4 s_Ls[FMM_SUB2 * FMM_PS];  // kept terms
+    __shared__ float s_tail[FMM_SUB2 * (FMM_P - FMM_PS)];  // bounds on the dropped terms' |L'_k|
+    const int tid = threadIdx.x;
+    if (!P->ok) return;  // grid-uniform
+    const int nocc = min(P->nocc, P->cap);
+    for (int q = tid; q < 32 * 32; q += FMM_ST) s_binom[q >> 5][q & 31] = make_float2(kBinom.hi[q >> 5][q & 31],
+                                                                                   kBinom.lo[q >> 5][q & 31]);
+    const float b = P->b;
+    for (int box = blockIdx.x; box < nocc; box += gridDim.x) {
+        __syncthreads();
+        if (tid < FMM_P) s_L[tid] = coeff[(size_t)box * FMM_P + tid];
+        const int2 bc = boxlist[box];
+        const unsigned mask = occ[(int64_t)bc.y * P->nbx + bc.x];
+        const int nsub = __popc(mask);
+        if (tid == 0) {
+            // table entries of this cell's occupied sub-cells, in sub-cell order (-1: pool full,
+            // its points use the cell's own expansion)
+            const int base = atomicAdd(&P->sub_used, nsub);
+            s_base = base + nsub <= sub_cap ? base : -1;
+            sub_base[box] = s_base;
+        }
+        __syncthreads();
+        const int base = s_base;
+        const int r = tid / FMM_PS, k = tid - r * FMM_PS;  // r-th occupied sub-cell, term k (and FMM_PS + k)
+        if (base >= 0 && r < nsub) {
+            unsigned mm = mask;
+            for (int q = 0; q < r; q++) mm &= mm - 1u;
+            const int sb = __ffs(mm) - 1;
+            const float ox = ((float)(sb % FMM_SUB) + 0.5f) * (1.0f / FMM_SUB) - 0.5f;
+            const float oy = ((float)(sb / FMM_SUB) + 0.5f) * (1.0f / FMM_SUB) - 0.5f;
+            const dfc d = dfc{two_prod(b, ox), two_prod(b, oy)};
+            const float4 top = s_L[FMM_P - 1];
+            const df c0 = df{s_binom[FMM_P - 1][k].x, s_binom[FMM_P - 1][k].y};
+            dfc a = dfc{df_mul(c0, df{top.x, top.y}), df_mul(c0, df{top.z, top.w})};
+            for (int j = FMM_P - 2; j >= k; j--) {
+                const float4 lj = s_L[j];
+                const df cj = df{s_binom[j][k].x, s_binom[j][k].y};
+                a = dfc_mul(a, d);
+                a.x = df_add(a.x, df_mul(cj, df{lj.x, lj.y}));
+                a.y = df_add(a.y, df_mul(cj, df{lj.z, lj.w}));
+            }
+            s_Ls[sb * FMM_PS + k] = make_float4(a.x.hi, a.x.lo, a.y.hi, a.y.lo);
+            scoeff[((size_t)base + r) * FMM_PS + k] = make_float4(a.x.hi, a.x.lo, a.y.hi, a.y.lo);
+            const int kt = FMM_PS + k;  // a dropped term
+            if (kt < FMM_P) {
+                const float ad = b * sqrtf(fmaf(ox, ox, oy * oy));
+                auto mag = [&](int j) {
+                    const float4 v = s_L[j];
+                    return sqrtf(fmaf(v.x, v.x, v.z * v.z)) * 1.0001f + fabsf(v.y) + fabsf(v.w);
+                };
+                float m = s_binom[FMM_P - 1][kt].x * mag(FMM_P - 1);
+                for (int j = FMM_P - 2; j >= kt; j--) m = fmaf(m, ad, s_binom[j][kt].x * mag(j));
+                s_tail[sb * (FMM_P - FMM_PS) + k] = 1.001f * m;
+            }
+        }
+        __syncthreads();
+        if (base >= 0 && tid < FMM_SUB2 && ((mask >> tid) & 1u)) {
+            // bounds for |z - c_s| <= rp: the dropped terms k >= FMM_PS in S2 = -D1 and S3 = D2/2,
+            // and the FP32 rounding of the terms FMM_KS0 <= k < FMM_PS (4 (PS - KS0) 2^-24 of
+            // their share of S2), on top of the cell's own truncation bound
+            const float rp = FMM_SUBR * b;
+            float t2 = 0.f, t3 = 0.f, mg = 0.f, pw = 1.f;  // pw = rp^(k-1)
+            for (int kk = 1; kk < FMM_P; kk++) {
+                if (kk >= FMM_PS) {
+                    const float a = s_tail[tid * (FMM_P - FMM_PS) + kk - FMM_PS];
+                    t2 = fmaf((float)kk * a, pw, t2);
+                    t3 = fmaf(0.5f * (float)(kk * (kk - 1)) * a, pw / rp, t3);
+                } else if (kk >= FMM_KS0) {
+                    const float4 v = s_Ls[tid * FMM_PS + kk];
+                    const float a = sqrtf(fmaf(v.x, v.x, v.z * v.z)) * 1.0001f + fabsf(v.y) + fabsf(v.w);
+                    mg = fmaf((float)kk * a, pw, mg);
+                }
+                pw *= rp;
+            }
+            const BoxInfo bi = info[box];
+            const float ox = ((float)(tid % FMM_SUB) + 0.5f) * (1.0f / FMM_SUB) - 0.5f;
+            const float oy = ((float)(tid / FMM_SUB) + 0.5f) * (1.0f / FMM_SUB) - 0.5f;
+            const df csx = df_add(df{bi.c.x, bi.c.y}, two_prod(b, ox)), csy = df_add(df{bi.c.z, bi.c.w}, two_prod(b, oy));
+            SubInfo si;
+            si.c = make_float4(csx.hi, csx.lo, csy.hi, csy.lo);
+            si.s2_err = 1.01f * (bi.s2_trunc + t2 + mg * (4.0f * (float)(FMM_PS - FMM_KS0) * 5.97e-8f));
+            si.s3_err = 1.01f * t3;
+            si.r2 = 0.999f * rp * rp;
+            si.pad = 0.f;
+            sinfo[(size_t)base + __popc(mask & ((1u << tid) - 1u))] = si;
+        }
     }
 }
 
@@ -1017,10 +1175,70 @@ __device__ __forceinline__ df df_dot2_add(df a1, df b1, df a2, df b2, df c) {
     return fast_two_sum(s2.hi, e);
 }
 
+// Far-field sums from a local expansion L_0..L_{PN-1} about a centre, at t = z - centre:
+// Horner with the first three derivatives, steps PN-2 .. K0N in FP32 (their terms carry so
+// little of S1, S2 that their FP32 rounding is negligible and is charged to the bound) and
+// the rest in double-float.  S1 += b0, S2 -= b1, S3 += b2, S4 -= b3.
+template <int PN, int K0N>
+__device__ __forceinline__ void far_horner(const float4* L, const df& tx, const df& ty, Sums& sm) {
+    const float tfx = tx.hi, tfy = ty.hi;
+    const float4 top = L[PN - 1];
+    float h0x = top.x, h0y = top.z, h1x = 0.f, h1y = 0.f;
+    float b2x = 0.f, b2y = 0.f, b3x = 0.f, b3y = 0.f;
+#pragma unroll
+    for (int kk = PN - 2; kk >= K0N; kk--) {
+        const float n3x = fmaf(b3x, tfx, fmaf(-b3y, tfy, b2x)), n3y = fmaf(b3x, tfy, fmaf(b3y, tfx, b2y));
+        const float n2x = fmaf(b2x, tfx, fmaf(-b2y, tfy, h1x)), n2y = fmaf(b2x, tfy, fmaf(b2y, tfx, h1y));
+        const float n1x = fmaf(h1x, tfx, fmaf(-h1y, tfy, h0x)), n1y = fmaf(h1x, tfy, fmaf(h1y, tfx, h0y));
+        const float4 Lk = L[kk];
+        const float n0x = fmaf(h0x, tfx, fmaf(-h0y, tfy, Lk.x)), n0y = fmaf(h0x, tfy, fmaf(h0y, tfx, Lk.z));
+        b3x = n3x;
+        b3y = n3y;
+        b2x = n2x;
+        b2y = n2y;
+        h1x = n1x;
+        h1y = n1y;
+        h0x = n0x;
+        h0y = n0y;
+    }
+    df b0x = df{h0x, 0.f}, b0y = df{h0y, 0.f};
+    df b1x = df{h1x, 0.f}, b1y = df{h1y, 0.f};
+#pragma unroll 4
+    for (int kk = K0N - 1; kk >= 0; kk--) {
+        // b3 <- b3 t + b2 ; b2 <- b2 t + b1 ; b1 <- b1 t + b0 ; b0 <- b0 t + L_k
+        const float n3x = fmaf(b3x, tfx, fmaf(-b3y, tfy, b2x)), n3y = fmaf(b3x, tfy, fmaf(b3y, tfx, b2y));
+        const float n2x = fmaf(b2x, tfx, fmaf(-b2y, tfy, b1x.hi)), n2y = fmaf(b2x, tfy, fmaf(b2y, tfx, b1y.hi));
+        b3x = n3x;
+        b3y = n3y;
+        b2x = n2x;
+        b2y = n2y;
+        const df m1x = df_dot2_add(b1x, tx, df_neg(b1y), ty, b0x);
+        const df m1y = df_dot2_add(b1x, ty, b1y, tx, b0y);
+        const float4 Lk = L[kk];
+        const df m0x = df_dot2_add(b0x, tx, df_neg(b0y), ty, df{Lk.x, Lk.y});
+        const df m0y = df_dot2_add(b0x, ty, b0y, tx, df{Lk.z, Lk.w});
+        b1x = m1x;
+        b1y = m1y;
+        b0x = m0x;
+        b0y = m0y;
+    }
+    sm.S1x = df_add(sm.S1x, b0x);
+    sm.S1y = df_add(sm.S1y, b0y);
+    sm.S2x = df_sub(sm.S2x, b1x);
+    sm.S2y = df_sub(sm.S2y, b1y);
+    sm.s3x += b2x;
+    sm.s3y += b2y;
+    sm.s4x -= b3x;
+    sm.s4y -= b3y;
+    sm.a3 += 4.0f * (fabsf(b2x) + fabsf(b2y));
+}
+
 template <bool UNIT>
-__global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const FmmParams* Pm, const int* slot,
+__global__ void __launch_bounds__(PB_THREADS, 3) fmm_polish_kernel(PolishK K, const FmmParams* Pm, const int* slot,
                                                                 const BoxInfo* info, const float4* coeff,
-                                                                const int* pool) {
+                                                                const int* pool, const unsigned* occ,
+                                                                const int* sub_base, const float4* scoeff,
+                                                                const SubInfo* sinfo) {
     if (!Pm->ok) return;  // grid-uniform (set before this launch)
     const int lane = threadIdx.x & 31;
     const int64_t wg = blockIdx.x * (int64_t)(PB_THREADS / 32) + (threadIdx.x >> 5);
@@ -1040,6 +1258,19 @@ __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const
     const int sl = slot[(int64_t)cy * Pm->nbx + cx];
     const BoxInfo bi = info[sl];
     const float4* L = coeff + (size_t)sl * FMM_P;
+    // the point's sub-cell, from its position inside the cell (the radius test in each pass
+    // decides whether the sub-cell expansion applies)
+    const int sbase = sub_base[sl];
+    const bool have_sub = sbase >= 0;
+    SubInfo si = {};
+    const float4* SL = nullptr;
+    if (have_sub) {
+        const int sx = fmm_subcell(z0.x, Pm->x0, Pm->inv_b, cx), sy = fmm_subcell(z0.y, Pm->y0, Pm->inv_b, cy);
+        const unsigned mask = occ[(int64_t)cy * Pm->nbx + cx];
+        const size_t sidx = (size_t)sbase + __popc(mask & ((1u << (sy * FMM_SUB + sx)) - 1u));
+        si = sinfo[sidx];
+        SL = scoeff + sidx * FMM_PS;
+    }
     tf zxt = tf{z0.x, 0.f, 0.f}, zyt = tf{z0.y, 0.f, 0.f};
     df cxr, cyr;
     row_constant(K, row, cxr, cyr);
@@ -1052,63 +1283,25 @@ __global__ void __launch_bounds__(PB_THREADS) fmm_polish_kernel(PolishK K, const
             const int j = pool[bi.near_off + q];
             star_df<UNIT>(zxt, zyt, K.dfp[j], K.dtf[j], K.dfm[j], sm);
         }
-        // far field: Horner with derivatives in t = z - c
-        const df tx = tf_sub(zxt, bi.c.x, bi.c.y, 0.f), ty = tf_sub(zyt, bi.c.z, bi.c.w, 0.f);
-        // Horner steps FMM_P-2 .. FMM_K0 in FP32: the terms k >= FMM_K0 carry at most
-        // R2 K0 rho^(K0-1) / (1 - rho)^2 of S2 (and less of S1), so their FP32 rounding
-        // is negligible and enters the bound; the steps below in double-float
-        const float tfx = tx.hi, tfy = ty.hi;
-        const float4 top = L[FMM_P - 1];
-        float h0x = top.x, h0y = top.z, h1x = 0.f, h1y = 0.f;
-        float b2x = 0.f, b2y = 0.f, b3x = 0.f, b3y = 0.f;
-#pragma unroll
-        for (int kk = FMM_P - 2; kk >= FMM_K0; kk--) {
-            const float n3x = fmaf(b3x, tfx, fmaf(-b3y, tfy, b2x)), n3y = fmaf(b3x, tfy, fmaf(b3y, tfx, b2y));
-            const float n2x = fmaf(b2x, tfx, fmaf(-b2y, tfy, h1x)), n2y = fmaf(b2x, tfy, fmaf(b2y, tfx, h1y));
-            const float n1x = fmaf(h1x, tfx, fmaf(-h1y, tfy, h0x)), n1y = fmaf(h1x, tfy, fmaf(h1y, tfx, h0y));
-            const float4 Lk = L[kk];
-            const float n0x = fmaf(h0x, tfx, fmaf(-h0y, tfy, Lk.x)), n0y = fmaf(h0x, tfy, fmaf(h0y, tfx, Lk.z));
-            b3x = n3x;
-            b3y = n3y;
-            b2x = n2x;
-            b2y = n2y;
-            h1x = n1x;
-            h1y = n1y;
-            h0x = n0x;
-            h0y = n0y;
+        // far field: Horner with derivatives, about the sub-cell centre when the point is within
+        // the sub-cell's radius (16 terms), else about the cell centre (32 terms)
+        float s2e = bi.s2_err, s3e = 0.f;
+        bool sub_done = false;
+        if (have_sub) {
+            const df ux = tf_sub(zxt, si.c.x, si.c.y, 0.f), uy = tf_sub(zyt, si.c.z, si.c.w, 0.f);
+            if (fmaf(ux.hi, ux.hi, uy.hi * uy.hi) <= si.r2) {
+                far_horner<FMM_PS, FMM_KS0>(SL, ux, uy, sm);
+                s2e = si.s2_err;
+                s3e = si.s3_err;
+                sub_done = true;
+            }
         }
-        df b0x = df{h0x, 0.f}, b0y = df{h0y, 0.f};
-        df b1x = df{h1x, 0.f}, b1y = df{h1y, 0.f};
-        for (int kk = FMM_K0 - 1; kk >= 0; kk--) {
-            // b3 <- b3 t + b2 ; b2 <- b2 t + b1 ; b1 <- b1 t + b0 ; b0 <- b0 t + L_k
-            const float n3x = fmaf(b3x, tfx, fmaf(-b3y, tfy, b2x)), n3y = fmaf(b3x, tfy, fmaf(b3y, tfx, b2y));
-            const float n2x = fmaf(b2x, tfx, fmaf(-b2y, tfy, b1x.hi)), n2y = fmaf(b2x, tfy, fmaf(b2y, tfx, b1y.hi));
-            b3x = n3x;
-            b3y = n3y;
-            b2x = n2x;
-            b2y = n2y;
-            const df m1x = df_dot2_add(b1x, tx, df_neg(b1y), ty, b0x);
-            const df m1y = df_dot2_add(b1x, ty, b1y, tx, b0y);
-            const float4 Lk = L[kk];
-            const df m0x = df_dot2_add(b0x, tx, df_neg(b0y), ty, df{Lk.x, Lk.y});
-            const df m0y = df_dot2_add(b0x, ty, b0y, tx, df{Lk.z, Lk.w});
-            b1x = m1x;
-            b1y = m1y;
-            b0x = m0x;
-            b0y = m0y;
+        if (!sub_done) {
+            const df tx = tf_sub(zxt, bi.c.x, bi.c.y, 0.f), ty = tf_sub(zyt, bi.c.z, bi.c.w, 0.f);
+            far_horner<FMM_P, FMM_K0>(L, tx, ty, sm);
         }
-        // S1 += b0, S2 += -b1, S3 += b2, S4 += -b3
-        sm.S1x = df_add(sm.S1x, b0x);
-        sm.S1y = df_add(sm.S1y, b0y);
-        sm.S2x = df_sub(sm.S2x, b1x);
-        sm.S2y = df_sub(sm.S2y, b1y);
-        sm.s3x += b2x;
-        sm.s3y += b2y;
-        sm.s4x -= b3x;
-        sm.s4y -= b3y;
-        sm.a3 += 4.0f * (fabsf(b2x) + fabsf(b2y));
         double est = 0.0;
-        if (polish_epilogue_df(K, point, row, sm, cxr, cyr, zxt, zyt, z0.x, z0.y, pass, it_in, est, bi.s2_err)) {
+        if (polish_epilogue_df(K, point, row, sm, cxr, cyr, zxt, zyt, z0.x, z0.y, pass, it_in, est, s2e, s3e)) {
             est_max = (float)est;
             break;
         }
@@ -1131,7 +1324,7 @@ size_t fmm_workspace_bytes(int64_t points) {
     auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
     add(sizeof(FmmParams));
     add(sizeof(float4) * 512);
-    add((size_t)FMM_G * FMM_G);                 // occupancy
+    add(sizeof(unsigned) * (size_t)FMM_G * FMM_G);  // occupancy (sub-cell bits)
     add(sizeof(int) * (size_t)FMM_G * FMM_G);   // slots
     add(sizeof(int2) * cap);
     add(sizeof(BoxInfo) * cap);
@@ -1142,6 +1335,11 @@ size_t fmm_workspace_bytes(int64_t points) {
     add(sizeof(float4) * FMM_P * (size_t)FMM_COARSE_MAX);
     add(sizeof(CoarseInfo) * (size_t)FMM_COARSE_MAX);
     add(sizeof(int) * (size_t)FMM_CPOOL);
+    const int64_t subs = 4 * cap < FMM_SUBPOOL ? 4 * cap : FMM_SUBPOOL;  // occupied sub-cells (a cell's
+                                                                           // curves hold a few of its 16)
+    add(sizeof(int) * cap);
+    add(sizeof(float4) * FMM_PS * (size_t)subs);
+    add(sizeof(SubInfo) * (size_t)subs);
     return b;
 }
 
@@ -1157,7 +1355,7 @@ cudaError_t launch_polish_fmm(const PolishArgs& a, void* ws, cudaStream_t st) {
     };
     FmmParams* P = (FmmParams*)take(sizeof(FmmParams));
     float4* part = (float4*)take(sizeof(float4) * 512);
-    uint8_t* occ = (uint8_t*)take((size_t)FMM_G * FMM_G);
+    unsigned* occ = (unsigned*)take(sizeof(unsigned) * (size_t)FMM_G * FMM_G);
     int* slot = (int*)take(sizeof(int) * (size_t)FMM_G * FMM_G);
     int2* boxlist = (int2*)take(sizeof(int2) * cap);
     BoxInfo* info = (BoxInfo*)take(sizeof(BoxInfo) * cap);
@@ -1168,10 +1366,14 @@ cudaError_t launch_polish_fmm(const PolishArgs& a, void* ws, cudaStream_t st) {
     float4* cLc = (float4*)take(sizeof(float4) * FMM_P * (size_t)FMM_COARSE_MAX);
     CoarseInfo* cinfo = (CoarseInfo*)take(sizeof(CoarseInfo) * (size_t)FMM_COARSE_MAX);
     int* cpool = (int*)take(sizeof(int) * (size_t)FMM_CPOOL);
+    const int subs = 4 * (int64_t)cap < FMM_SUBPOOL ? 4 * cap : FMM_SUBPOOL;
+    int* sub_base = (int*)take(sizeof(int) * cap);
+    float4* scoeff = (float4*)take(sizeof(float4) * FMM_PS * (size_t)subs);
+    SubInfo* sinfo = (SubInfo*)take(sizeof(SubInfo) * (size_t)subs);
     cudaError_t e;
     fmm_extent_kernel<<<512, 256, 0, st>>>(a.zrows, points, part);
     fmm_setup_kernel<<<1, 32, 0, st>>>(part, 512, a.f->fmm_cell, cap, pool_cap, P);
-    if ((e = cudaMemsetAsync(occ, 0, (size_t)FMM_G * FMM_G, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(occ, 0, sizeof(unsigned) * (size_t)FMM_G * FMM_G, st)) != cudaSuccess) return e;
     {
         const int64_t warps = ((a.m + 1 + 31) / 32) * a.nr;
         fmm_occupy_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(a.zrows, a.m + 1, a.nr, P, occ);
@@ -1189,14 +1391,17 @@ cudaError_t launch_polish_fmm(const PolishArgs& a, void* ws, cudaStream_t st) {
                                                    (int)a.f->n, cLc, cinfo, cpool, FMM_CPOOL);
     fmm_coeff_kernel<<<1216, FMM_CT, csmem2, st>>>(P, boxlist, cslot, cLc, cinfo, cpool, a.f->star_dfp, a.f->star_dfm,
                                                    a.f->star32, info, coeff, pool);
+    fmm_subcell_kernel<<<1216, FMM_ST, 0, st>>>(P, boxlist, occ, info, coeff, sub_base, scoeff, sinfo, subs);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     PolishK K = make_polish_k(a);
     const int64_t warps = ((a.m + 1 + 31) / 32) * a.nr;
     const unsigned blocks = (unsigned)((warps + (PB_THREADS / 32) - 1) / (PB_THREADS / 32));
     if (a.f->unit_mass)
-        fmm_polish_kernel<true><<<blocks, PB_THREADS, 0, st>>>(K, P, slot, info, coeff, pool);
+        fmm_polish_kernel<true><<<blocks, PB_THREADS, 0, st>>>(K, P, slot, info, coeff, pool, occ, sub_base, scoeff,
+                                                              sinfo);
     else
-        fmm_polish_kernel<false><<<blocks, PB_THREADS, 0, st>>>(K, P, slot, info, coeff, pool);
+        fmm_polish_kernel<false><<<blocks, PB_THREADS, 0, st>>>(K, P, slot, info, coeff, pool, occ, sub_base, scoeff,
+                                                               sinfo);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // the direct polish runs (and does the whole job) only when the tables did not fit
     PolishArgs b = a;

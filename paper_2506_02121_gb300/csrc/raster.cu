@@ -109,23 +109,6 @@ __device__ __forceinline__ double pix(double lo, double step, int64_t i) {
     return __dadd_rn(lo, __dmul_rn(__dadd_rn((double)i, 0.5), step));
 }
 
-// Integer <-> float without conversion instructions (which share the FP64 pipe's low rate on
-// this part): adding an integer to the bits of 1.5 * 2^23 steps its value by exactly one per
-// unit, so for |x| < 2^22 the value is 1.5 * 2^23 + x, and an FP32 sum with 1.5 * 2^23
-// rounds to the nearest integer.
-constexpr float MAGIC_F = 12582912.0f;  // 1.5 * 2^23
-constexpr int MAGIC_I = 0x4B400000;     // its bits
-__device__ __forceinline__ float i2f_small(int x) { return __int_as_float(MAGIC_I + x) - MAGIC_F; }  // |x| < 2^22
-__device__ __forceinline__ int ceil_small(float x) {  // |x| < 2^21
-    const float t = x + MAGIC_F;
-    const int n = __float_as_int(t) - MAGIC_I;
-    return (t - MAGIC_F) < x ? n + 1 : n;
-}
-__device__ __forceinline__ int floor_small(float x) {  // |x| < 2^21
-    const float t = x + MAGIC_F;
-    const int n = __float_as_int(t) - MAGIC_I;
-    return (t - MAGIC_F) > x ? n - 1 : n;
-}
 // Maps of up to this many pixels per side take the conversion-free forms above.
 constexpr int SMALL_GRID = 1 << 20;
 
