@@ -361,7 +361,8 @@ def run_ours(args):
                 "ops_per_unit": {"star_term": TRACE_OPS_PER_STAR, "root_term": TRACE_OPS_PER_ROOT,
                                  "far_eval": TRACE_OPS_PER_FAR_EVAL},
                 "units": f"{rep['star_terms']} star terms, {rep['root_terms']} root terms "
-                         f"({rep['root_iterations']} root-iterations), {rep['far_evals']} expansion evaluations"}
+                         f"({rep['root_iterations']} root-iterations, {rep['cold_root_iterations']} of them at "
+                         f"cold-started rows), {rep['far_evals']} expansion evaluations"}
     # crossing map: vertex reads + one int32 read+write per pixel for the scan + the clearing
     # store; distance map: N_cc read, g written and read, distance written (8 B)
     cross_bytes = rows * nr * 16 + 3 * px * px * 4

@@ -653,10 +653,13 @@ __global__ void fmm_extent_kernel(const float2* z, int64_t npts, float4* part) {
 
 __global__ void fmm_setup_kernel(const float4* part, int nparts, float b_target, int cap, int pool_cap,
                                  FmmParams* P) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0) return;
+    // one warp: each lane reduces a share of the partial extents, then a butterfly
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x >= 32) return;
     float mnx = 3.0e38f, mny = 3.0e38f, mxx = -3.0e38f, mxy = -3.0e38f;
     bool ok = true;
-    for (int i = 0; i < nparts; i++) {
+    for (int i = lane; i < nparts; i += 32) {
         const float4 r = part[i];
         if (r.x != r.x) {
             ok = false;
@@ -667,6 +670,14 @@ __global__ void fmm_setup_kernel(const float4* part, int nparts, float b_target,
         mxx = fmaxf(mxx, r.z);
         mxy = fmaxf(mxy, r.w);
     }
+    for (int off = 16; off > 0; off >>= 1) {
+        mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, off));
+        mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, off));
+        mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, off));
+        mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, off));
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    if (lane != 0) return;
     float b = b_target > 0.f ? b_target : 1.0f;
     const float span = fmaxf(mxx - mnx, mxy - mny);
     const int margin = 2 * (FMM_K + 1) + 2;
@@ -708,13 +719,13 @@ __global__ void fmm_occupy_kernel(const float2* z, int64_t rows, int64_t nr, Fmm
     // other warps may clear ok while this one runs: one read per warp keeps the return
     // warp-uniform (the full-warp match below needs every lane)
     if (!__shfl_sync(0xffffffffu, P->ok, 0)) return;
-    int64_t cell = -1;
+    int cell = -1;  // < FMM_G^2 = 2^22
     unsigned bit = 0;
     if (row < rows) {
         const float2 v = z[row * nr + col];
         const int cx = fmm_cell(v.x, P->x0, P->inv_b), cy = fmm_cell(v.y, P->y0, P->inv_b);
         if (cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby) {
-            cell = (int64_t)cy * P->nbx + cx;
+            cell = cy * P->nbx + cx;
             bit = 1u << (fmm_subcell(v.y, P->y0, P->inv_b, cy) * FMM_SUB + fmm_subcell(v.x, P->x0, P->inv_b, cx));
         } else {
             P->ok = 0;
@@ -807,16 +818,38 @@ __device__ __forceinline__ void fmm_acc_star(float* acc, int warp, int lane, con
     }
 }
 
-// Sum of coefficient k over the lanes and warps, in a fixed order (thread k < FMM_P).
-__device__ __forceinline__ dfc fmm_acc_sum(const float* acc, int k) {
-    df sx = df{0.f, 0.f}, sy = df{0.f, 0.f};
-    for (int w = 0; w < FMM_WARPS; w++)
-        for (int l = 0; l < 32; l++) {
-            const int a = ((w * FMM_P + k) << 5) + l;
+// Sum of each coefficient over the warps and lanes, in a fixed order: warp w takes the
+// coefficients k = w, w + FMM_WARPS, ...; each lane adds the warps' partials at its lane, then
+// a butterfly adds the lanes. Lane 0 writes out[k] = (x.hi, x.lo, y.hi, y.lo).
+__device__ __forceinline__ void fmm_acc_reduce(const float* acc, int warp, int lane, float4* out) {
+    for (int k = warp; k < FMM_P; k += FMM_WARPS) {
+        df sx = df{0.f, 0.f}, sy = df{0.f, 0.f};
+        for (int w = 0; w < FMM_WARPS; w++) {
+            const int a = ((w * FMM_P + k) << 5) + lane;
             sx = df_add(sx, df{acc[a], acc[a + FMM_ACC]});
             sy = df_add(sy, df{acc[a + 2 * FMM_ACC], acc[a + 3 * FMM_ACC]});
         }
-    return dfc{sx, sy};
+        for (int off = 16; off > 0; off >>= 1) {
+            sx = df_add(sx, df{__shfl_xor_sync(0xffffffffu, sx.hi, off), __shfl_xor_sync(0xffffffffu, sx.lo, off)});
+            sy = df_add(sy, df{__shfl_xor_sync(0xffffffffu, sy.hi, off), __shfl_xor_sync(0xffffffffu, sy.lo, off)});
+        }
+        if (lane == 0) out[k] = make_float4(sx.hi, sx.lo, sy.hi, sy.lo);
+    }
+}
+
+// Sum of the per-thread bound terms: r2 added, dmin minimised (warp 0, all lanes get it).
+__device__ __forceinline__ void fmm_bound_reduce(const float* s_r2, const float* s_dmin, int lane, float& R2,
+                                                 float& D) {
+    R2 = 0.f;
+    D = 3.0e38f;
+    for (int t = lane; t < FMM_CT; t += 32) {
+        R2 += s_r2[t];
+        D = fminf(D, s_dmin[t]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        R2 += __shfl_xor_sync(0xffffffffu, R2, off);
+        D = fminf(D, __shfl_xor_sync(0xffffffffu, D, off));
+    }
 }
 
 __device__ __forceinline__ float fmm_tail(float r2, float rho) {
@@ -898,27 +931,23 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coarse_kernel(FmmParams* P, const 
         s_dmin[tid] = dmin;
         __syncthreads();
         const int lcnt = s_lcnt;
-        if (tid == 0) {
-            const int off = lcnt <= FMM_CLIST ? atomicAdd(&P->cpool_used, lcnt) : 0;
-            if (lcnt > FMM_CLIST || off + lcnt > cpool_cap) P->ok = 0;  // the direct polish takes over
-            s_off = off;
-            float R2 = 0.f, D = 3.0e38f;
-            for (int t = 0; t < FMM_CT; t++) {
-                R2 += s_r2[t];
-                D = fminf(D, s_dmin[t]);
+        if (warp == 0) {
+            float R2, D;
+            fmm_bound_reduce(s_r2, s_dmin, lane, R2, D);
+            if (lane == 0) {
+                const int off = lcnt <= FMM_CLIST ? atomicAdd(&P->cpool_used, lcnt) : 0;
+                if (lcnt > FMM_CLIST || off + lcnt > cpool_cap) P->ok = 0;  // the direct polish takes over
+                s_off = off;
+                CoarseInfo c;
+                c.off = off;
+                c.cnt = lcnt;
+                c.r2 = R2;
+                c.dmin = D;
+                cinfo[ci] = c;
+                cslot[X.y * ncx + X.x] = ci;
             }
-            CoarseInfo c;
-            c.off = off;
-            c.cnt = lcnt;
-            c.r2 = R2;
-            c.dmin = D;
-            cinfo[ci] = c;
-            cslot[X.y * ncx + X.x] = ci;
         }
-        if (tid < FMM_P) {
-            const dfc L = fmm_acc_sum(acc, tid);
-            cLc[(size_t)ci * FMM_P + tid] = make_float4(L.x.hi, L.x.lo, L.y.hi, L.y.lo);
-        }
+        fmm_acc_reduce(acc, warp, lane, cLc + (size_t)ci * FMM_P);
         __syncthreads();
         if (lcnt <= FMM_CLIST && s_off + lcnt <= cpool_cap)
             for (int i = tid; i < lcnt; i += FMM_CT) cpool[s_off + i] = s_list[i];
@@ -934,6 +963,8 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
                                                            const float4* s32, BoxInfo* info, float4* coeff,
                                                            int* pool) {
     extern __shared__ __align__(16) float acc[];  // [4 components][warp][k][lane]
+    __shared__ float2 s_binom[32][32];            // C(j, k) as double-float
+    __shared__ float4 s_Ld[FMM_P];                // direct part of each coefficient
     __shared__ int s_wcnt[FMM_WARPS];
     __shared__ int s_off, s_cnt;
     __shared__ float s_r2[FMM_CT], s_dmin[FMM_CT];
@@ -945,6 +976,8 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
     }
     __syncthreads();
     if (!s_ok) return;  // block-uniform
+    for (int q = tid; q < 32 * 32; q += FMM_CT) s_binom[q >> 5][q & 31] = make_float2(kBinom.hi[q >> 5][q & 31],
+                                                                                   kBinom.lo[q >> 5][q & 31]);
     const int ncx = (P->nbx + FMM_F - 1) / FMM_F;
     const double b = (double)P->b;
     for (int box = blockIdx.x; box < s_nocc; box += gridDim.x) {
@@ -1008,45 +1041,44 @@ __global__ void __launch_bounds__(FMM_CT) fmm_coeff_kernel(FmmParams* P, const i
         s_r2[tid] = r2i;
         s_dmin[tid] = dmi;
         __syncthreads();
+        fmm_acc_reduce(acc, warp, lane, s_Ld);  // direct part
+        __syncthreads();
         if (tid < FMM_P) {
             // Lc re-centred at c (Taylor shift by t0 = c - C: Horner in t0 with binomial
-            // weights C(k, j)), plus the direct part
+            // weights C(k, jk)), plus the direct part
             const int jk = tid;
             const float4* Lc = cLc + (size_t)ci * FMM_P;
             const df tx = df_from_double(cxd - Cxd), ty = df_from_double(cyd - Cyd);
-            double bin = 1.0;  // C(P-1, jk)
-            for (int i = 0; i < jk; i++) bin = bin * (double)(FMM_P - 1 - i) / (double)(i + 1);
             const float4 top = Lc[FMM_P - 1];
-            dfc sacc = dfc{df_mul(df_from_double(bin), df{top.x, top.y}), df_mul(df_from_double(bin), df{top.z, top.w})};
+            const df b0 = df{s_binom[FMM_P - 1][jk].x, s_binom[FMM_P - 1][jk].y};
+            dfc sacc = dfc{df_mul(b0, df{top.x, top.y}), df_mul(b0, df{top.z, top.w})};
             for (int k = FMM_P - 2; k >= jk; k--) {
-                bin = bin * (double)(k + 1 - jk) / (double)(k + 1);  // C(k, jk) from C(k+1, jk)
+                const df bk = df{s_binom[k][jk].x, s_binom[k][jk].y};
                 const float4 lk = Lc[k];
                 sacc = dfc_mul(sacc, dfc{tx, ty});
-                sacc.x = df_add(sacc.x, df_mul(df_from_double(bin), df{lk.x, lk.y}));
-                sacc.y = df_add(sacc.y, df_mul(df_from_double(bin), df{lk.z, lk.w}));
+                sacc.x = df_add(sacc.x, df_mul(bk, df{lk.x, lk.y}));
+                sacc.y = df_add(sacc.y, df_mul(bk, df{lk.z, lk.w}));
             }
-            const dfc Ld = fmm_acc_sum(acc, jk);
-            const df lx = df_add(sacc.x, Ld.x), ly = df_add(sacc.y, Ld.y);
+            const float4 ld = s_Ld[jk];
+            const df lx = df_add(sacc.x, df{ld.x, ld.y}), ly = df_add(sacc.y, df{ld.z, ld.w});
             coeff[(size_t)box * FMM_P + jk] = make_float4(lx.hi, lx.lo, ly.hi, ly.lo);
         }
-        if (tid == 0) {
-            float R2 = 0.f, D = 3.0e38f;
-            for (int t = 0; t < FMM_CT; t++) {
-                R2 += s_r2[t];
-                D = fminf(D, s_dmin[t]);
+        if (warp == 0) {
+            float R2, D;
+            fmm_bound_reduce(s_r2, s_dmin, lane, R2, D);
+            if (lane == 0) {
+                BoxInfo bi;
+                bi.c = make_float4(cx.hi, cx.lo, cy.hi, cy.lo);
+                bi.near_off = s_off;
+                bi.near_cnt = room ? s_cnt : 0;
+                // points lie within 0.72 b of c (half-diagonal plus the Newton steps)
+                const float tc = (float)sqrt((cxd - Cxd) * (cxd - Cxd) + (cyd - Cyd) * (cyd - Cyd));
+                const float rho1 = 0.72f * P->b / D, rho2 = (tc + 0.72f * P->b) / cI.dmin;
+                bi.s2_trunc = fmm_tail(R2, rho1) + fmm_tail(cI.r2, rho2);
+                bi.s2_err = bi.s2_trunc + fmm_fp32_part(R2, rho1) + fmm_fp32_part(cI.r2, rho2);
+                info[box] = bi;
             }
-            BoxInfo bi;
-            bi.c = make_float4(cx.hi, cx.lo, cy.hi, cy.lo);
-            bi.near_off = s_off;
-            bi.near_cnt = room ? s_cnt : 0;
-            // points lie within 0.72 b of c (half-diagonal plus the Newton steps)
-            const float tc = (float)sqrt((cxd - Cxd) * (cxd - Cxd) + (cyd - Cyd) * (cyd - Cyd));
-            const float rho1 = 0.72f * P->b / D, rho2 = (tc + 0.72f * P->b) / cI.dmin;
-            bi.s2_trunc = fmm_tail(R2, rho1) + fmm_tail(cI.r2, rho2);
-            bi.s2_err = bi.s2_trunc + fmm_fp32_part(R2, rho1) + fmm_fp32_part(cI.r2, rho2);
-            info[box] = bi;
         }
-        __syncthreads();
         __syncthreads();
     }
 }
