@@ -111,6 +111,8 @@ struct TK {
     int max_iter_cold, max_iter_warm, predictor;
     int root_refresh;  // FP32 warm rows: exact far part of the root sum every root_refresh rows (< 2: every sweep)
     int near_cap;      // rows of up to near_cap roots keep the split's ordered positions in shared memory
+    int near_ext;      // ... and also its far parts, refresh positions and cells (the host sized the shared
+                       // memory for them)
     // FP32 far-field tables (tfmm.ok == 0: every star summed directly)
     TfmmParams tfmm;
     const TCell* tcells;
@@ -137,14 +139,18 @@ struct Ctx {
     unsigned long long* n_terms;  // this thread's work counters (registers of the caller)
     unsigned long long* n_far;
     unsigned long long* n_root;
-    // near/far split of the root sum (per direction d: [d nr, d nr + nr) of each array)
-    float2* nfar;   // far part of root k's sum, captured at the last refresh row
-    float2* npos;   // current positions in cell order
-    int* nkey;      // refresh cell of root k
-    int* nord;      // keys d nr + k of direction d's roots in cell order (row-major cells, index order within a cell)
+    // near/far split of the root sum (per direction d: [d nr, d nr + nr) of each array).  A
+    // root's code is d nr + its place in cell order (the refresh's order); arrays indexed by
+    // code are read in that order by a light sweep's first pass (neighbouring threads,
+    // neighbouring entries)
+    float2* nfar;   // [code]: far part of the root's sum, captured at the last refresh row
+    float2* npos;   // [code]: current positions
+    int* nkey;      // [key]: refresh cell (scratch of the cell building)
+    int* ncell;     // [code]: refresh cell as (cy << 16) | cx
+    int* nord;      // [code]: key d nr + k (row-major cells, index order within a cell)
     int* ncst;      // [d (ncm + 1) + c]: first entry of cell c in nord
     int* nfill;     // [d ncm + c]: scatter counters
-    float2* nref;   // positions at the last refresh
+    float2* nref;   // [code]: position at the last refresh
     float2* npred;  // this row's predicted positions
     int* nrank;     // [key]: position of the root within its direction's part of nord
     int* act2;      // second active list (split sweeps alternate between act and act2)
@@ -209,6 +215,37 @@ __device__ __forceinline__ float4 lds_f4(unsigned addr) {
     return v;
 }
 
+// The cell's far-field series at t = z - centre, by Horner on packed pairs: the table holds
+// per k (U_k re, S1'_k re, U_k im, S1'_k im), U the expansion of sum_far 1/(z - z_i) and S1' =
+// sum k L_k t^(k-1) that of the derivative of S1 = sum_far m_i/(z - z_i) (S1'_13 = 0).  One
+// chain gives (U, S1') and its derivative chain S1''; out: U, S1' and S1''/2.
+__device__ __forceinline__ void far_eval(const float4* L, float tx, float ty, float& Ux, float& Uy, float& Sx,
+                                         float& Sy, float& Hx, float& Hy) {
+    const f2p TX = f2_pack(tx, tx), TY = f2_pack(ty, ty), NTY = f2_pack(-ty, -ty);
+    const float4 top = L[TFMM_P - 1];
+    f2p X = f2_pack(top.x, top.y), Y = f2_pack(top.z, top.w);
+    f2p DX = f2_pack(0.f, 0.f), DY = DX;
+#pragma unroll
+    for (int kk = TFMM_P - 2; kk >= 0; kk--) {
+        const float4 c4 = L[kk];
+        const f2p nDX = f2_fma(DX, TX, f2_fma(DY, NTY, X));
+        const f2p nDY = f2_fma(DX, TY, f2_fma(DY, TX, Y));
+        const f2p nX = f2_fma(X, TX, f2_fma(Y, NTY, f2_pack(c4.x, c4.y)));
+        const f2p nY = f2_fma(X, TY, f2_fma(Y, TX, f2_pack(c4.z, c4.w)));
+        DX = nDX;
+        DY = nDY;
+        X = nX;
+        Y = nY;
+    }
+    float dux, duy;
+    f2_unpack(X, Ux, Sx);
+    f2_unpack(Y, Uy, Sy);
+    f2_unpack(DX, dux, Hx);
+    f2_unpack(DY, duy, Hy);
+    Hx *= 0.5f;
+    Hy *= 0.5f;
+}
+
 // Cell of z in the FP32 far-field grid, or -1 when every star is summed directly (FP64
 // tracer, no grid, z outside it, or a cell with too many near stars).
 template <typename T>
@@ -222,8 +259,7 @@ __device__ __forceinline__ int far_cell(const TK& K, T zx, T zy) {
 }
 
 // Star terms of a root in a far-field cell: its near stars (lanes lane, lane + g, ...) and,
-// on lane 0, the cell's two local expansions by Horner, U(t) = sum U_k t^k -> C and
-// S1(t) = sum L_k t^k with its first and half second derivative -> A = -S1', B = S1''/2.
+// on lane 0, the cell's local expansions (far_eval): U(t) -> C, A = -S1'(t), B = S1''(t)/2.
 template <typename T>
 __device__ __forceinline__ void cell_part(const Ctx<T>& x, int cell, T zx, T zy, int lane, int g, Acc<T>& acc) {
     const TK& K = *x.k;
@@ -236,40 +272,21 @@ __device__ __forceinline__ void cell_part(const Ctx<T>& x, int cell, T zx, T zy,
         acc_star(zx, zy, x.resident ? x.s_star[j] : gs[j], acc);
     }
     if (lane != 0) return;
-    const float tx = (float)zx - tc.cx, ty = (float)zy - tc.cy;
-    const float4* L = K.tcoeff + (size_t)cell * TFMM_P;
-    const float4 top = L[TFMM_P - 1];
-    float ux = top.x, uy = top.y, b0x = top.z, b0y = top.w;
-    float b1x = 0.f, b1y = 0.f, b2x = 0.f, b2y = 0.f;
-#pragma unroll
-    for (int kk = TFMM_P - 2; kk >= 0; kk--) {
-        const float4 c4 = L[kk];
-        const float n2x = fmaf(b2x, tx, fmaf(-b2y, ty, b1x)), n2y = fmaf(b2x, ty, fmaf(b2y, tx, b1y));
-        const float n1x = fmaf(b1x, tx, fmaf(-b1y, ty, b0x)), n1y = fmaf(b1x, ty, fmaf(b1y, tx, b0y));
-        const float n0x = fmaf(b0x, tx, fmaf(-b0y, ty, c4.z)), n0y = fmaf(b0x, ty, fmaf(b0y, tx, c4.w));
-        const float nux = fmaf(ux, tx, fmaf(-uy, ty, c4.x)), nuy = fmaf(ux, ty, fmaf(uy, tx, c4.y));
-        b2x = n2x;
-        b2y = n2y;
-        b1x = n1x;
-        b1y = n1y;
-        b0x = n0x;
-        b0y = n0y;
-        ux = nux;
-        uy = nuy;
-    }
+    float ux, uy, sx, sy, hx, hy;
+    far_eval(K.tcoeff + (size_t)cell * TFMM_P, (float)zx - tc.cx, (float)zy - tc.cy, ux, uy, sx, sy, hx, hy);
     acc.Cx += (T)ux;
     acc.Cy += (T)uy;
-    acc.Ax -= (T)b1x;
-    acc.Ay -= (T)b1y;
-    acc.Bx += (T)b2x;
-    acc.By += (T)b2y;
+    acc.Ax -= (T)sx;
+    acc.Ay -= (T)sy;
+    acc.Bx += (T)hx;
+    acc.By += (T)hy;
     acc.Am += (T)tc.far_m_d2;
 }
 
 // Aberth update of one root from its sums (Eq. 9 with F, F' of Eqs. 6-7), and the stop rule.
 template <typename T>
-__device__ __forceinline__ void finish_root(const Ctx<T>& x, int key, typename CT<T>::C z, const Acc<T>& acc, T cph,
-                                            T sph, int* s_maxit) {
+__device__ __forceinline__ typename CT<T>::C finish_root(const Ctx<T>& x, int key, typename CT<T>::C z,
+                                                         const Acc<T>& acc, T cph, T sph, int* s_maxit) {
     using C = typename CT<T>::C;
     const TK& K = *x.k;
     const T oms = (T)(1.0 - K.kappa_s);
@@ -351,6 +368,7 @@ __device__ __forceinline__ void finish_root(const Ctx<T>& x, int key, typename C
     x.dprev[key] = (float)ad;
     if (done) x.conv[key] = 1;
     x.nxt[key] = zn;
+    return zn;
 }
 
 // ----------------------------------------------------------------------------------
@@ -372,14 +390,14 @@ __device__ __forceinline__ void finish_root(const Ctx<T>& x, int key, typename C
 // ----------------------------------------------------------------------------------
 constexpr int NEAR_PER_CELL = 4;  // roots per cell on average over the bounding box
 
-// sum over the near set of root key (direction key >= nr) at the positions in npos; returns
-// the number of terms.  Its own entry contributes 0 (see acc_root_f).
-__device__ __forceinline__ int near_sum(const Ctx<float>& x, int key, float zx, float zy, float& Dx, float& Dy) {
+// sum over the near set of a root of direction d in refresh cell cell (= (cy << 16) | cx) at
+// the positions in npos; returns the number of terms.  Its own entry contributes 0 (see
+// acc_root_f).
+__device__ __forceinline__ int near_sum(const Ctx<float>& x, int d, int cell, float zx, float zy, float& Dx,
+                                        float& Dy) {
     const int nr = x.k->nr;
-    const int d = key >= nr ? 1 : 0;
     const int nbx = x.s_ngrid[2 * d], nby = x.s_ngrid[2 * d + 1];
-    const int c = x.nkey[key];
-    const int cx = c % nbx, cy = c / nbx;
+    const int cx = cell & 0xffff, cy = cell >> 16;
     const int* cst = x.ncst + (size_t)d * (x.ncm + 1);
     const float2* p = x.npos + (size_t)d * nr;
     const int xa = max(cx - 1, 0), xb = min(cx + 1, nbx - 1);
@@ -496,7 +514,6 @@ __device__ void near_build(const Ctx<float>& x, int d) {
     __syncthreads();
     for (int k = tid; k < nr; k += P) {
         const float2 v = z[k];
-        x.nref[(size_t)d * nr + k] = v;
         // clamped in floating point first (a NaN position lands in cell 0)
         const float fx = fminf(fmaxf((v.x - x0) * ih, 0.f), (float)(nbx - 1));
         const float fy = fminf(fmaxf((v.y - y0) * ih, 0.f), (float)(nby - 1));
@@ -524,7 +541,12 @@ __device__ void near_build(const Ctx<float>& x, int d) {
         }
     }
     __syncthreads();
-    for (int i = tid; i < nr; i += P) x.nrank[ord[i]] = i;
+    for (int i = tid; i < nr; i += P) {
+        const int kk = ord[i], k = kk - d * nr, c = key[k];
+        x.nrank[kk] = i;
+        x.nref[d * nr + i] = z[k];
+        x.ncell[d * nr + i] = ((c / nbx) << 16) | (c % nbx);
+    }
     __syncthreads();
 }
 
@@ -642,8 +664,9 @@ __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool
             for (int r = 0; r < R; r++)
                 if (valid[r]) {
                     float nx = 0.f, ny = 0.f;
-                    *x.n_root += (unsigned long long)near_sum(x, key[r], z[r].x, z[r].y, nx, ny);
-                    x.nfar[key[r]] = make_float2(acc[r].Dx - nx, acc[r].Dy - ny);
+                    const int code = d * nr + x.nrank[key[r]];
+                    *x.n_root += (unsigned long long)near_sum(x, d, x.ncell[code], z[r].x, z[r].y, nx, ny);
+                    x.nfar[code] = make_float2(acc[r].Dx - nx, acc[r].Dy - ny);
                 }
         }
 #pragma unroll
@@ -652,68 +675,94 @@ __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool
     }
 }
 
-// One sweep of a row between refreshes: each active root sums its stars as in the full sweep,
-// its near roots exactly at their current positions, and adds its stored far part.  Each
-// thread takes RL roots (slots base, base + P, ...) whose independent loads and sums the
-// compiler may interleave; one root per thread measured fastest (two: 6% slower).
-template <int RL>
-__device__ void sweep_light(const Ctx<float>& x, int A0, int A1, float cph0, float sph0, float cph1, float sph1,
-                            int* s_maxit) {
+// Star terms of a root at z for a light sweep: those of cell_part with one thread per root,
+// but the cell's header, its first 8 near-star indices and its expansion coefficients are
+// requested together (they depend on the cell alone), so that they cost one memory round trip.
+__device__ __forceinline__ void star_part_light(const Ctx<float>& x, float zx, float zy, Acc<float>& acc) {
     const TK& K = *x.k;
-    const int nr = K.nr, n = K.n, P = blockDim.x, A = A0 + A1;
+    const int n = K.n;
     const float4* gs = (const float4*)K.stars;
-    for (int base = threadIdx.x; base < A; base += RL * P) {
-        int key[RL], cell[RL];
-        bool valid[RL];
-        float2 z[RL];
-        Acc<float> acc[RL];
-#pragma unroll
-        for (int r = 0; r < RL; r++) {
-            const int slot = base + r * P;
-            valid[r] = slot < A;
-            const int sl = valid[r] ? slot : base;
-            key[r] = sl < A0 ? x.act[sl] : x.act[nr + sl - A0];
-        }
-#pragma unroll
-        for (int r = 0; r < RL; r++) {
-            z[r] = x.cur[key[r]];
-            acc[r] = Acc<float>{0, 0, 0, 0, 0, 0, 0, 0, 0};
-            cell[r] = far_cell<float>(K, z[r].x, z[r].y);
-        }
-#pragma unroll
-        for (int r = 0; r < RL; r++) {
-            if (!valid[r]) continue;
-            *x.n_terms += (unsigned long long)(cell[r] >= 0 ? K.tcells[cell[r]].near_cnt : n);
-            *x.n_far += cell[r] >= 0 ? 1ull : 0ull;
-            if (cell[r] >= 0) {
-                cell_part<float>(x, cell[r], z[r].x, z[r].y, 0, 1, acc[r]);
-            } else if (x.resident) {
+    int c = -1;
+    if (K.tfmm.ok) {
+        const float fx = floorf((zx - K.tfmm.x0) * K.tfmm.inv_b);
+        const float fy = floorf((zy - K.tfmm.y0) * K.tfmm.inv_b);
+        if (fx >= 0.f && fy >= 0.f && fx < (float)K.tfmm.nbx && fy < (float)K.tfmm.nby)
+            c = (int)fy * K.tfmm.nbx + (int)fx;
+    }
+    int cnt = -1;
+    float4 hd = make_float4(0.f, 0.f, 0.f, 0.f);
+    int4 i0 = make_int4(0, 0, 0, 0), i1 = i0;
+    if (c >= 0) {
+        hd = *(const float4*)(K.tcells + c);  // cx, cy, near_cnt, far_m_d2
+        const int4* nl4 = (const int4*)(K.tnear + (size_t)c * TFMM_NEAR_MAX);
+        i0 = nl4[0];
+        i1 = nl4[1];
+        cnt = __float_as_int(hd.z);
+    }
+    *x.n_terms += (unsigned long long)(cnt >= 0 ? cnt : n);
+    *x.n_far += cnt >= 0 ? 1ull : 0ull;
+    if (cnt < 0) {
+        if (x.resident) {
 #pragma unroll 4
-                for (int j = 0; j < n; j++) acc_star(z[r].x, z[r].y, x.s_star[j], acc[r]);
-            } else {
+            for (int j = 0; j < n; j++) acc_star(zx, zy, x.s_star[j], acc);
+        } else {
 #pragma unroll 4
-                for (int j = 0; j < n; j++) acc_star(z[r].x, z[r].y, gs[j], acc[r]);
-            }
+            for (int j = 0; j < n; j++) acc_star(zx, zy, gs[j], acc);
         }
-        float Dx[RL], Dy[RL];
+        return;
+    }
+    const int id[8] = {i0.x, i0.y, i0.z, i0.w, i1.x, i1.y, i1.z, i1.w};
 #pragma unroll
-        for (int r = 0; r < RL; r++) {
-            Dx[r] = 0.f;
-            Dy[r] = 0.f;
-            if (valid[r]) *x.n_root += (unsigned long long)near_sum(x, key[r], z[r].x, z[r].y, Dx[r], Dy[r]);
+    for (int q = 0; q < 8; q++)
+        if (q < cnt) acc_star(zx, zy, x.resident ? x.s_star[id[q]] : gs[id[q]], acc);
+    const int* nl = K.tnear + (size_t)c * TFMM_NEAR_MAX;
+    for (int q = 8; q < cnt; q++) {
+        const int j = nl[q];
+        acc_star(zx, zy, x.resident ? x.s_star[j] : gs[j], acc);
+    }
+    float ux, uy, sx, sy, hx, hy;
+    far_eval(K.tcoeff + (size_t)c * TFMM_P, zx - hd.x, zy - hd.y, ux, uy, sx, sy, hx, hy);
+    acc.Cx += ux;
+    acc.Cy += uy;
+    acc.Ax -= sx;
+    acc.Ay -= sy;
+    acc.Bx += hx;
+    acc.By += hy;
+    acc.Am += hd.w;
+}
+
+// One sweep of a row between refreshes: each active root sums its stars as in the full sweep,
+// its near roots exactly at their current positions, and adds its stored far part.  One root
+// per thread (two interleaved per thread measured 6% slower).  Positions, cells, far parts and
+// refresh positions are read by code (in shared memory when they fit).  ordered: the list is
+// the refresh's cell order itself (a row's first sweep), so slot s holds code s (direction 0)
+// or nr + s - A0 (direction 1) and neighbouring threads read neighbouring entries.
+__device__ void sweep_light(const Ctx<float>& x, bool ordered, int A0, int A1, float cph0, float sph0, float cph1,
+                            float sph1, int* s_maxit) {
+    const TK& K = *x.k;
+    const int nr = K.nr, P = blockDim.x, A = A0 + A1;
+    for (int slot = threadIdx.x; slot < A; slot += P) {
+        const int d = slot < A0 ? 0 : 1;
+        int key, code;
+        if (ordered) {
+            code = d ? nr + slot - A0 : slot;
+            key = x.nord[code];
+        } else {
+            key = d ? x.act[nr + slot - A0] : x.act[slot];
+            code = d * nr + x.nrank[key];
         }
-#pragma unroll
-        for (int r = 0; r < RL; r++) {
-            if (!valid[r]) continue;
-            const int d = key[r] >= nr ? 1 : 0;
-            const float2 f = x.nfar[key[r]];
-            acc[r].Dx = Dx[r] + f.x;
-            acc[r].Dy = Dy[r] + f.y;
-            finish_root<float>(x, key[r], z[r], acc[r], d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
-            const float2 zn = x.nxt[key[r]], zr = x.nref[key[r]];
-            const float ex = zn.x - zr.x, ey = zn.y - zr.y;
-            if (!(ex * ex + ey * ey <= x.s_nlim2[d])) *x.s_nesc = 1;
-        }
+        const float2 z = x.npos[code];
+        Acc<float> acc = Acc<float>{0, 0, 0, 0, 0, 0, 0, 0, 0};
+        star_part_light(x, z.x, z.y, acc);
+        float Dx = 0.f, Dy = 0.f;
+        *x.n_root += (unsigned long long)near_sum(x, d, x.ncell[code], z.x, z.y, Dx, Dy);
+        const float2 f = x.nfar[code];
+        acc.Dx = Dx + f.x;
+        acc.Dy = Dy + f.y;
+        const float2 zn = finish_root<float>(x, key, z, acc, d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
+        const float2 zr = x.nref[code];
+        const float ex = zn.x - zr.x, ey = zn.y - zr.y;
+        if (!(ex * ex + ey * ey <= x.s_nlim2[d])) *x.s_nesc = 1;
     }
 }
 
@@ -812,7 +861,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
     Ctx<T> xs = x;
     xs.act = x.act + lo;  // this CTA's lists: [lo, lo + A0) and [nr + lo, nr + lo + A1)
     if constexpr (sizeof(T) != 4 || WIDE) mode = SUM_FULL;
-    const bool split = mode != SUM_FULL;
+    bool split = mode != SUM_FULL;  // (cleared when a sweep's few roots are summed exactly instead)
     if constexpr (sizeof(T) == 4 && !WIDE) {
         if (split) {
             __syncthreads();
@@ -825,6 +874,8 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         }
     }
     int Ap0 = 0, Ap1 = 0;  // previous sweep's list lengths (split sweeps)
+    bool recap = false;    // a cold row's iterate left its limit: new cells and far parts first
+    bool esc = false;      // a warm row's iterate left its limit: the caller solves the row again
     for (int iter = 0;; iter++) {
         __syncthreads();
         if (tid < 2) s_count[tid] = 0;
@@ -863,6 +914,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             }
         }
         if (!listed) {
+            xs.act = x.act + lo;
             for (int i = tid; i < 2 * W; i += P) {
                 const int d = i >= W;
                 const int key = d * nr + lo + (i - d * W);
@@ -894,10 +946,35 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             if constexpr (WIDE) cluster_sync();  // the barrier the other CTAs take before their copies
             continue;
         }
+        if constexpr (sizeof(T) == 4 && !WIDE) {
+            // A light sweep costs about one root update's latency however few roots it
+            // holds, an exact sweep of A roots about A nr terms spread over the block: below
+            // A nr = 1024 P the rest of the row is summed exactly (always valid; the next
+            // row's prediction guard still checks every position against its refresh).
+            if (split && iter > 0 && mode == SUM_LIGHT && (int64_t)A * nr <= (int64_t)P * 1024) {
+                split = false;
+                mode = SUM_FULL;
+                recap = false;
+            }
+            if (recap) {  // block-uniform
+                // cells at the current positions and an exact sweep capturing the far parts
+                // again: from here on the split holds as after any refresh
+                if (a0) near_build(x, 0);
+                if (a1) near_build(x, 1);
+                for (int i = tid; i < nr; i += P) {
+                    if (a0) x.npos[i] = x.cur[x.nord[i]];
+                    if (a1) x.npos[nr + i] = x.cur[x.nord[nr + i]];
+                }
+                if (tid == 0) *x.s_nesc = 0;
+                __syncthreads();
+                mode = SUM_CAPTURE;
+                recap = false;
+            }
+        }
         bool blocked = false;
         if constexpr (sizeof(T) == 4 && !WIDE) {
             if (mode == SUM_LIGHT) {
-                sweep_light<1>(xs, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                sweep_light(xs, iter == 0, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
                 blocked = true;
             }
         }
@@ -981,8 +1058,9 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 if constexpr (sizeof(T) == 4 && !WIDE) {
                     if (mode == SUM_CAPTURE && valid && lane == 0) {
                         float nx = 0.f, ny = 0.f;
-                        *x.n_root += (unsigned long long)near_sum(x, key, z.x, z.y, nx, ny);
-                        x.nfar[key] = make_float2(acc.Dx - nx, acc.Dy - ny);
+                        const int code = d * nr + x.nrank[key];
+                        *x.n_root += (unsigned long long)near_sum(x, d, x.ncell[code], z.x, z.y, nx, ny);
+                        x.nfar[code] = make_float2(acc.Dx - nx, acc.Dy - ny);
                     }
                 }
                 if (valid && lane == 0) finish_root<T>(x, key, z, acc, d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
@@ -992,6 +1070,17 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         // every CTA of a cluster has finished reading the positions before any is updated
         if constexpr (WIDE) cluster_sync();
         else __syncthreads();
+        // an iterate beyond its limit (only light sweeps set the flag): a cold row, with no
+        // prediction to fall back on, refreshes the split; a warm row stops here and is solved
+        // again from its predictions
+        if constexpr (sizeof(T) == 4 && !WIDE) {
+            const bool e = split && *x.s_nesc;
+            if (cold) recap = e;
+            else if (e) {
+                esc = true;
+                break;
+            }
+        }
         for (int i = tid; i < A; i += P) {
             const int key = i < A0 ? xs.act[i] : xs.act[nr + i - A0];
             x.cur[key] = x.nxt[key];
@@ -1013,8 +1102,6 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         int u2 = 0;
         cluster_sum3(x, m0, m1, u2);
     }
-    int esc = 0;
-    if constexpr (sizeof(T) == 4 && !WIDE) esc = split && *x.s_nesc;
     return (m0 ? 1 : 0) | (m1 ? 2 : 0) | (esc ? 4 : 0);
 }
 
@@ -1083,20 +1170,11 @@ __device__ __forceinline__ void seed_guesses(const Ctx<T>& x, int d, T cph, T sp
                 const TCell tc = K.tcells[cell];
                 const int* nl = K.tnear + (size_t)cell * TFMM_NEAR_MAX;
                 for (int q = 0; q < tc.near_cnt; q++) add(gs[nl[q]], nl[q]);
-                const float tx = (float)si.x - tc.cx, ty = (float)si.y - tc.cy;
-                const float4* L = K.tcoeff + (size_t)cell * TFMM_P;
-                float b0x = L[TFMM_P - 1].z, b0y = L[TFMM_P - 1].w, b1x = 0.f, b1y = 0.f;
-                for (int kk = TFMM_P - 2; kk >= 0; kk--) {
-                    const float4 c4 = L[kk];
-                    const float n1x = fmaf(b1x, tx, fmaf(-b1y, ty, b0x)), n1y = fmaf(b1x, ty, fmaf(b1y, tx, b0y));
-                    const float n0x = fmaf(b0x, tx, fmaf(-b0y, ty, c4.z)), n0y = fmaf(b0x, ty, fmaf(b0y, tx, c4.w));
-                    b1x = n1x;
-                    b1y = n1y;
-                    b0x = n0x;
-                    b0y = n0y;
-                }
-                ax -= (T)b1x;
-                ay -= (T)b1y;
+                float ux, uy, sx, sy, hx, hy;
+                far_eval(K.tcoeff + (size_t)cell * TFMM_P, (float)si.x - tc.cx, (float)si.y - tc.cy, ux, uy, sx, sy,
+                         hx, hy);
+                ax -= (T)sx;
+                ay -= (T)sy;
             }
             const T den = ax * ax + ay * ay;
             // w = -m_i / c_i, and its principal square root
@@ -1187,11 +1265,20 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
         x.nrank = (int*)nb;
         nb += sizeof(int) * 2 * (size_t)nr;
         x.act2 = (int*)nb;
+        nb += sizeof(int) * 2 * (size_t)nr;
+        x.ncell = (int*)nb;
         if (nr <= K.near_cap) {
-            // ordered positions and cell starts in shared memory, after the root tiles
+            // ordered positions and cell starts in shared memory, after the root tiles, and
+            // (near_ext) the far parts, refresh positions and cells after them
             unsigned char* ns = (unsigned char*)(x.s_root + 2 * TR);
             x.npos = (float2*)ns;
             x.ncst = (int*)(ns + sizeof(float2) * 2 * (size_t)nr);
+            if (K.near_ext) {
+                float2* ne = (float2*)(((uintptr_t)(x.ncst + 2 * (size_t)(x.ncm + 1)) + 15) & ~(uintptr_t)15);
+                x.nfar = ne;
+                x.nref = ne + 2 * (size_t)nr;
+                x.ncell = (int*)(ne + 4 * (size_t)nr);
+            }
         }
     }
     __shared__ int s_ngrid[4], s_nesc;
@@ -1221,7 +1308,11 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
         seed_guesses<T>(x, 0, (T)ph.x, (T)ph.y);
     }
     for (int k = lo + tid; k < hi; k += P) x.conv[nr + k] = 1;
-    solve_rows<T, WIDE>(x, true, false, c, -1, K.max_iter_cold, true, true, s_count, &s_maxit);
+    const int KR = (sizeof(T) == 4 && !WIDE) ? K.root_refresh : 0;
+    // the cold row splits its root sum too: cells and far parts at the guesses, refreshed
+    // whenever an iterate leaves its limit
+    solve_rows<T, WIDE>(x, true, false, c, -1, K.max_iter_cold, true, true, s_count, &s_maxit,
+                        KR >= 2 ? SUM_CAPTURE : SUM_FULL);
 
     C* zrows = (C*)K.zrows;
     C* seam = (C*)K.seam;
@@ -1243,13 +1334,15 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     __shared__ int s_refresh;
     if (tid == 0) s_hist[0] = s_hist[1] = 0;
     if (tid == 0) s_refresh = 1;
-    const int KR = (sizeof(T) == 4 && !WIDE) ? K.root_refresh : 0;
     for (int64_t t = 1;; t++) {
         const bool a0 = c - t >= b0, a1 = c + t <= b1;
         if (!a0 && !a1) break;
         const int64_t r0 = c - t, r1 = c + t;
         __syncthreads();
         const bool refresh_due = s_refresh != 0;
+        int mode = SUM_FULL;
+        if (KR >= 2) mode = (refresh_due || (t - 1) % KR == 0) ? SUM_CAPTURE : SUM_LIGHT;
+        bool out = false;  // a prediction beyond its displacement limit (light rows)
         for (int i = tid; i < 2 * (hi - lo); i += P) {
             const int dd = i >= hi - lo;
             const int k = dd * nr + lo + (i - dd * (hi - lo));
@@ -1279,32 +1372,23 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
                     x.npred[k] = g;
                     // cells from an earlier refresh: the prediction goes to its place in cell
                     // order (a refresh row gathers all positions again after its new cells)
-                    if (!refresh_due) x.npos[(k >= nr ? nr : 0) + x.nrank[k]] = g;
+                    if (!refresh_due) {
+                        const int code = (k >= nr ? nr : 0) + x.nrank[k];
+                        x.npos[code] = g;
+                        if (mode == SUM_LIGHT) {
+                            const float2 r = x.nref[code];
+                            const float ex = g.x - r.x, ey = g.y - r.y;
+                            out |= !(ex * ex + ey * ey <= s_nlim2[dd]);
+                        }
+                    }
                 }
             }
             x.conv[k] = 0;
             x.it[k] = 0;
             x.dprev[k] = FLT_MAX;
         }
-        int mode = SUM_FULL;
-        if (KR >= 2) {
-            mode = (s_refresh || (t - 1) % KR == 0) ? SUM_CAPTURE : SUM_LIGHT;
-            if (mode == SUM_LIGHT) {
-                // a prediction beyond its displacement limit: refresh at this row
-                bool out = false;
-                if constexpr (sizeof(T) == 4) {
-                    for (int i = tid; i < 2 * (hi - lo); i += P) {
-                        const int dd = i >= hi - lo;
-                        if (!(dd ? a1 : a0)) continue;
-                        const int k = dd * nr + lo + (i - dd * (hi - lo));
-                        const float2 g = x.npred[k], r = x.nref[k];
-                        const float ex = g.x - r.x, ey = g.y - r.y;
-                        out |= !(ex * ex + ey * ey <= s_nlim2[dd]);
-                    }
-                }
-                if (__syncthreads_or(out)) mode = SUM_CAPTURE;
-            }
-        }
+        // a prediction beyond its displacement limit: refresh at this row
+        if (mode == SUM_LIGHT && __syncthreads_or(out)) mode = SUM_CAPTURE;
         int bad = solve_rows<T, WIDE>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit, mode);
         if (bad & 4) {
             // an iterate went beyond its limit: this row again from its predictions, with the
@@ -1449,6 +1533,7 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
         K.tcoeff = t.tcoeff;
         K.root_refresh = B.root_refresh;
         K.near_cap = B.near_cap;
+        K.near_ext = B.near_ext;
         if (threadIdx.x == 0) s_maxit = 0;
         n_terms = 0;
         n_far = 0;
@@ -1460,8 +1545,10 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
 }
 
 // Shared memory of a tracing CTA: a star tile of min(n, TS) stars, then the root tiles, then
-// (near_cap > 0) the split's ordered positions and cell starts for rows of up to near_cap roots.
-size_t tracer_smem_bytes(bool fp64, int64_t n, int near_cap) {
+// (near_cap > 0) the split's ordered positions and cell starts for rows of up to near_cap roots,
+// then, when they fit in an SM's 227 KB (tracer_near_ext), its far parts, refresh positions and
+// cells.
+static size_t tracer_smem_base(bool fp64, int64_t n, int near_cap) {
     const int64_t ts = std::min<int64_t>(n, fp64 ? CT<double>::TS : CT<float>::TS);
     size_t b = fp64 ? ts * sizeof(StarD) + 2 * TR * sizeof(double2) : ts * sizeof(float4) + 2 * TR * sizeof(float2);
     if (near_cap > 0)
@@ -1469,12 +1556,26 @@ size_t tracer_smem_bytes(bool fp64, int64_t n, int near_cap) {
     return b;
 }
 
+static size_t near_ext_bytes(int near_cap) {
+    return 16 + (size_t)2 * near_cap * (2 * sizeof(float2) + sizeof(int));
+}
+
+bool tracer_near_ext(int64_t n, int near_cap) {
+    return near_cap > 0 && tracer_smem_base(false, n, near_cap) + near_ext_bytes(near_cap) <= (size_t)227 * 1024;
+}
+
+size_t tracer_smem_bytes(bool fp64, int64_t n, int near_cap) {
+    size_t b = tracer_smem_base(fp64, n, near_cap);
+    if (!fp64 && tracer_near_ext(n, near_cap)) b += near_ext_bytes(near_cap);
+    return b;
+}
+
 size_t tracer_work_stride(int64_t nr, size_t elem) {
     size_t b = (size_t)(2 * nr) * (4 * elem + 4 * 4);
     // near/far split of the root sum: far part, ordered, refresh and predicted positions
-    // (float2), cell, ordered index, rank and a second active list (int) per root; cell starts
-    // and scatter counters per direction
-    b += (size_t)(2 * nr) * (4 * sizeof(float2) + 4 * sizeof(int)) +
+    // (float2), cell by key, ordered index, rank, a second active list and cell by code (int)
+    // per root; cell starts and scatter counters per direction
+    b += (size_t)(2 * nr) * (4 * sizeof(float2) + 5 * sizeof(int)) +
          (size_t)2 * (2 * (size_t)near_cells_max((int)nr) + 1) * sizeof(int) + 16;
     return (b + 255) / 256 * 256;
 }
@@ -1588,6 +1689,7 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
     K.tnear = a.f->tnear;
     K.tcoeff = a.f->tcoeff;
     K.near_cap = (!fp64 && a.cluster <= 1 && a.root_refresh >= 2 && a.f->nr <= NEAR_SMEM_NR) ? (int)a.f->nr : 0;
+    K.near_ext = tracer_near_ext(a.f->n, K.near_cap) ? 1 : 0;
     const size_t smem = tracer_smem_bytes(fp64, a.f->n, K.near_cap);
     cudaError_t e;
     if (a.cluster > 1) {
@@ -1859,7 +1961,9 @@ cudaError_t launch_trace_batch(const BatchTraceArgs& b, int grid, int threads, c
     const size_t smem = tracer_smem_bytes(false, (int64_t)CT<float>::TS, b.near_cap);
     cudaError_t e = cudaFuncSetAttribute(trace_batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    trace_batch_kernel<float><<<grid, threads, smem, st>>>(b);
+    BatchTraceArgs a = b;
+    a.near_ext = tracer_near_ext((int64_t)CT<float>::TS, b.near_cap) ? 1 : 0;  // as the size above
+    trace_batch_kernel<float><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1907,7 +2011,9 @@ cudaError_t launch_phase_batch(const TraceTask* tasks, int count, int64_t max_m,
 // Tracer far-field tables (built once per field): one warp per cell.  Near stars (the 5x5
 // block of cells around it) are listed in star order; every other star (at least 2.5
 // cells from the centre, while a root in the cell is within 0.71 cells) adds to the FP32
-// local expansions U_k = -sum 1/(z_i - c)^(k+1) and L_k = -sum m_i/(z_i - c)^(k+1).
+// local expansions U_k = -sum 1/(z_i - c)^(k+1) and L_k = -sum m_i/(z_i - c)^(k+1); the
+// table keeps U_k and the coefficients S1'_k = (k + 1) L_(k+1) of the derivative of S1, packed
+// as far_eval reads them.
 // ----------------------------------------------------------------------------------
 __global__ void tracer_far_field_kernel(const float4* s32, int n, TfmmParams P, TCell* cells, int* near,
                                         float4* coeff) {
@@ -1972,7 +2078,11 @@ __global__ void tracer_far_field_kernel(const float4* s32, int n, TfmmParams P, 
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int k = 0; k < TFMM_P; k++)
-            if (k == lane) v = make_float4(ux[k], uy[k], lx[k], ly[k]);
+            if (k == lane) {
+                const float dx = k + 1 < TFMM_P ? (float)(k + 1) * lx[k + 1 < TFMM_P ? k + 1 : k] : 0.f;
+                const float dy = k + 1 < TFMM_P ? (float)(k + 1) * ly[k + 1 < TFMM_P ? k + 1 : k] : 0.f;
+                v = make_float4(ux[k], dx, uy[k], dy);
+            }
         coeff[(size_t)cell * TFMM_P + lane] = v;
     }
     if (lane == 0) {

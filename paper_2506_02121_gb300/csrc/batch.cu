@@ -98,6 +98,7 @@ cudaError_t enqueue(cc_batch* b, cudaStream_t st, bool capturing) {
     a.predictor = b->opt.predictor;
     a.root_refresh = b->opt.root_refresh;
     a.near_cap = b->near_cap;
+    a.near_ext = 0;  // set by launch_trace_batch
     if ((e = launch_trace_batch(a, b->grid, b->threads, st)) != cudaSuccess) return e;
     if ((e = rec(b->ev[1], st, capturing)) != cudaSuccess) return e;
     if ((e = launch_seam_join_batch(tasks, b->count, (const int2*)(ws + b->off_seams), b->nseams, b->max_nr, st)) !=

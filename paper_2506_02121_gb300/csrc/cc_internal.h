@@ -187,7 +187,7 @@ struct FieldDev {
     TfmmParams tfmm;
     TCell* tcells;    // nbx * nby
     int* tnear;       // nbx * nby * TFMM_NEAR_MAX star indices
-    float4* tcoeff;   // nbx * nby * TFMM_P: (U_k re, U_k im, L_k re, L_k im)
+    float4* tcoeff;   // nbx * nby * TFMM_P: (U_k re, S1'_k re, U_k im, S1'_k im), S1'_k = (k + 1) L_(k+1)
 };
 cudaError_t launch_tracer_far_field(const float4* s32, int n, const TfmmParams& P, TCell* cells, int* near,
                                     float4* coeff, cudaStream_t st);
@@ -242,6 +242,7 @@ struct BatchTraceArgs {
     int max_iter_cold, max_iter_warm, predictor;
     int root_refresh;
     int near_cap;           // shared-memory rows of the split (0: none)
+    int near_ext;           // tracer_near_ext(CT<float>::TS stars, near_cap)
 };
 
 // One field's points for the FP64 rescue of uncertified points.
@@ -285,6 +286,7 @@ __host__ __device__ inline int near_cells_max(int nr) { return nr / 4 + 64; }
 constexpr int NEAR_SMEM_NR = 4096;
 size_t tracer_work_stride(int64_t nr, size_t elem);
 size_t tracer_smem_bytes(bool fp64, int64_t n, int near_cap = 0);
+bool tracer_near_ext(int64_t n, int near_cap);
 int tracer_blocks_per_sm(bool fp64, int threads, int64_t n);
 int subchain_count(int64_t m, int64_t nr, const cc_options& o, int sms, int blocks_per_sm);
 constexpr int WIDE_MIN_NR = 4096;   // automatic cluster tracing from this many roots per row
