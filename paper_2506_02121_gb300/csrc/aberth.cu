@@ -552,10 +552,12 @@ __device__ void near_build(const Ctx<float>& x, int d) {
 
 // One sweep over the active FP32 roots with R roots per thread.  Slots [0, A0) hold the
 // direction-0 roots, [A0p, A0p + A1) the direction-1 roots, A0p = A0 rounded up to 32 R so
-// that a warp never mixes the directions and every root-tile load is a broadcast.
+// that a warp never mixes the directions and every root-tile load is a broadcast.  twin: the
+// two directions hold the same positions (the first rows either side of a cold row), so
+// direction 0's sums serve root k + nr too, which is then updated with direction 1's phase.
 template <int R, bool CAPTURE>
 __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool a1, int A0, int A1, float cph0,
-                                              float sph0, float cph1, float sph1, int* s_maxit) {
+                                              float sph0, float cph1, float sph1, int* s_maxit, bool twin = false) {
     using C = float2;
     constexpr int TS = CT<float>::TS;
     const TK& K = *x.k;
@@ -667,11 +669,15 @@ __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool
                     const int code = d * nr + x.nrank[key[r]];
                     *x.n_root += (unsigned long long)near_sum(x, d, x.ncell[code], z[r].x, z[r].y, nx, ny);
                     x.nfar[code] = make_float2(acc[r].Dx - nx, acc[r].Dy - ny);
+                    if (twin) x.nfar[nr + code] = x.nfar[code];
                 }
         }
 #pragma unroll
         for (int r = 0; r < R; r++)
-            if (valid[r]) finish_root<float>(x, key[r], z[r], acc[r], d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
+            if (valid[r]) {
+                finish_root<float>(x, key[r], z[r], acc[r], d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
+                if (twin) finish_root<float>(x, key[r] + nr, z[r], acc[r], cph1, sph1, s_maxit);
+            }
     }
 }
 
@@ -840,7 +846,7 @@ enum SumMode { SUM_FULL = 0, SUM_CAPTURE = 1, SUM_LIGHT = 2 };
 template <typename T, bool WIDE>
 __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int64_t row0, int64_t row1,
                                           int max_iter, bool cold, bool report, int* s_count, int* s_maxit,
-                                          int mode = SUM_FULL) {
+                                          int mode = SUM_FULL, bool twin = false) {
     using C = typename CT<T>::C;
     constexpr int TS = CT<T>::TS;
     const TK& K = *x.k;
@@ -869,8 +875,27 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         }
         if (mode == SUM_CAPTURE) {
             __syncthreads();
-            if (a0) near_build(x, 0);
-            if (a1) near_build(x, 1);
+            if (twin) {
+                // both directions at the same positions: direction 0's cells serve both
+                near_build(x, 0);
+                const int nc1 = x.s_ngrid[0] * x.s_ngrid[1] + 1;
+                for (int i = tid; i < nr; i += P) {
+                    x.nord[nr + i] = x.nord[i] + nr;
+                    x.nrank[nr + i] = x.nrank[i];
+                    x.ncell[nr + i] = x.ncell[i];
+                    x.nref[nr + i] = x.nref[i];
+                }
+                for (int c = tid; c < nc1; c += P) x.ncst[(x.ncm + 1) + c] = x.ncst[c];
+                if (tid == 0) {
+                    x.s_ngrid[2] = x.s_ngrid[0];
+                    x.s_ngrid[3] = x.s_ngrid[1];
+                    x.s_nlim2[1] = x.s_nlim2[0];
+                }
+                __syncthreads();
+            } else {
+                if (a0) near_build(x, 0);
+                if (a1) near_build(x, 1);
+            }
         }
     }
     int Ap0 = 0, Ap1 = 0;  // previous sweep's list lengths (split sweeps)
@@ -978,16 +1003,20 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 blocked = true;
             }
         }
-        if (mode != SUM_LIGHT && tid == 0) *x.n_root += (unsigned long long)A * nr;
+        // twin: direction 0's sweep updates both directions (its first sweep only)
+        const bool tw = twin && iter == 0;
+        const int SA1 = tw ? 0 : A1;
+        if (mode != SUM_LIGHT && tid == 0) *x.n_root += (unsigned long long)(A0 + SA1) * nr;
         if constexpr (sizeof(T) == 4) {
-            if (!blocked && A >= P) {
+            if (!blocked && A0 + SA1 >= P) {
                 const bool cap = !WIDE && mode == SUM_CAPTURE;
-                if (A >= 2 * P) {
-                    if (cap) sweep_blocked<4, !WIDE>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
-                    else sweep_blocked<4, false>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                const bool b1 = tw ? false : a1;
+                if (A0 + SA1 >= 2 * P) {
+                    if (cap) sweep_blocked<4, !WIDE>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
+                    else sweep_blocked<4, false>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
                 } else {
-                    if (cap) sweep_blocked<2, !WIDE>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
-                    else sweep_blocked<2, false>(xs, a0, a1, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                    if (cap) sweep_blocked<2, !WIDE>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
+                    else sweep_blocked<2, false>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
                 }
                 blocked = true;
             }
@@ -1389,7 +1418,12 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
         }
         // a prediction beyond its displacement limit: refresh at this row
         if (mode == SUM_LIGHT && __syncthreads_or(out)) mode = SUM_CAPTURE;
-        int bad = solve_rows<T, WIDE>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit, mode);
+        // the first rows either side of the cold row start from its positions (no history yet):
+        // one capture sweep serves both directions when every root of both is swept
+        const bool twin = sizeof(T) == 4 && !WIDE && t == 1 && a0 && a1 && mode == SUM_CAPTURE && nr >= P &&
+                          lo == 0 && hi == nr;
+        int bad = solve_rows<T, WIDE>(x, a0, a1, r0, r1, K.max_iter_warm, false, false, s_count, &s_maxit, mode,
+                                      twin);
         if (bad & 4) {
             // an iterate went beyond its limit: this row again from its predictions, with the
             // exact root sum in every sweep
