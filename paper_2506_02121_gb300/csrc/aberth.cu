@@ -901,9 +901,10 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
     int Ap0 = 0, Ap1 = 0;  // previous sweep's list lengths (split sweeps)
     bool recap = false;    // a cold row's iterate left its limit: new cells and far parts first
     bool esc = false;      // a warm row's iterate left its limit: the caller solves the row again
+    int* next = nullptr;   // split sweeps: the next list, already built by the last position update
     for (int iter = 0;; iter++) {
         __syncthreads();
-        if (tid < 2) s_count[tid] = 0;
+        if (!next && tid < 2) s_count[tid] = 0;
         __syncthreads();
         bool listed = false;
         if constexpr (sizeof(T) == 4 && !WIDE) {
@@ -925,6 +926,8 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                         s_count[0] = a0 ? nr : 0;
                         s_count[1] = a1 ? nr : 0;
                     }
+                } else if (next) {
+                    xs.act = next;  // (s_count holds its lengths)
                 } else {
                     // the previous list's unfrozen roots, into the other list
                     const int* src = xs.act;
@@ -1110,12 +1113,32 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 break;
             }
         }
-        for (int i = tid; i < A; i += P) {
-            const int key = i < A0 ? xs.act[i] : xs.act[nr + i - A0];
-            x.cur[key] = x.nxt[key];
-            if constexpr (sizeof(T) == 4 && !WIDE)
-                if (split) x.npos[(key >= nr ? nr : 0) + x.nrank[key]] = x.nxt[key];
+        next = nullptr;
+        if constexpr (sizeof(T) == 4 && !WIDE) {
+            if (split) {
+                // positions, and the unfrozen roots into the next list (the other list; after
+                // the first sweep, whose list is the cell order itself, the first one)
+                int* dst = xs.act == x.act ? x.act2 : x.act;
+                if (tid < 2) s_count[tid] = 0;
+                __syncthreads();
+                const bool ordered = xs.act == x.nord;
+                for (int i = tid; i < A; i += P) {
+                    const int d = i < A0 ? 0 : 1;
+                    const int key = d ? xs.act[nr + i - A0] : xs.act[i];
+                    const int code = ordered ? (d ? nr + i - A0 : i) : d * nr + x.nrank[key];
+                    const float2 zn = x.nxt[key];
+                    x.cur[key] = zn;
+                    x.npos[code] = zn;
+                    if (!x.conv[key]) dst[d * nr + atomicAdd(&s_count[d], 1)] = key;
+                }
+                next = dst;
+            }
         }
+        if (!next)
+            for (int i = tid; i < A; i += P) {
+                const int key = i < A0 ? xs.act[i] : xs.act[nr + i - A0];
+                x.cur[key] = x.nxt[key];
+            }
     }
     // directions that still hold unfrozen roots
     bool b0 = false, b1 = false;
