@@ -566,6 +566,7 @@ constexpr int FMM_SUB = 4;
 constexpr int FMM_SUB2 = FMM_SUB * FMM_SUB;
 constexpr int FMM_PS = 16;            // terms kept at a sub-cell centre
 constexpr int FMM_KS0 = 9;            // of which terms k >= FMM_KS0 in FP32
+constexpr int FMM_OCC_ROWS = 64;     // rows per thread of the occupancy pass
 constexpr int FMM_SUBPOOL = 1 << 20;  // sub-cell tables (occupied sub-cells) at most; cells beyond use the cell's
 constexpr float FMM_SUBR = 0.185f;    // sub-cell radius / b: 1.05 x the half-diagonal sqrt(2)/8 (so that
                                       // |z - c| <= 0.375 sqrt(2) b + 0.185 b <= 0.72 b, the cell bound's radius)
@@ -708,33 +709,41 @@ __global__ void fmm_setup_kernel(const float4* part, int nparts, float b_target,
     P->sub_used = 0;
 }
 
-// Occupied cells.  A warp takes one tracer column over 32 consecutive rows: one chain
-// (within a sub-range), whose points mostly share a cell, so after a warp-level match of the
-// cell indices one lane per distinct cell tests and marks it.
+// Occupied cells and sub-cells (a bit mask per cell).
 __global__ void fmm_occupy_kernel(const float2* z, int64_t rows, int64_t nr, FmmParams* P, unsigned* occ) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t col = w % nr, row = (w / nr) * 32 + lane;
-    if (w >= nr * ((rows + 31) / 32)) return;  // warp-uniform
-    // other warps may clear ok while this one runs: one read per warp keeps the return
-    // warp-uniform (the full-warp match below needs every lane)
-    if (!__shfl_sync(0xffffffffu, P->ok, 0)) return;
-    int cell = -1;  // < FMM_G^2 = 2^22
-    unsigned bit = 0;
-    if (row < rows) {
-        const float2 v = z[row * nr + col];
-        const int cx = fmm_cell(v.x, P->x0, P->inv_b), cy = fmm_cell(v.y, P->y0, P->inv_b);
-        if (cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby) {
-            cell = cy * P->nbx + cx;
-            bit = 1u << (fmm_subcell(v.y, P->y0, P->inv_b, cy) * FMM_SUB + fmm_subcell(v.x, P->x0, P->inv_b, cx));
-        } else {
-            P->ok = 0;
+    // one thread per (column, run of FMM_OCC_ROWS rows): neighbouring threads read neighbouring
+    // columns of a row (coalesced); a chain stays in one cell for many rows, so each thread ORs
+    // its sub-cell bits per cell it enters rather than per point
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t col = t % nr, r0 = (t / nr) * FMM_OCC_ROWS;
+    if (r0 >= rows || !P->ok) return;
+    const int64_t r1 = r0 + FMM_OCC_ROWS < rows ? r0 + FMM_OCC_ROWS : rows;
+    int cur = -1;  // < FMM_G^2 = 2^22
+    unsigned bits = 0;
+    for (int64_t rb = r0; rb < r1; rb += 4) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (rb + u < r1) v[u] = z[(rb + u) * nr + col];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (rb + u >= r1) break;
+            const int cx = fmm_cell(v[u].x, P->x0, P->inv_b), cy = fmm_cell(v[u].y, P->y0, P->inv_b);
+            if (!(cx >= 0 && cx < P->nbx && cy >= 0 && cy < P->nby)) {
+                P->ok = 0;
+                continue;
+            }
+            const int cell = cy * P->nbx + cx;
+            if (cell != cur) {
+                if (cur >= 0 && (occ[cur] & bits) != bits) atomicOr(occ + cur, bits);
+                cur = cell;
+                bits = 0;
+            }
+            // occ[cell]: bit s set when sub-cell s holds a traced point
+            bits |= 1u << (fmm_subcell(v[u].y, P->y0, P->inv_b, cy) * FMM_SUB + fmm_subcell(v[u].x, P->x0, P->inv_b, cx));
         }
     }
-    // occ[cell]: bit s set when sub-cell s holds a traced point
-    const unsigned same = __match_any_sync(0xffffffffu, cell);
-    const unsigned bits = __reduce_or_sync(same, bit);
-    if (cell >= 0 && lane == __ffs(same) - 1 && (occ[cell] & bits) != bits) atomicOr(occ + cell, bits);
+    if (cur >= 0 && (occ[cur] & bits) != bits) atomicOr(occ + cur, bits);
 }
 
 __global__ void fmm_slot_kernel(FmmParams* P, const unsigned* occ, int* slot, int2* boxlist) {
@@ -1407,8 +1416,8 @@ cudaError_t launch_polish_fmm(const PolishArgs& a, void* ws, cudaStream_t st) {
     fmm_setup_kernel<<<1, 32, 0, st>>>(part, 512, a.f->fmm_cell, cap, pool_cap, P);
     if ((e = cudaMemsetAsync(occ, 0, sizeof(unsigned) * (size_t)FMM_G * FMM_G, st)) != cudaSuccess) return e;
     {
-        const int64_t warps = ((a.m + 1 + 31) / 32) * a.nr;
-        fmm_occupy_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(a.zrows, a.m + 1, a.nr, P, occ);
+        const int64_t threads = ((a.m + 1 + FMM_OCC_ROWS - 1) / FMM_OCC_ROWS) * a.nr;
+        fmm_occupy_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a.zrows, a.m + 1, a.nr, P, occ);
     }
     fmm_slot_kernel<<<(unsigned)(((int64_t)FMM_G * FMM_G + 255) / 256), 256, 0, st>>>(P, occ, slot, boxlist);
     fmm_coarse_list_kernel<<<(unsigned)((FMM_COARSE_MAX + 255) / 256), 256, 0, st>>>(P, occ, clist);
