@@ -376,5 +376,16 @@ __host__ __device__ __forceinline__ int subchain_of_row(int64_t j, int64_t m, in
     while (s > 0 && subchain_begin(s, m, S) > j) s--;
     return (int)s;
 }
+// The same in 32-bit unsigned arithmetic where (m + 1) S < 2^32 (then every product below
+// fits), else the 64-bit form: equal results, a fraction of the instructions.
+__device__ __forceinline__ int subchain_of_row_fast(int64_t j, int64_t m, int64_t S) {
+    if ((m + 1) * S >= (int64_t)1 << 32) return subchain_of_row(j, m, S);
+    const unsigned jj = (unsigned)j, mm = (unsigned)m, SS = (unsigned)S;
+    if (jj >= mm) return (int)(SS - 1);
+    unsigned q = jj * SS / mm;
+    while (q + 1 < SS && (q + 1) * mm / SS <= jj) q++;
+    while (q > 0 && q * mm / SS > jj) q--;
+    return (int)q;
+}
 
 }  // namespace ccg

@@ -337,7 +337,7 @@ __device__ __forceinline__ void polish_body(const PolishK& K, const int64_t blk,
     if (valid) {
         row = point / K.nr;
         const int64_t g = point - row * K.nr;
-        const int s = subchain_of_row(row, K.m, K.S);
+        const int s = subchain_of_row_fast(row, K.m, K.S);
         const int32_t k = K.perm[(size_t)s * K.nr + g];
         const float2 z0 = K.zrows[(size_t)row * K.nr + k];
         z0x = z0.x;
@@ -1283,15 +1283,23 @@ __global__ void __launch_bounds__(PB_THREADS, 3) fmm_polish_kernel(PolishK K, co
     if (!Pm->ok) return;  // grid-uniform (set before this launch)
     const int lane = threadIdx.x & 31;
     const int64_t wg = blockIdx.x * (int64_t)(PB_THREADS / 32) + (threadIdx.x >> 5);
-    const int64_t g = wg % K.nr;
-    const int64_t row0 = (wg / K.nr) * 32 + lane;
+    int64_t g, rb;  // column and row block (32-bit division when it fits)
+    if (wg < ((int64_t)1 << 32)) {
+        const unsigned a = (unsigned)wg, b = (unsigned)K.nr;
+        g = a % b;
+        rb = a / b;
+    } else {
+        g = wg % K.nr;
+        rb = wg / K.nr;
+    }
+    const int64_t row0 = rb * 32 + lane;
     const bool valid = wg < K.nr * ((K.m + 32) / 32) && row0 <= K.m;
     int passes = 0;
     float est_max = 0.f;  // certified estimates are FP32 values
     if (valid) {
     const int64_t row = row0;
     const int64_t point = row * K.nr + g;
-    const int s = subchain_of_row(row, K.m, K.S);
+    const int s = subchain_of_row_fast(row, K.m, K.S);
     const int32_t k = K.perm[(size_t)s * K.nr + g];
     const float2 z0 = K.zrows[(size_t)row * K.nr + k];
     const int32_t it_in = K.iters_out ? K.iters_in[(size_t)row * K.nr + k] : 0;
