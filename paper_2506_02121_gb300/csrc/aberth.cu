@@ -747,10 +747,17 @@ __device__ void sweep_light(const Ctx<float>& x, bool ordered, int A0, int A1, f
                             float sph1, int* s_maxit) {
     const TK& K = *x.k;
     const int nr = K.nr, P = blockDim.x, A = A0 + A1;
+    // both directions whole: neighbouring lanes take the two directions' roots of one chain
+    // (key k and k + nr), which lie close together and mostly share a star cell
+    const bool paired = ordered && A0 == nr && A1 == nr;
     for (int slot = threadIdx.x; slot < A; slot += P) {
-        const int d = slot < A0 ? 0 : 1;
+        int d = slot < A0 ? 0 : 1;
         int key, code;
-        if (ordered) {
+        if (paired) {
+            d = slot & 1;
+            key = x.nord[slot >> 1] + d * nr;
+            code = d ? nr + x.nrank[key] : slot >> 1;
+        } else if (ordered) {
             code = d ? nr + slot - A0 : slot;
             key = x.nord[code];
         } else {
