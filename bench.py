@@ -48,11 +48,11 @@ if ROOT not in sys.path:
 METRIC = "critical-curve roots/s at 1e-9 theta_E (batched/served vs plain FP64); p99 latency"
 UNIT = "roots/s"
 
-# FP32 pipe operations (FADD, FMUL, FFMA each counted once) of the FP32 tracer (the dominant
-# kernel once the polish uses local expansions), csrc/aberth.cu: per star term summed
-# directly (acc_star), per root-root term (acc_root), and per evaluation of a cell's two
-# 14-term local expansions with the first two derivatives (13 Horner steps of 4 complex
-# multiply-adds, 16 FP32 ops each).
+# FP32 pipe operations (FADD, FMUL, FFMA each counted once, a packed FP32x2 operation twice)
+# of the FP32 tracer (the dominant kernel), csrc/aberth.cu: per star term summed directly
+# (acc_star), per root-root term (acc_root), and per evaluation of a cell's 14-term local
+# expansions of U and S1' with the derivative chain (far_eval: 13 Horner steps of 8 packed
+# FMAs, 16 FP32 ops each).
 TRACE_OPS_PER_STAR = 21
 TRACE_OPS_PER_ROOT = 6
 TRACE_OPS_PER_FAR_EVAL = 13 * 16
@@ -370,8 +370,8 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     extra = {
         "polish": {"ms": round(polish_ms, 3), "passes": rep["polish_passes"],
-                   "method": "local expansions (32 terms) for stars beyond a 5x5 block of cells, direct double-float "
-                             "sums for the rest"},
+                   "method": "stars beyond a 5x5 block of cells by local expansions (32 terms per cell, re-centred "
+                             "to 16 at each occupied 4x4 sub-cell), direct double-float sums for the rest"},
         "crossing_map": {"bytes": cross_bytes, "achieved_gbs": round(cross_bytes / (cross_ms / 1e3) / 1e9, 1),
                          "frac_hbm": round(cross_bytes / (cross_ms / 1e3) / 1e9 / hbm, 4)},
         "distance_map": {"bytes": dist_bytes, "achieved_gbs": round(dist_bytes / (dist_ms / 1e3) / 1e9, 1),
