@@ -1876,24 +1876,237 @@ __global__ void compose_perm_batch_kernel(const TraceTask* tasks) {
     compose_perm_body(t.S, t.nr, t.match, t.hits, t.perm, t.rep, threadIdx.x, blockDim.x);
 }
 
+// Seam join of the FP32 tracer by a grid, one CTA per seam.  The later sub-range's first row B
+// is binned into square cells of side h over its bounding box (about 2 roots per cell, at most
+// SEAM_G^2 cells) in scratch that the tracer no longer needs (the work area of sub-range s);
+// each root q of the seam row then looks at the 3x3 cells around its own.  Any root of B closer
+// than 0.9 h to q lies in those cells (FP32 cell assignment errs far below 0.1 h), so the nearest
+// root, with the full scan's tie rule (the lowest index among equal distances), is the full
+// scan's whenever it is closer than 0.9 h, and the ambiguity test is settled whenever the best
+// distance is below 1e-4 of min(second found, (0.9 h)^2).  Otherwise, and for a q outside the
+// grid or not finite, that q takes the full scan of seam_match_block.
+constexpr int SEAM_G = 256;
+constexpr int SEAM_T = 512;
+
+__device__ __forceinline__ void seam_consider(float2 b, float2 q, int j, float& best, float& second, int& bi) {
+    const float dx = b.x - q.x, dy = b.y - q.y;  // (this unit contracts no a*b + c: as the full scan)
+    const float d2 = dx * dx + dy * dy;
+    if (d2 < best || (d2 == best && j < bi)) {
+        second = best;
+        best = d2;
+        bi = j;
+    } else if (d2 < second) {
+        second = d2;
+    }
+}
+
+__global__ void __launch_bounds__(SEAM_T) seam_grid_kernel(const float2* zrows, const float2* seam, int64_t m, int S,
+                                                           int nr, char* work, size_t work_stride, int32_t* match,
+                                                           int32_t* hits, DevReport* rep) {
+    __shared__ float s_box[4][SEAM_T / 32];
+    __shared__ float s_g[4];  // x0, y0, 1/h, h
+    __shared__ int s_scan[32];
+    __shared__ int s_amb;
+    const int tid = threadIdx.x, P = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = P >> 5;
+    const int s = blockIdx.x;
+    const float2* B = zrows + (size_t)subchain_begin(s + 1, m, S) * nr;
+    const float2* Q = seam + (size_t)s * nr;
+    const int G = max(1, min(SEAM_G, (int)ceilf(sqrtf(0.5f * (float)nr))));
+    const int nc = G * G;
+    float2* pos = (float2*)(work + (size_t)s * work_stride);
+    int* idx = (int*)(pos + nr);
+    int* cst = idx + nr;   // nc + 1 cell starts
+    int* fill = cst + nc + 1;
+    // bounding box of the finite roots of B
+    float b[4] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f};  // min x, min y, -max x, -max y
+    for (int j = tid; j < nr; j += P) {
+        const float2 v = B[j];
+        if (isfinite(v.x) && isfinite(v.y)) {
+            b[0] = fminf(b[0], v.x);
+            b[1] = fminf(b[1], v.y);
+            b[2] = fminf(b[2], -v.x);
+            b[3] = fminf(b[3], -v.y);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        for (int o = 16; o > 0; o >>= 1) b[q] = fminf(b[q], __shfl_xor_sync(0xffffffffu, b[q], o));
+        if (lane == 0) s_box[q][wid] = b[q];
+    }
+    if (tid == 0) s_amb = 0;
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < nw; w++)
+            for (int q = 0; q < 4; q++) b[q] = fminf(b[q], s_box[q][w]);
+        const float span = fmaxf(fmaxf(-b[2] - b[0], -b[3] - b[1]), 0.f);
+        float h = span > 0.f && span < 1.0e38f ? span / (float)G * (1.f + 1.f / 1024.f) : 1.f;
+        if (!(h > 0.f)) h = 1.f;
+        s_g[0] = b[0] <= -b[2] ? b[0] : 0.f;
+        s_g[1] = b[1] <= -b[3] ? b[1] : 0.f;
+        s_g[2] = 1.f / h;
+        s_g[3] = h;
+    }
+    for (int c = tid; c < nc; c += P) fill[c] = 0;
+    __syncthreads();
+    const float x0 = s_g[0], y0 = s_g[1], ih = s_g[2], h = s_g[3];
+    auto cell_of = [&](float2 v, int& cx, int& cy) -> bool {
+        const float fx = (v.x - x0) * ih, fy = (v.y - y0) * ih;
+        if (!(fx >= 0.f && fy >= 0.f && fx < (float)G && fy < (float)G)) return false;
+        cx = min((int)fx, G - 1);
+        cy = min((int)fy, G - 1);
+        return true;
+    };
+    for (int j = tid; j < nr; j += P) {
+        int cx, cy;
+        if (cell_of(B[j], cx, cy)) atomicAdd(&fill[cy * G + cx], 1);
+    }
+    __syncthreads();
+    for (int c = tid; c < nc; c += P) cst[c + 1] = fill[c];
+    if (tid == 0) cst[0] = 0;
+    __syncthreads();
+    block_scan_inclusive(cst + 1, nc, s_scan);
+    for (int c = tid; c < nc; c += P) fill[c] = 0;
+    __syncthreads();
+    for (int j = tid; j < nr; j += P) {
+        const float2 v = B[j];
+        int cx, cy;
+        if (cell_of(v, cx, cy)) {
+            const int c = cy * G + cx;
+            const int at = cst[c] + atomicAdd(&fill[c], 1);
+            idx[at] = j;
+            pos[at] = v;
+        }
+    }
+    __syncthreads();
+    const float lim = 0.81f * h * h;  // (0.9 h)^2
+    int amb = 0;
+    for (int k = tid; k < nr; k += P) {
+        const float2 q = Q[k];
+        float best = 3.0e38f, second = 3.0e38f;
+        int bi = 0;
+        int cx, cy;
+        bool full = !cell_of(q, cx, cy);
+        if (!full) {
+            for (int yy = max(cy - 1, 0); yy <= min(cy + 1, G - 1); yy++) {
+                const int a = cst[yy * G + max(cx - 1, 0)], e = cst[yy * G + min(cx + 1, G - 1) + 1];
+                for (int t = a; t < e; t++) seam_consider(pos[t], q, idx[t], best, second, bi);
+            }
+            full = !(best < lim) || !(best <= 1e-4f * fminf(second, lim));
+        }
+        if (full) {
+            best = 3.0e38f;
+            second = 3.0e38f;
+            bi = 0;
+            for (int j = 0; j < nr; j++) {
+                const float2 v = B[j];
+                const float dx = v.x - q.x, dy = v.y - q.y;
+                const float d2 = dx * dx + dy * dy;
+                if (d2 < best) {
+                    second = best;
+                    best = d2;
+                    bi = j;
+                } else if (d2 < second) {
+                    second = d2;
+                }
+            }
+        }
+        match[(size_t)s * nr + k] = bi;
+        atomicAdd(&hits[(size_t)s * nr + bi], 1);
+        amb += !(best <= 1e-4f * second);
+    }
+    if (amb) atomicAdd(&s_amb, amb);
+    __syncthreads();
+    if (tid == 0 && s_amb) atomicAdd(&rep->seam_ambiguous, (unsigned long long)s_amb);
+}
+
+// Chain permutations in three passes over blocks of SEAM_BLK seams: each block's composition
+// L_b = match_(e-1) o ... o match_(b0), then the block starts perm_(b0) in sequence, then each
+// block's rows: 2 SEAM_BLK + S / SEAM_BLK dependent gathers per column instead of S.
+constexpr int SEAM_BLK = 16;
+
+__global__ void compose_local_kernel(int S, int nr, const int32_t* match, const int32_t* hits, int32_t* local,
+                                     DevReport* rep) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x, bk = blockIdx.y;
+    const int s0 = bk * SEAM_BLK, s1 = min(S - 1, s0 + SEAM_BLK);
+    int bad = 0;
+    if (g < nr) {
+        int p = g;
+        for (int s = s0; s < s1; s++) {
+            p = match[(size_t)s * nr + p];
+            bad += hits[(size_t)s * nr + g] != 1;
+        }
+        local[(size_t)bk * nr + g] = p;
+    }
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&rep->seam_ambiguous, (unsigned long long)bad);
+}
+
+__global__ void compose_starts_kernel(int nb, int nr, const int32_t* local, int32_t* start) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nr) return;
+    int p = g;
+    start[g] = p;
+    for (int bk = 0; bk < nb; bk++) {
+        p = local[(size_t)bk * nr + p];
+        start[(size_t)(bk + 1) * nr + g] = p;
+    }
+}
+
+__global__ void compose_fill_kernel(int S, int nr, const int32_t* match, const int32_t* start, int32_t* perm) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x, bk = blockIdx.y;
+    if (g >= nr) return;
+    const int s0 = bk * SEAM_BLK, s1 = min(S - 1, s0 + SEAM_BLK);
+    int p = start[(size_t)bk * nr + g];
+    if (bk == 0) perm[g] = g;
+    for (int s = s0; s < s1; s++) {
+        p = match[(size_t)s * nr + p];
+        perm[(size_t)(s + 1) * nr + g] = p;
+    }
+}
+
 cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int S, int64_t nr,
                              bool fp64, int32_t* match, int32_t* hits, int32_t* perm,
-                             DevReport* rep, cudaStream_t st) {
+                             DevReport* rep, cudaStream_t st, void* work, size_t work_stride) {
+    // the FP32 form joins through a grid in the sub-ranges' work areas (free once traced)
+    const bool grid_ok = !fp64 && work && work_stride >= seam_grid_bytes(nr) &&
+                         work_stride >= (size_t)(2 * ((S - 1 + SEAM_BLK - 1) / SEAM_BLK) + 1) * nr * sizeof(int32_t);
     if (S > 1) {
         cudaError_t e = cudaMemsetAsync(hits, 0, sizeof(int32_t) * (size_t)(S - 1) * nr, st);
         if (e != cudaSuccess) return e;
-        dim3 grid((unsigned)((nr + 255) / 256), (unsigned)(S - 1));
-        if (fp64)
-            seam_match_kernel<double2, double><<<grid, 256, 0, st>>>((const double2*)zrows, (const double2*)seam,
-                                                              m, S, (int)nr, match, hits, rep);
-        else
-            seam_match_kernel<float2, float><<<grid, 256, 0, st>>>((const float2*)zrows, (const float2*)seam,
-                                                             m, S, (int)nr, match, hits, rep);
+        if (grid_ok) {
+            seam_grid_kernel<<<(unsigned)(S - 1), SEAM_T, 0, st>>>((const float2*)zrows, (const float2*)seam, m, S,
+                                                                 (int)nr, (char*)work, work_stride, match, hits, rep);
+        } else {
+            dim3 grid((unsigned)((nr + 255) / 256), (unsigned)(S - 1));
+            if (fp64)
+                seam_match_kernel<double2, double><<<grid, 256, 0, st>>>((const double2*)zrows, (const double2*)seam,
+                                                                  m, S, (int)nr, match, hits, rep);
+            else
+                seam_match_kernel<float2, float><<<grid, 256, 0, st>>>((const float2*)zrows, (const float2*)seam,
+                                                                 m, S, (int)nr, match, hits, rep);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (grid_ok && S > 1) {
+        // (work area 0 again: the grids are done by stream order)
+        const int nb = (S - 1 + SEAM_BLK - 1) / SEAM_BLK;
+        int32_t* local = (int32_t*)work;
+        int32_t* start = local + (size_t)nb * nr;
+        const dim3 g2((unsigned)((nr + 127) / 128), (unsigned)nb);
+        compose_local_kernel<<<g2, 128, 0, st>>>(S, (int)nr, match, hits, local, rep);
+        compose_starts_kernel<<<(unsigned)((nr + 127) / 128), 128, 0, st>>>(nb, (int)nr, local, start);
+        compose_fill_kernel<<<g2, 128, 0, st>>>(S, (int)nr, match, start, perm);
+        return cudaGetLastError();
+    }
     compose_perm_kernel<<<(unsigned)((nr + 127) / 128), 128, 0, st>>>(S, (int)nr, match, hits, perm, rep);
     return cudaGetLastError();
+}
+
+// Scratch of one seam's grid: positions and indices of the row, cell starts and counters.
+size_t seam_grid_bytes(int64_t nr) {
+    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(SEAM_G, (int64_t)std::ceil(std::sqrt(0.5 * (double)nr))));
+    return (size_t)nr * (sizeof(float2) + sizeof(int)) + (size_t)(2 * G * G + 1) * sizeof(int);
 }
 
 // ----------------------------------------------------------------------------------

@@ -529,7 +529,7 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
     CC_CUDA(cudaEventRecord(f->ev[1], st), "event record");
     int32_t* perm = (int32_t*)(ws + L.off_perm);
     CC_CUDA(launch_seam_join(ws + L.off_zrows, ws + L.off_seam, m, L.S, nr, fp64, (int32_t*)(ws + L.off_match),
-                             (int32_t*)(ws + L.off_hits), perm, rep, st),
+                             (int32_t*)(ws + L.off_hits), perm, rep, st, ws + L.off_work, L.work_stride),
             "seam join");
     CC_CUDA(cudaEventRecord(f->ev[2], st), "event record");
     if (fp64) {

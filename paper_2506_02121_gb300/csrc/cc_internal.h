@@ -295,9 +295,12 @@ int tracer_max_clusters(int G, int threads, bool fp64);  // co-resident clusters
 
 cudaError_t launch_phase_table(double2* phase, int64_t m, cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st);
+// work, work_stride: the sub-ranges' tracer work areas (scratch of the FP32 form's grid join;
+// nullptr: the full scan)
 cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int S, int64_t nr,
                              bool fp64, int32_t* match, int32_t* hits, int32_t* perm,
-                             DevReport* rep, cudaStream_t st);
+                             DevReport* rep, cudaStream_t st, void* work = nullptr, size_t work_stride = 0);
+size_t seam_grid_bytes(int64_t nr);
 
 // Polish + caustic (mixed form) and the FP64 finalisation.
 struct PolishArgs {

@@ -208,8 +208,24 @@ struct dfc {
     df x, y;
 };
 
+// a1 b1 + a2 b2 in double-float with one normalisation: both high products and their sum
+// exact (two_prod, two_sum), the error terms and the four low-part cross products gathered by
+// FP32 adds and FMAs: 20 FP32 operations against 27 for two df_mul and a df_add, with the same
+// ~2^-46 relative rounding (the final fast two-sum assumes, as df_add does, that the sum does
+// not cancel below its accumulated error).
+__device__ __forceinline__ df df_dot2(df a1, df b1, df a2, df b2) {
+    const df p1 = two_prod(a1.hi, b1.hi), p2 = two_prod(a2.hi, b2.hi);
+    const df s1 = two_sum(p1.hi, p2.hi);
+    float e = __fadd_rn(__fadd_rn(p1.lo, p2.lo), s1.lo);
+    e = __fmaf_rn(a1.hi, b1.lo, e);
+    e = __fmaf_rn(a1.lo, b1.hi, e);
+    e = __fmaf_rn(a2.hi, b2.lo, e);
+    e = __fmaf_rn(a2.lo, b2.hi, e);
+    return fast_two_sum(s1.hi, e);
+}
+
 __device__ __forceinline__ dfc dfc_mul(const dfc& a, const dfc& b) {
-    return dfc{df_sub(df_mul(a.x, b.x), df_mul(a.y, b.y)), df_add(df_mul(a.x, b.y), df_mul(a.y, b.x))};
+    return dfc{df_dot2(a.x, b.x, df_neg(a.y), b.y), df_dot2(a.x, b.y, a.y, b.x)};
 }
 
 __device__ __forceinline__ dfc poly_Q_df(const SmoothPoly* P, df zx, df zy) {
@@ -820,8 +836,8 @@ __device__ __forceinline__ void fmm_acc_star(float* acc, int warp, int lane, con
         acc[a + FMM_ACC] = ax.lo;
         acc[a + 2 * FMM_ACC] = ay.hi;
         acc[a + 3 * FMM_ACC] = ay.lo;
-        const df nx = df_sub(df_mul(wx, ux), df_mul(wy, uy));  // w <- w u
-        const df ny = df_add(df_mul(wx, uy), df_mul(wy, ux));
+        const df nx = df_dot2(wx, ux, df_neg(wy), uy);  // w <- w u
+        const df ny = df_dot2(wx, uy, wy, ux);
         wx = nx;
         wy = ny;
     }
