@@ -118,6 +118,7 @@ struct TK {
     const TCell* tcells;
     const int* tnear;
     const float4* tcoeff;
+    float4* ext;  // FP32 form: this CTA's extent of the points written to zrows (may be null)
 };
 
 template <typename T>
@@ -1378,13 +1379,51 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
     auto dst = [&](int64_t row) -> C* {
         return (row == b1 && s < K.S - 1) ? seam + (size_t)s * nr : zrows + (size_t)row * nr;
     };
+    // extent of the points written to zrows (FP32 form; the far-field polish grids them):
+    // each output pass folds its values per thread, then per warp into order-preserving
+    // integer keys in shared memory (min x, min y, -max x, -max y; flag of a non-finite point)
+    __shared__ int s_ek[5];
+    if (tid < 4) s_ek[tid] = 0x7fffffff;
+    if (tid == 4) s_ek[4] = 0;
+    __syncthreads();
+    const bool want_ext = sizeof(T) == 4 && K.ext != nullptr;
+    auto fold = [&](const C* vals, int n_lo, int n_hi) {  // called by every thread
+        float e[4] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f};
+        int bad = 0;
+        for (int k = n_lo + tid; k < n_hi; k += P) {
+            const C v = vals[k];
+            const float vx = (float)v.x, vy = (float)v.y;
+            if (!(isfinite(vx) && isfinite(vy))) {
+                bad = 1;
+                continue;
+            }
+            e[0] = fminf(e[0], vx);
+            e[1] = fminf(e[1], vy);
+            e[2] = fminf(e[2], -vx);
+            e[3] = fminf(e[3], -vy);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            for (int off = 16; off > 0; off >>= 1) e[q] = fminf(e[q], __shfl_xor_sync(0xffffffffu, e[q], off));
+        bad = __any_sync(0xffffffffu, bad);
+        if ((tid & 31) == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int b = __float_as_int(e[q]);
+                atomicMin(&s_ek[q], b >= 0 ? b : b ^ 0x7fffffff);  // float order as int order
+            }
+            if (bad) s_ek[4] = 1;
+        }
+    };
     {
         C* o = dst(c);
+        const bool into_rows = !(c == b1 && s < K.S - 1);
         for (int k = lo + tid; k < hi; k += P) {
             o[k] = x.cur[k];
             x.cur[nr + k] = x.cur[k];
             K.iters[(size_t)c * nr + k] = x.it[k];
         }
+        if (want_ext && into_rows) fold(x.cur, lo, hi);
     }
     // s_hist[d]: rows of direction d already behind the current one that belong to the same
     // chains (a row re-solved from the star guesses has new column labels: history restarts)
@@ -1493,14 +1532,27 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
                 o[k] = x.cur[k];
                 K.iters[(size_t)r0 * nr + k] = x.it[k];
             }
+            if (want_ext) fold(x.cur, lo, hi);
         }
         if (a1) {
             C* o = dst(r1);
+            const bool into_rows = !(r1 == b1 && s < K.S - 1);
             for (int k = lo + tid; k < hi; k += P) {
                 o[k] = x.cur[nr + k];
-                if (!(r1 == b1 && s < K.S - 1)) K.iters[(size_t)r1 * nr + k] = x.it[nr + k];
+                if (into_rows) K.iters[(size_t)r1 * nr + k] = x.it[nr + k];
             }
+            if (want_ext && into_rows) fold(x.cur + nr, lo, hi);
         }
+    }
+    __syncthreads();
+    if (want_ext && tid == 0) {
+        float e[4];
+        for (int q = 0; q < 4; q++) {
+            const int b = s_ek[q];
+            e[q] = __int_as_float(b >= 0 ? b : b ^ 0x7fffffff);
+        }
+        // a NaN marks a non-finite point
+        K.ext[blockIdx.x] = make_float4(s_ek[4] ? __int_as_float(0x7fc00000) : e[0], e[1], -e[2], -e[3]);
     }
     __syncthreads();
 }
@@ -1597,6 +1649,7 @@ __global__ void __launch_bounds__(512, 1) trace_batch_kernel(BatchTraceArgs B) {
         K.tcoeff = t.tcoeff;
         K.root_refresh = B.root_refresh;
         K.near_cap = B.near_cap;
+        K.ext = nullptr;
         K.near_ext = B.near_ext;
         if (threadIdx.x == 0) s_maxit = 0;
         n_terms = 0;
@@ -1752,6 +1805,7 @@ cudaError_t launch_trace(const TraceArgs& a, bool fp64, cudaStream_t st) {
     K.tcells = a.f->tcells;
     K.tnear = a.f->tnear;
     K.tcoeff = a.f->tcoeff;
+    K.ext = fp64 ? nullptr : a.ext;
     K.near_cap = (!fp64 && a.cluster <= 1 && a.root_refresh >= 2 && a.f->nr <= NEAR_SMEM_NR) ? (int)a.f->nr : 0;
     K.near_ext = tracer_near_ext(a.f->n, K.near_cap) ? 1 : 0;
     const size_t smem = tracer_smem_bytes(fp64, a.f->n, K.near_cap);

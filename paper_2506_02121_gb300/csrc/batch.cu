@@ -318,6 +318,8 @@ int cc_batch_bind(cc_batch* b, double* const* z_out, double* const* w_out, void*
         const double per = cost / (double)b->S[f] + 20.0 * (double)b->nr[f] * (double)(fd.n + b->nr[f]);
         for (int s = 0; s < b->S[f]; s++) items.push_back({per, make_int2(f, s)});
         PolishArgs pa;
+        pa.ext = nullptr;
+        pa.ext_n = 0;
         pa.f = &b->dev[f];
         pa.m = b->m[f];
         pa.S = b->S[f];

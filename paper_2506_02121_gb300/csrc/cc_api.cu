@@ -122,6 +122,8 @@ CurveLayout curve_layout(const cc_field* f, int64_t m) {
     o += 256;
     L.off_work = o;
     o += L.work_stride * (size_t)L.S;
+    L.off_ext = o;
+    o += align256(sizeof(float4) * (size_t)L.S * (size_t)std::max(1, L.G));
     L.fmm = !fp64 && f->opt.far_field && f->opt.hp_arith == CC_HP_DFLOAT && f->dev.n >= FMM_MIN_STARS;
     L.off_fmm = o;
     if (L.fmm) o += align256(fmm_workspace_bytes((m + 1) * nr));
@@ -525,6 +527,7 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
     ta.root_refresh = f->opt.root_refresh;
     ta.threads = L.threads;
     ta.cluster = L.G;
+    ta.ext = fp64 ? nullptr : (float4*)(ws + L.off_ext);
     CC_CUDA(launch_trace(ta, fp64, st), "trace");
     CC_CUDA(cudaEventRecord(f->ev[1], st), "event record");
     int32_t* perm = (int32_t*)(ws + L.off_perm);
@@ -549,6 +552,8 @@ int cc_critical_curves(cc_field* f, int64_t m, double* z_out, double* w_out, int
                     "map caustics");
     } else {
         PolishArgs pa;
+        pa.ext = (const float4*)(ws + L.off_ext);
+        pa.ext_n = L.S * std::max(1, L.G);
         pa.f = &f->dev;
         pa.m = m;
         pa.S = L.S;

@@ -209,6 +209,8 @@ struct TraceArgs {
     int root_refresh;      // FP32 warm rows: exact far part of the root sum every root_refresh rows
     int threads;
     int cluster;           // CTAs per sub-range (> 1: one thread-block cluster per sub-range)
+    float4* ext;           // FP32 form, may be null: per CTA the extent (min x, min y, max x, max y) of
+                           // the points it wrote to zrows, x = NaN if one was not finite
 };
 
 // One field of a batched launch (device table entry).
@@ -276,6 +278,7 @@ struct CurveLayout {
     size_t elem;           // bytes per tracer complex (8 FP32, 16 FP64)
     size_t off_phase, off_zrows, off_seam, off_iters, off_match, off_hits, off_perm, off_work,
         off_report, off_list, off_nlist, off_fmm, total;
+    size_t off_ext;        // per tracing CTA: extent of the points it wrote (FP32 form)
     bool fmm;
     size_t work_stride;
 };
@@ -323,6 +326,8 @@ struct PolishArgs {
     int* rescue_count;
     int field_id;
     const int* skip_if;     // direct polish does nothing when *skip_if != 0 (may be null)
+    const float4* ext;      // far-field polish: ext_n partial extents of zrows from the tracer (null: the
+    int ext_n;              // polish measures them itself)
 };
 constexpr int FMM_MIN_STARS = 128;
 cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st);

@@ -440,6 +440,19 @@ __global__ void __launch_bounds__(PB_THREADS) polish_kernel(PolishK K) {
     polish_body<UNIT, FP64>(K, blockIdx.x, smem, &s_passes);
 }
 
+// The direct polish as the far-field path's fallback: a small grid striding over the blocks,
+// so that the usual case (*skip_if set: the far-field path did the job) costs one short launch.
+template <bool UNIT, bool FP64>
+__global__ void __launch_bounds__(PB_THREADS) polish_fallback_kernel(PolishK K, int64_t nblocks) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_passes;
+    if (*K.skip_if) return;  // uniform across the grid (set before this launch)
+    for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        polish_body<UNIT, FP64>(K, blk, smem, &s_passes);
+        __syncthreads();
+    }
+}
+
 // Batched: the blocks of all fields in one launch; each field's points start on a block
 // boundary, so every block polishes points of one field against that field's stars.
 __global__ void __launch_bounds__(PB_THREADS) polish_batch_kernel(const PolishK* tasks, int count) {
@@ -516,13 +529,24 @@ cudaError_t launch_polish(const PolishArgs& a, cudaStream_t st) {
     const unsigned blocks = (unsigned)((K.points + PB_THREADS - 1) / PB_THREADS);
     const size_t smem_df = TSB * (sizeof(float4) + 2 * sizeof(float2));
     const size_t smem_d = TSB * sizeof(StarD);
+    int sms = 1, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned fb_blocks = (unsigned)std::min<int64_t>(blocks, (int64_t)sms * 8);
     cudaError_t e;
 #define CC_LAUNCH_POLISH(U, D, SM)                                                                     \
     do {                                                                                               \
-        e = cudaFuncSetAttribute(polish_kernel<U, D>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                 (int)(SM));                                                           \
-        if (e != cudaSuccess) return e;                                                                \
-        polish_kernel<U, D><<<blocks, PB_THREADS, SM, st>>>(K);                                        \
+        if (K.skip_if) {                                                                               \
+            e = cudaFuncSetAttribute(polish_fallback_kernel<U, D>,                                     \
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(SM));          \
+            if (e != cudaSuccess) return e;                                                            \
+            polish_fallback_kernel<U, D><<<fb_blocks, PB_THREADS, SM, st>>>(K, (int64_t)blocks);       \
+        } else {                                                                                       \
+            e = cudaFuncSetAttribute(polish_kernel<U, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     (int)(SM));                                                       \
+            if (e != cudaSuccess) return e;                                                            \
+            polish_kernel<U, D><<<blocks, PB_THREADS, SM, st>>>(K);                                    \
+        }                                                                                              \
     } while (0)
     if (a.hp_fp64)
         CC_LAUNCH_POLISH(false, true, smem_d);
@@ -1436,8 +1460,13 @@ cudaError_t launch_polish_fmm(const PolishArgs& a, void* ws, cudaStream_t st) {
     float4* scoeff = (float4*)take(sizeof(float4) * FMM_PS * (size_t)subs);
     SubInfo* sinfo = (SubInfo*)take(sizeof(SubInfo) * (size_t)subs);
     cudaError_t e;
-    fmm_extent_kernel<<<512, 256, 0, st>>>(a.zrows, points, part);
-    fmm_setup_kernel<<<1, 32, 0, st>>>(part, 512, a.f->fmm_cell, cap, pool_cap, P);
+    // the points' extent: the tracer's per-CTA extents when it kept them, else one pass here
+    if (a.ext && a.ext_n > 0) {
+        fmm_setup_kernel<<<1, 32, 0, st>>>(a.ext, a.ext_n, a.f->fmm_cell, cap, pool_cap, P);
+    } else {
+        fmm_extent_kernel<<<512, 256, 0, st>>>(a.zrows, points, part);
+        fmm_setup_kernel<<<1, 32, 0, st>>>(part, 512, a.f->fmm_cell, cap, pool_cap, P);
+    }
     if ((e = cudaMemsetAsync(occ, 0, sizeof(unsigned) * (size_t)FMM_G * FMM_G, st)) != cudaSuccess) return e;
     {
         const int64_t threads = ((a.m + 1 + FMM_OCC_ROWS - 1) / FMM_OCC_ROWS) * a.nr;
