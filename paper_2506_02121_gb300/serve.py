@@ -210,7 +210,7 @@ class GpuExecutor:
     library default) or "fp64" (the paper's plain FP64 Aberth form with FP64 caustics), so
     that one request trace can be served by both."""
 
-    def __init__(self, slots: int, block_threads: int = 256, subchains: int = 0, device: int = 0,
+    def __init__(self, slots: int, block_threads: int = 0, subchains: int = 0, device: int = 0,
                  cache_bytes: int = 8 << 30, precision: str = "mixed"):
         import torch
 
