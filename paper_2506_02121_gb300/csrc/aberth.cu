@@ -389,11 +389,52 @@ __device__ __forceinline__ typename CT<T>::C finish_root(const Ctx<T>& x, int ke
 // motion allows.  A prediction beyond the limit makes its row a refresh row; an iterate
 // beyond it has its row solved again with the exact sum in every sweep.
 // ----------------------------------------------------------------------------------
+// Thread-block clusters: several CTAs share one phi sub-range (each updates a slice of the
+// roots and reads all of them); hardware cluster barriers order the sweeps, and per-CTA
+// counts are summed through distributed shared memory.
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of all CTAs of the cluster; global and shared writes before it are visible
+// to every thread of the cluster after it.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ int ld_cluster(const int* local, unsigned rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
+    unsigned ra;
+    int v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+    return v;
+}
+
 constexpr int NEAR_PER_CELL = 4;  // roots per cell on average over the bounding box
+
+// Loads of the split's arrays.  W: a thread-block cluster shares one sub-range, and the
+// arrays (in the sub-range's work area) are written by other SMs of the cluster between
+// cluster barriers: read through L2 (ld.cg), never a stale L1 line.  Otherwise a plain load
+// (shared or global memory).
+template <bool W, typename V>
+__device__ __forceinline__ V ldw(const V* p) {
+    if constexpr (W) return __ldcg(p);
+    else return *p;
+}
 
 // sum over the near set of a root of direction d in refresh cell cell (= (cy << 16) | cx) at
 // the positions in npos; returns the number of terms.  Its own entry contributes 0 (see
 // acc_root_f).
+template <bool W = false>
 __device__ __forceinline__ int near_sum(const Ctx<float>& x, int d, int cell, float zx, float zy, float& Dx,
                                         float& Dy) {
     const int nr = x.k->nr;
@@ -406,16 +447,16 @@ __device__ __forceinline__ int near_sum(const Ctx<float>& x, int d, int cell, fl
     f2p Dx2 = f2_pack(0.f, 0.f), Dy2 = Dx2;
     int cnt = 0;
     for (int yy = max(cy - 1, 0); yy <= min(cy + 1, nby - 1); yy++) {
-        const int i0 = cst[yy * nbx + xa], i1 = cst[yy * nbx + xb + 1];
+        const int i0 = ldw<W>(cst + yy * nbx + xa), i1 = ldw<W>(cst + yy * nbx + xb + 1);
         cnt += i1 - i0;
         int i = i0;
 #pragma unroll 4
         for (; i + 1 < i1; i += 2) {
-            const float2 r0 = p[i], r1 = p[i + 1];
+            const float2 r0 = ldw<W>(p + i), r1 = ldw<W>(p + i + 1);
             acc_root_f2(zxx, zyy, f2_pack(r0.x, r1.x), f2_pack(r0.y, r1.y), Dx2, Dy2);
         }
         if (i < i1) {
-            const float2 r = p[i];
+            const float2 r = ldw<W>(p + i);
             acc_root_f(zx, zy, r.x, r.y, Dx, Dy);
         }
     }
@@ -462,6 +503,10 @@ __device__ void block_scan_inclusive(int* a, int n, int* s_scan) {
 // current roots with about NEAR_PER_CELL roots per cell (at most ncm cells), every root's
 // cell, and the roots listed cell by cell (row-major), each cell in root-index order so that
 // the near sums add their terms in a fixed order.
+// W (a cluster shares the sub-range): every CTA of the cluster computes the grid (nbx, nby,
+// h: the same values from the same positions) into its own shared memory, and only cluster
+// rank 0 writes the arrays, which the others read after the caller's cluster barrier.
+template <bool W = false>
 __device__ void near_build(const Ctx<float>& x, int d) {
     __shared__ float s_box[4][32];
     __shared__ float s_g[3];
@@ -470,7 +515,7 @@ __device__ void near_build(const Ctx<float>& x, int d) {
     const float2* z = x.cur + (size_t)d * nr;
     float b[4] = {FLT_MAX, FLT_MAX, FLT_MAX, FLT_MAX};  // min x, min y, -max x, -max y
     for (int k = tid; k < nr; k += P) {
-        const float2 v = z[k];
+        const float2 v = ldw<W>(z + k);
         b[0] = fminf(b[0], v.x);
         b[1] = fminf(b[1], v.y);
         b[2] = fminf(b[2], -v.x);
@@ -504,6 +549,9 @@ __device__ void near_build(const Ctx<float>& x, int d) {
         s_g[2] = 1.f / h;
     }
     __syncthreads();
+    if constexpr (W) {
+        if (cluster_rank() != 0) return;  // block-uniform
+    }
     const int nbx = x.s_ngrid[2 * d], nby = x.s_ngrid[2 * d + 1], nc = nbx * nby;
     const float x0 = s_g[0], y0 = s_g[1], ih = s_g[2];
     int* key = x.nkey + (size_t)d * nr;
@@ -514,7 +562,7 @@ __device__ void near_build(const Ctx<float>& x, int d) {
     for (int c = tid; c < nc; c += P) fill[c] = 0;
     __syncthreads();
     for (int k = tid; k < nr; k += P) {
-        const float2 v = z[k];
+        const float2 v = ldw<W>(z + k);
         // clamped in floating point first (a NaN position lands in cell 0)
         const float fx = fminf(fmaxf((v.x - x0) * ih, 0.f), (float)(nbx - 1));
         const float fy = fminf(fmaxf((v.y - y0) * ih, 0.f), (float)(nby - 1));
@@ -545,7 +593,7 @@ __device__ void near_build(const Ctx<float>& x, int d) {
     for (int i = tid; i < nr; i += P) {
         const int kk = ord[i], k = kk - d * nr, c = key[k];
         x.nrank[kk] = i;
-        x.nref[d * nr + i] = z[k];
+        x.nref[d * nr + i] = ldw<W>(z + k);
         x.ncell[d * nr + i] = ((c / nbx) << 16) | (c % nbx);
     }
     __syncthreads();
@@ -556,7 +604,7 @@ __device__ void near_build(const Ctx<float>& x, int d) {
 // that a warp never mixes the directions and every root-tile load is a broadcast.  twin: the
 // two directions hold the same positions (the first rows either side of a cold row), so
 // direction 0's sums serve root k + nr too, which is then updated with direction 1's phase.
-template <int R, bool CAPTURE>
+template <int R, bool CAPTURE, bool W = false>
 __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool a1, int A0, int A1, float cph0,
                                               float sph0, float cph1, float sph1, int* s_maxit, bool twin = false) {
     using C = float2;
@@ -667,8 +715,8 @@ __device__ __forceinline__ void sweep_blocked(const Ctx<float>& x, bool a0, bool
             for (int r = 0; r < R; r++)
                 if (valid[r]) {
                     float nx = 0.f, ny = 0.f;
-                    const int code = d * nr + x.nrank[key[r]];
-                    *x.n_root += (unsigned long long)near_sum(x, d, x.ncell[code], z[r].x, z[r].y, nx, ny);
+                    const int code = d * nr + ldw<W>(x.nrank + key[r]);
+                    *x.n_root += (unsigned long long)near_sum<W>(x, d, ldw<W>(x.ncell + code), z[r].x, z[r].y, nx, ny);
                     x.nfar[code] = make_float2(acc[r].Dx - nx, acc[r].Dy - ny);
                     if (twin) x.nfar[nr + code] = x.nfar[code];
                 }
@@ -744,6 +792,7 @@ __device__ __forceinline__ void star_part_light(const Ctx<float>& x, float zx, f
 // refresh positions are read by code (in shared memory when they fit).  ordered: the list is
 // the refresh's cell order itself (a row's first sweep), so slot s holds code s (direction 0)
 // or nr + s - A0 (direction 1) and neighbouring threads read neighbouring entries.
+template <bool W = false>
 __device__ void sweep_light(const Ctx<float>& x, bool ordered, int A0, int A1, float cph0, float sph0, float cph1,
                             float sph1, int* s_maxit) {
     const TK& K = *x.k;
@@ -763,51 +812,21 @@ __device__ void sweep_light(const Ctx<float>& x, bool ordered, int A0, int A1, f
             key = x.nord[code];
         } else {
             key = d ? x.act[nr + slot - A0] : x.act[slot];
-            code = d * nr + x.nrank[key];
+            code = d * nr + ldw<W>(x.nrank + key);
         }
-        const float2 z = x.npos[code];
+        const float2 z = ldw<W>(x.npos + code);
         Acc<float> acc = Acc<float>{0, 0, 0, 0, 0, 0, 0, 0, 0};
         star_part_light(x, z.x, z.y, acc);
         float Dx = 0.f, Dy = 0.f;
-        *x.n_root += (unsigned long long)near_sum(x, d, x.ncell[code], z.x, z.y, Dx, Dy);
-        const float2 f = x.nfar[code];
+        *x.n_root += (unsigned long long)near_sum<W>(x, d, ldw<W>(x.ncell + code), z.x, z.y, Dx, Dy);
+        const float2 f = x.nfar[code];  // (written by this CTA)
         acc.Dx = Dx + f.x;
         acc.Dy = Dy + f.y;
         const float2 zn = finish_root<float>(x, key, z, acc, d ? cph1 : cph0, d ? sph1 : sph0, s_maxit);
-        const float2 zr = x.nref[code];
+        const float2 zr = ldw<W>(x.nref + code);
         const float ex = zn.x - zr.x, ey = zn.y - zr.y;
         if (!(ex * ex + ey * ey <= x.s_nlim2[d])) *x.s_nesc = 1;
     }
-}
-
-// Thread-block clusters: several CTAs share one phi sub-range (each updates a slice of the
-// roots and reads all of them); hardware cluster barriers order the sweeps, and per-CTA
-// counts are summed through distributed shared memory.
-__device__ __forceinline__ unsigned cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ unsigned cluster_size() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
-
-// All threads of all CTAs of the cluster; global and shared writes before it are visible
-// to every thread of the cluster after it.
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ int ld_cluster(const int* local, unsigned rank) {
-    const unsigned a = (unsigned)__cvta_generic_to_shared(local);
-    unsigned ra;
-    int v;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
-    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
-    return v;
 }
 
 // Sum of three CTA-uniform ints over the cluster (called by all threads of every CTA in the
@@ -842,6 +861,25 @@ __device__ __forceinline__ void cluster_sum3(const Ctx<T>& x, int& a, int& b, in
     c = x.s_tot[2];
 }
 
+// A cluster's split refresh at the current positions: every CTA computes the grid, cluster
+// rank 0 writes the cell arrays, each CTA then writes the cell-ordered positions of its own
+// roots.  Cluster barriers before (every CTA's positions published), between and after.
+// Called by every thread of every CTA of the cluster, with the same a0, a1.
+__device__ void wide_refresh(const Ctx<float>& x, bool a0, bool a1) {
+    const int nr = x.k->nr, tid = threadIdx.x, P = blockDim.x, W = x.hi - x.lo;
+    cluster_sync();
+    if (a0) near_build<true>(x, 0);
+    if (a1) near_build<true>(x, 1);
+    cluster_sync();
+    for (int i = tid; i < 2 * W; i += P) {
+        const int d = i >= W;
+        if (!(d ? a1 : a0)) continue;
+        const int key = d * nr + x.lo + (i - d * W);
+        x.npos[d * nr + __ldcg(x.nrank + key)] = x.cur[key];
+    }
+    cluster_sync();
+}
+
 // Run Jacobi Aberth sweeps on the active rows (dir 0: row0, dir 1: row1) until every root
 // is frozen or max_iter sweeps were made.  Called by all threads of the CTA.  The unfrozen
 // roots of direction d are listed in act[d nr, d nr + A_d).  With many of them the FP32
@@ -874,7 +912,7 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
     const int lo = x.lo, W = x.hi - x.lo;
     Ctx<T> xs = x;
     xs.act = x.act + lo;  // this CTA's lists: [lo, lo + A0) and [nr + lo, nr + lo + A1)
-    if constexpr (sizeof(T) != 4 || WIDE) mode = SUM_FULL;
+    if constexpr (sizeof(T) != 4) mode = SUM_FULL;
     bool split = mode != SUM_FULL;  // (cleared when a sweep's few roots are summed exactly instead)
     if constexpr (sizeof(T) == 4 && !WIDE) {
         if (split) {
@@ -906,10 +944,19 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             }
         }
     }
+    if constexpr (sizeof(T) == 4 && WIDE) {
+        // (mode is cluster-uniform: the same sequence of cluster barriers in every CTA)
+        if (split) {
+            __syncthreads();
+            if (tid == 0) *x.s_nesc = 0;
+        }
+        if (mode == SUM_CAPTURE) wide_refresh(x, a0, a1);
+    }
     int Ap0 = 0, Ap1 = 0;  // previous sweep's list lengths (split sweeps)
     bool recap = false;    // a cold row's iterate left its limit: new cells and far parts first
     bool esc = false;      // a warm row's iterate left its limit: the caller solves the row again
     int* next = nullptr;   // split sweeps: the next list, already built by the last position update
+    int pend = 0;          // cluster: an iterate of this CTA left its limit in the last sweep
     for (int iter = 0;; iter++) {
         __syncthreads();
         if (!next && tid < 2) s_count[tid] = 0;
@@ -965,9 +1012,22 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         const int A = A0 + A1;
         int At = A;
         if constexpr (WIDE) {
-            int u0 = A0, u1 = A1, u2 = 0;
+            int u0 = A0, u1 = A1, u2 = pend;
             cluster_sum3(x, u0, u1, u2);  // also publishes the previous sweep's positions
             At = u0 + u1;
+            if constexpr (sizeof(T) == 4) {
+                // an escape anywhere in the cluster (a cluster-uniform decision): a cold row
+                // refreshes the split, a warm row stops and is solved again
+                pend = 0;
+                if (u2 > 0) {
+                    if (cold) {
+                        recap = true;
+                    } else {
+                        esc = true;
+                        break;
+                    }
+                }
+            }
         }
         if (At == 0) break;
         if (iter >= max_iter) {
@@ -978,28 +1038,35 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             atomicAdd(&K.rep->root_iterations, (unsigned long long)A);
             if (cold) atomicAdd(&K.rep->cold_root_iterations, (unsigned long long)A);
         }
-        if (A == 0) {
-            if constexpr (WIDE) cluster_sync();  // the barrier the other CTAs take before their copies
-            continue;
-        }
-        if constexpr (sizeof(T) == 4 && !WIDE) {
+        if constexpr (sizeof(T) == 4) {
             // A light sweep costs about one root update's latency however few roots it
             // holds, an exact sweep of A roots about A nr terms spread over the block: below
-            // A nr = 1024 P the rest of the row is summed exactly (always valid; the next
-            // row's prediction guard still checks every position against its refresh).
-            if (split && iter > 0 && mode == SUM_LIGHT && (int64_t)A * nr <= (int64_t)P * 1024) {
+            // A nr = 1024 P (over the cluster: its active roots and threads) the rest of the row
+            // is summed exactly (always valid; the next row's prediction guard still checks
+            // every position against its refresh).  Decided before a CTA without active roots
+            // leaves the iteration, from cluster-uniform values.
+            int64_t Au = A, Pu = P;
+            if constexpr (WIDE) {
+                Au = At;
+                Pu = (int64_t)P * cluster_size();
+            }
+            if (split && iter > 0 && mode == SUM_LIGHT && Au * nr <= Pu * 1024) {
                 split = false;
                 mode = SUM_FULL;
                 recap = false;
             }
-            if (recap) {  // block-uniform
+            if (recap) {  // block- (cluster-) uniform
                 // cells at the current positions and an exact sweep capturing the far parts
                 // again: from here on the split holds as after any refresh
-                if (a0) near_build(x, 0);
-                if (a1) near_build(x, 1);
-                for (int i = tid; i < nr; i += P) {
-                    if (a0) x.npos[i] = x.cur[x.nord[i]];
-                    if (a1) x.npos[nr + i] = x.cur[x.nord[nr + i]];
+                if constexpr (WIDE) {
+                    wide_refresh(x, a0, a1);
+                } else {
+                    if (a0) near_build(x, 0);
+                    if (a1) near_build(x, 1);
+                    for (int i = tid; i < nr; i += P) {
+                        if (a0) x.npos[i] = x.cur[x.nord[i]];
+                        if (a1) x.npos[nr + i] = x.cur[x.nord[nr + i]];
+                    }
                 }
                 if (tid == 0) *x.s_nesc = 0;
                 __syncthreads();
@@ -1007,10 +1074,17 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 recap = false;
             }
         }
+        if (A == 0) {
+            // (the other CTAs sweep: keep the cluster-uniform state as they will have it)
+            if (mode == SUM_CAPTURE) mode = SUM_LIGHT;
+            if constexpr (WIDE) cluster_sync();  // the barrier the other CTAs take before their copies
+            continue;
+        }
         bool blocked = false;
-        if constexpr (sizeof(T) == 4 && !WIDE) {
+        if constexpr (sizeof(T) == 4) {
             if (mode == SUM_LIGHT) {
-                sweep_light(xs, iter == 0, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
+                // (a cluster's lists are slices of keys, never the cell order itself)
+                sweep_light<WIDE>(xs, !WIDE && iter == 0, A0, A1, cph0, sph0, cph1, sph1, s_maxit);
                 blocked = true;
             }
         }
@@ -1020,14 +1094,14 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
         if (mode != SUM_LIGHT && tid == 0) *x.n_root += (unsigned long long)(A0 + SA1) * nr;
         if constexpr (sizeof(T) == 4) {
             if (!blocked && A0 + SA1 >= P) {
-                const bool cap = !WIDE && mode == SUM_CAPTURE;
+                const bool cap = mode == SUM_CAPTURE;
                 const bool b1 = tw ? false : a1;
                 if (A0 + SA1 >= 2 * P) {
-                    if (cap) sweep_blocked<4, !WIDE>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
-                    else sweep_blocked<4, false>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
+                    if (cap) sweep_blocked<4, true, WIDE>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
+                    else sweep_blocked<4, false, WIDE>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
                 } else {
-                    if (cap) sweep_blocked<2, !WIDE>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
-                    else sweep_blocked<2, false>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
+                    if (cap) sweep_blocked<2, true, WIDE>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
+                    else sweep_blocked<2, false, WIDE>(xs, a0, b1, A0, SA1, cph0, sph0, cph1, sph1, s_maxit, tw);
                 }
                 blocked = true;
             }
@@ -1095,11 +1169,12 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                     acc.Dy += shfl_x(acc.Dy, off);
                     acc.Am += shfl_x(acc.Am, off);
                 }
-                if constexpr (sizeof(T) == 4 && !WIDE) {
+                if constexpr (sizeof(T) == 4) {
                     if (mode == SUM_CAPTURE && valid && lane == 0) {
                         float nx = 0.f, ny = 0.f;
-                        const int code = d * nr + x.nrank[key];
-                        *x.n_root += (unsigned long long)near_sum(x, d, x.ncell[code], z.x, z.y, nx, ny);
+                        const int code = d * nr + ldw<WIDE>(x.nrank + key);
+                        *x.n_root +=
+                            (unsigned long long)near_sum<WIDE>(x, d, ldw<WIDE>(x.ncell + code), z.x, z.y, nx, ny);
                         x.nfar[code] = make_float2(acc.Dx - nx, acc.Dy - ny);
                     }
                 }
@@ -1121,6 +1196,8 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
                 break;
             }
         }
+        // a cluster decides at the next reduction, over all its CTAs
+        if constexpr (sizeof(T) == 4 && WIDE) pend = (split && *x.s_nesc) ? 1 : 0;
         next = nullptr;
         if constexpr (sizeof(T) == 4 && !WIDE) {
             if (split) {
@@ -1146,6 +1223,11 @@ __device__ __forceinline__ int solve_rows(const Ctx<T>& x, bool a0, bool a1, int
             for (int i = tid; i < A; i += P) {
                 const int key = i < A0 ? xs.act[i] : xs.act[nr + i - A0];
                 x.cur[key] = x.nxt[key];
+                if constexpr (sizeof(T) == 4 && WIDE) {
+                    // a cluster's own roots into the shared cell-ordered positions (read by the
+                    // other CTAs after the next cluster barrier)
+                    if (split) x.npos[(key >= nr ? nr : 0) + __ldcg(x.nrank + key)] = x.nxt[key];
+                }
             }
     }
     // directions that still hold unfrozen roots
@@ -1368,7 +1450,7 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
         seed_guesses<T>(x, 0, (T)ph.x, (T)ph.y);
     }
     for (int k = lo + tid; k < hi; k += P) x.conv[nr + k] = 1;
-    const int KR = (sizeof(T) == 4 && !WIDE) ? K.root_refresh : 0;
+    const int KR = sizeof(T) == 4 ? K.root_refresh : 0;
     // the cold row splits its root sum too: cells and far parts at the guesses, refreshed
     // whenever an iterate leaves its limit
     solve_rows<T, WIDE>(x, true, false, c, -1, K.max_iter_cold, true, true, s_count, &s_maxit,
@@ -1471,10 +1553,10 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
                     // cells from an earlier refresh: the prediction goes to its place in cell
                     // order (a refresh row gathers all positions again after its new cells)
                     if (!refresh_due) {
-                        const int code = (k >= nr ? nr : 0) + x.nrank[k];
+                        const int code = (k >= nr ? nr : 0) + ldw<WIDE>(x.nrank + k);
                         x.npos[code] = g;
                         if (mode == SUM_LIGHT) {
-                            const float2 r = x.nref[code];
+                            const float2 r = ldw<WIDE>(x.nref + code);
                             const float ex = g.x - r.x, ey = g.y - r.y;
                             out |= !(ex * ex + ey * ey <= s_nlim2[dd]);
                         }
@@ -1485,8 +1567,16 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
             x.it[k] = 0;
             x.dprev[k] = FLT_MAX;
         }
-        // a prediction beyond its displacement limit: refresh at this row
-        if (mode == SUM_LIGHT && __syncthreads_or(out)) mode = SUM_CAPTURE;
+        // a prediction beyond its displacement limit: refresh at this row (over a cluster: any
+        // CTA's, a cluster-uniform decision; mode itself is uniform)
+        if (mode == SUM_LIGHT) {
+            int o = __syncthreads_or(out);
+            if constexpr (WIDE) {
+                int z1 = 0, z2 = 0;
+                cluster_sum3(x, o, z1, z2);
+            }
+            if (o) mode = SUM_CAPTURE;
+        }
         // the first rows either side of the cold row start from its positions (no history yet):
         // one capture sweep serves both directions when every root of both is swept
         const bool twin = sizeof(T) == 4 && !WIDE && t == 1 && a0 && a1 && mode == SUM_CAPTURE && nr >= P &&
