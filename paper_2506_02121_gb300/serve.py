@@ -116,6 +116,7 @@ class Server:
         self.policy = AdmissionPolicy(slots, budget_bytes)
         self.clock = clock
         self.t0 = clock()
+        self.realtime = True
         self.results: dict = {}
         self.running: dict = {}   # slot -> (request, handle, nbytes)
         self.free_slots = list(range(slots))
@@ -124,7 +125,9 @@ class Server:
         return self.clock() - self.t0
 
     def submit(self, req: Request):
-        res = Result(req.rid, req.arrival)
+        # latency runs from the arrival, or from the submission when requests are fed all at
+        # once ahead of their arrival times
+        res = Result(req.rid, req.arrival if self.realtime else self.now())
         self.results[req.rid] = res
         nb = self.ex.estimate_bytes(req)
         if not self.policy.fits_ever(nb):
@@ -170,6 +173,7 @@ class Server:
         """Feed requests at their arrival times (realtime) or all at once; return results."""
         pending = sorted(requests, key=lambda r: r.arrival)
         i = 0
+        self.realtime = realtime
         self.t0 = self.clock()
         while i < len(pending) or not self.idle():
             t = self.now()
