@@ -116,12 +116,15 @@ typedef struct cc_options {
                               0 = automatic (1 when n_r < 4096, or when m >= 8 x the SM count and
                               the form is CC_FP64 or root_refresh >= 2; else 8), 1 = one CTA per
                               sub-range, 2..16 = that many */
-    int32_t root_refresh;  /* Aberth root sum of the FP32 tracer's warm rows (one CTA per sub-range):
-                              0 or 1 = exact in every sweep (Sec. 3.2); K >= 2 = exact every K-th row
-                              of a chain, where each root's sum is split into the roots of the 3 x 3
-                              cells around it (summed exactly in every sweep) and the rest (kept
-                              from the refresh row).  The roots found are the same zeros of F; only
-                              the Aberth iteration path changes.  At most 4096; default 64. */
+    int32_t root_refresh;  /* Aberth root sum of the FP32 tracer (one CTA or a cluster per
+                              sub-range): 0 or 1 = exact in every sweep (Sec. 3.2); K >= 2 = exact
+                              every K-th row of a chain (and whenever an iterate moves beyond a
+                              quarter cell from its refresh position), where each root's sum is
+                              split into the roots of the 3 x 3 cells around it (summed exactly in
+                              every sweep) and the rest (kept from the refresh).  Cold rows split
+                              too, from cells at the guesses.  The roots found are the same zeros
+                              of F; only the Aberth iteration path changes.  At most 4096; default
+                              64.  The FP64 forms always sum exactly. */
 } cc_options;
 
 /* Solve statistics of the last cc_critical_curves on a field (host copy). */
