@@ -100,3 +100,32 @@ def test_policy_never_overtakes_a_blocked_head():
     assert p.pop_admissible() == ("tiny", 1)
     with pytest.raises(ValueError):
         AdmissionPolicy(0, 10)
+
+
+class TickClock:
+    """Advances by a fixed step at every reading (the server loop reads it as it polls)."""
+
+    def __init__(self, step=1e-3):
+        self.t = 0.0
+        self.step = step
+
+    def __call__(self):
+        self.t += self.step
+        return self.t
+
+
+def test_all_at_once_latency_runs_from_submission():
+    """Requests fed all at once ahead of their arrival times: latency counts from the
+    submission (never negative); fed in real time it counts from the arrival."""
+    for realtime in (False, True):
+        clock = TickClock()
+        ex = FakeExecutor(clock)
+        srv = Server(ex, slots=3, budget_bytes=9000, clock=clock)
+        reqs = [r for r in _requests() if r.rid not in (13, 99)]
+        res = srv.run(reqs, realtime=realtime, sleep=0)
+        assert all(r.status == "ok" for r in res)
+        assert all(r.latency >= 0.0 for r in res)
+        if not realtime:
+            assert max(r.arrival for r in res) < 0.05   # every request submitted at the start
+        else:
+            assert [r.arrival for r in res] == [q.arrival for q in reqs]
