@@ -1521,7 +1521,7 @@ __device__ __forceinline__ void run_subchain(const TK& K, const int s, char* w, 
         __syncthreads();
         const bool refresh_due = s_refresh != 0;
         int mode = SUM_FULL;
-        if (KR >= 2) mode = (refresh_due || (t - 1) % KR == 0) ? SUM_CAPTURE : SUM_LIGHT;
+        if (KR >= 2) mode = (refresh_due || (t - 1) % max(KR, 1) == 0) ? SUM_CAPTURE : SUM_LIGHT;
         bool out = false;  // a prediction beyond its displacement limit (light rows)
         for (int i = tid; i < 2 * (hi - lo); i += P) {
             const int dd = i >= hi - lo;
@@ -2032,6 +2032,11 @@ __global__ void compose_perm_batch_kernel(const TraceTask* tasks) {
 constexpr int SEAM_G = 256;
 constexpr int SEAM_T = 512;
 
+// Cells per side of a seam's grid: about 2 roots per cell, at most SEAM_G.
+static int seam_grid_cells(int64_t nr) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(SEAM_G, (int64_t)std::ceil(std::sqrt(0.5 * (double)nr))));
+}
+
 __device__ __forceinline__ void seam_consider(float2 b, float2 q, int j, float& best, float& second, int& bi) {
     const float dx = b.x - q.x, dy = b.y - q.y;  // (this unit contracts no a*b + c: as the full scan)
     const float d2 = dx * dx + dy * dy;
@@ -2045,8 +2050,8 @@ __device__ __forceinline__ void seam_consider(float2 b, float2 q, int j, float& 
 }
 
 __global__ void __launch_bounds__(SEAM_T) seam_grid_kernel(const float2* zrows, const float2* seam, int64_t m, int S,
-                                                           int nr, char* work, size_t work_stride, int32_t* match,
-                                                           int32_t* hits, DevReport* rep) {
+                                                           int nr, int G, char* work, size_t work_stride,
+                                                           int32_t* match, int32_t* hits, DevReport* rep) {
     __shared__ float s_box[4][SEAM_T / 32];
     __shared__ float s_g[4];  // x0, y0, 1/h, h
     __shared__ int s_scan[32];
@@ -2055,7 +2060,7 @@ __global__ void __launch_bounds__(SEAM_T) seam_grid_kernel(const float2* zrows, 
     const int s = blockIdx.x;
     const float2* B = zrows + (size_t)subchain_begin(s + 1, m, S) * nr;
     const float2* Q = seam + (size_t)s * nr;
-    const int G = max(1, min(SEAM_G, (int)ceilf(sqrtf(0.5f * (float)nr))));
+    // G: cells per side, from seam_grid_cells (the size the host checked the scratch for)
     const int nc = G * G;
     float2* pos = (float2*)(work + (size_t)s * work_stride);
     int* idx = (int*)(pos + nr);
@@ -2219,7 +2224,8 @@ cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int
         if (e != cudaSuccess) return e;
         if (grid_ok) {
             seam_grid_kernel<<<(unsigned)(S - 1), SEAM_T, 0, st>>>((const float2*)zrows, (const float2*)seam, m, S,
-                                                                 (int)nr, (char*)work, work_stride, match, hits, rep);
+                                                                 (int)nr, seam_grid_cells(nr), (char*)work,
+                                                                 work_stride, match, hits, rep);
         } else {
             dim3 grid((unsigned)((nr + 255) / 256), (unsigned)(S - 1));
             if (fp64)
@@ -2249,7 +2255,7 @@ cudaError_t launch_seam_join(const void* zrows, const void* seam, int64_t m, int
 
 // Scratch of one seam's grid: positions and indices of the row, cell starts and counters.
 size_t seam_grid_bytes(int64_t nr) {
-    const int64_t G = std::max<int64_t>(1, std::min<int64_t>(SEAM_G, (int64_t)std::ceil(std::sqrt(0.5 * (double)nr))));
+    const int64_t G = seam_grid_cells(nr);
     return (size_t)nr * (sizeof(float2) + sizeof(int)) + (size_t)(2 * G * G + 1) * sizeof(int);
 }
 
